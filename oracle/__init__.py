@@ -1,0 +1,23 @@
+"""FP64 CPU oracle for the SPECT system matrix and OSEM (test infrastructure).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library never imports it and
+shares no code with it.  See ``spect_oracle.c`` for the definitions and the
+readings taken where the paper is silent.
+"""
+from .oracle import (  # noqa: F401
+    Geom,
+    attenuation,
+    back,
+    build,
+    forward,
+    n_threads,
+    osem,
+    poisson_ll,
+    psf_rmax,
+    psf_taps,
+    rotate,
+    rotate_adjoint,
+    set_threads,
+    subset_angles,
+)

@@ -1,0 +1,233 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test is chosen so that a plausible slip in the oracle (a dropped term,
+a wrong sign or index, a transposed operand) fails at least one of them:
+  - brute force: dense H assembled from scipy/numpy library routines (8^3);
+  - rotation: identity at 0, exact index permutations at 90/180/270 degrees,
+    scipy's bilinear affine transform at arbitrary angles;
+  - attenuation: exp(-mu L) through a uniform medium (closed form);
+  - PSF: unit sum, centre and second moment of a point source against the
+    continuous Gaussian sigma_i^2 with sigma_i linear in the depth distance;
+  - adjointness <Hx, y> = <x, H^T y>;
+  - OSEM count conservation (s = 0) and its s > 0 form;
+  - the Poisson gradient of Table 1 against central finite differences of
+    the log-likelihood.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import brute
+from paper_2309_01977_gb300 import phantom
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+# ---------------------------------------------------------------- rotation
+
+def test_rotation_zero_angle_is_identity(oracle_mod):
+    f = _rng(1).uniform(size=(9, 9, 4))
+    np.testing.assert_array_equal(oracle_mod.rotate(f, 0.0), f)
+
+
+@pytest.mark.parametrize("quarter", [1, 2, 3])
+def test_rotation_quarter_turns_are_permutations(oracle_mod, quarter):
+    n, nz = 10, 3
+    f = _rng(2).uniform(size=(n, n, nz))
+    out = oracle_mod.rotate(f, quarter * math.pi / 2)
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    # sample point of rotated voxel (i, j) for cos/sin in {0, +-1}
+    ct = [1, 0, -1, 0][quarter]
+    st = [0, 1, 0, -1][quarter]
+    c2 = n - 1  # 2c
+    u2 = c2 + ct * (2 * i - c2) - st * (2 * j - c2)
+    v2 = c2 + st * (2 * i - c2) + ct * (2 * j - c2)
+    expect = f[u2 // 2, v2 // 2, :]
+    np.testing.assert_allclose(out, expect, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("theta", [0.3, 1.1, 2.5, 4.0, 5.9])
+def test_rotation_matches_scipy_bilinear(oracle_mod, theta):
+    f = _rng(3).uniform(size=(13, 13, 5))
+    np.testing.assert_allclose(oracle_mod.rotate(f, theta), brute.rotate_lib(f, theta), rtol=0, atol=1e-13)
+
+
+def test_rotation_adjoint_dot(oracle_mod):
+    rng = _rng(4)
+    x = rng.normal(size=(11, 11, 3))
+    y = rng.normal(size=(11, 11, 3))
+    for theta in (0.7, 2.0, 3.3):
+        lhs = np.vdot(oracle_mod.rotate(x, theta), y)
+        rhs = np.vdot(x, oracle_mod.rotate_adjoint(y, theta))
+        assert abs(lhs - rhs) <= 1e-13 * (abs(lhs) + 1)
+
+
+# ---------------------------------------------------------------- attenuation
+
+@pytest.mark.parametrize("theta_q", [0, 1, 2])
+def test_uniform_medium_attenuation_closed_form(oracle_mod, theta_q):
+    """A point source behind L = (n-1-i+1/2) voxels of uniform mu reaches the detector with exp(-mu*dx*L)."""
+    n, nz, mu0, dx = 12, 5, 0.2, 0.48
+    theta = theta_q * math.pi / 2
+    mu = np.full((n, n, nz), mu0)
+    g = oracle_mod.Geom(n=n, nz=nz, n_angles=1, angles=[theta], voxel_cm=dx, mu=mu, use_psf=False)
+    for (x0, y0, z0) in [(2, 3, 1), (9, 6, 4), (5, 11, 0)]:
+        f = np.zeros((n, n, nz))
+        f[x0, y0, z0] = 1.0
+        proj = oracle_mod.forward(f, g)[0]
+        # rotated-frame coordinates of the source (quarter turns are permutations)
+        if theta_q == 0:
+            depth, bin_y = x0, y0
+        elif theta_q == 1:
+            depth, bin_y = y0, n - 1 - x0
+        else:
+            depth, bin_y = n - 1 - x0, n - 1 - y0
+        expect = math.exp(-mu0 * dx * (n - 1 - depth + 0.5))
+        assert proj[bin_y, z0] == pytest.approx(expect, rel=1e-13)
+        proj[bin_y, z0] = 0.0
+        assert np.abs(proj).max() < 1e-14
+
+
+def test_attenuation_map_matches_cumulative_sum(oracle_mod):
+    mu = _rng(5).uniform(0, 0.3, size=(9, 9, 4))
+    for theta in (0.0, 0.9, 4.4):
+        np.testing.assert_allclose(oracle_mod.attenuation(mu, theta, 0.48),
+                                   brute.attenuation_lib(mu, theta, 0.48), rtol=1e-13, atol=0)
+
+
+# ---------------------------------------------------------------- PSF
+
+@pytest.mark.parametrize("depth", [0, 10, 20, 40])
+def test_psf_point_source_second_moment(oracle_mod, depth):
+    """With negligible truncation (12 sigma) the sampled Gaussian of sigma >= 1 has
+    variance sigma^2 up to e^(-2 pi^2 sigma^2); sigma_i = sigma0 + slope*(n - i - 1/2)."""
+    n, nz = 64, 64
+    sigma0, slope = 0.5, 0.03
+    g = oracle_mod.Geom(n=n, nz=nz, n_angles=1, angles=[0.0], mu=None, use_psf=True,
+                        sigma0=sigma0, slope=slope, nsigma=12.0)
+    f = np.zeros((n, n, nz))
+    j0, k0 = 31, 33
+    f[depth, j0, k0] = 1.0
+    p = oracle_mod.forward(f, g)[0]
+    sigma = sigma0 + slope * (n - depth - 0.5)
+    assert sigma >= 1.0
+    jj, kk = np.meshgrid(np.arange(n) - j0, np.arange(nz) - k0, indexing="ij")
+    assert p.sum() == pytest.approx(1.0, abs=1e-13)
+    assert (p * jj).sum() == pytest.approx(0.0, abs=1e-12)
+    assert (p * kk).sum() == pytest.approx(0.0, abs=1e-12)
+    assert (p * jj * jj).sum() == pytest.approx(sigma * sigma, rel=1e-7)
+    assert (p * kk * kk).sum() == pytest.approx(sigma * sigma, rel=1e-7)
+    assert (p * jj * kk).sum() == pytest.approx(0.0, abs=1e-12)
+
+
+def test_psf_taps_radius_and_normalisation(oracle_mod):
+    sig, rad, taps = oracle_mod.psf_taps(128, 0.5, 0.03, 3.0)
+    d = 128 - np.arange(128) - 0.5
+    np.testing.assert_allclose(sig, 0.5 + 0.03 * d, rtol=1e-15)
+    np.testing.assert_array_equal(rad, np.ceil(3 * sig).astype(int))
+    assert rad.max() == 13 and rad.min() == 2
+    np.testing.assert_allclose(taps.sum(axis=1), 1.0, rtol=1e-14)
+    for i in (0, 64, 127):
+        np.testing.assert_allclose(taps[i][13 - rad[i]:13 + rad[i] + 1],
+                                   brute.gaussian_taps_lib(sig[i], 3.0), rtol=1e-14)
+
+
+# ---------------------------------------------------------------- whole operator
+
+def test_brute_force_dense_h_8cubed(oracle_mod):
+    """H x and H^T y of the oracle equal the library-built dense H at 8^3, 8 angles."""
+    n = nz = 8
+    rng = _rng(6)
+    mu = rng.uniform(0.0, 0.4, size=(n, n, nz))
+    angles = [2 * math.pi * a / 8 + 0.05 for a in range(8)]
+    kw = dict(voxel_cm=0.48, use_psf=True, sigma0=0.6, slope=0.15, nsigma=3.0)
+    H = brute.dense_h(n, nz, angles, mu, **kw)
+    g = oracle_mod.Geom(n=n, nz=nz, n_angles=8, angles=angles, mu=mu, **kw)
+    x = rng.uniform(size=(n, n, nz))
+    y = rng.uniform(size=(8, n, nz))
+    hx = oracle_mod.forward(x, g).ravel()
+    hty = oracle_mod.back(y, g).ravel()
+    ref_hx = H @ x.ravel()
+    ref_hty = H.T @ y.ravel()
+    assert np.abs(hx - ref_hx).max() <= 1e-12 * np.abs(ref_hx).max()
+    assert np.abs(hty - ref_hty).max() <= 1e-12 * np.abs(ref_hty).max()
+
+
+def test_adjoint_dot_product_composed(oracle_mod):
+    n, nz = 16, 12
+    rng = _rng(7)
+    mu = rng.uniform(0, 0.3, size=(n, n, nz))
+    g = oracle_mod.Geom(n=n, nz=nz, n_angles=12, mu=mu, use_psf=True, sigma0=0.5, slope=0.1)
+    x = rng.normal(size=(n, n, nz))
+    y = rng.normal(size=(12, n, nz))
+    lhs = np.vdot(oracle_mod.forward(x, g), y)
+    rhs = np.vdot(x, oracle_mod.back(y, g))
+    assert abs(lhs - rhs) <= 1e-13 * max(abs(lhs), 1.0)
+
+
+def test_subset_selection_is_interleaved(oracle_mod):
+    assert oracle_mod.subset_angles(60, 8, 0) == [0, 8, 16, 24, 32, 40, 48, 56]
+    assert oracle_mod.subset_angles(60, 8, 7) == [7, 15, 23, 31, 39, 47, 55]
+    sizes = [len(oracle_mod.subset_angles(120, 8, m)) for m in range(8)]
+    assert sizes == [15] * 8
+
+
+def _small_problem(oracle_mod, s_frac, seed=8):
+    n = nz = 16
+    f_raw, mu = phantom.make_phantom(n, nz, seed)
+    g = oracle_mod.Geom(n=n, nz=nz, n_angles=16, mu=mu, use_psf=True, sigma0=0.5, slope=0.05)
+    hf = oracle_mod.forward(f_raw, g)
+    f_true, y, s, _ = phantom.make_counts(f_raw, hf, 1e5, s_frac, seed)
+    return g, y, s
+
+
+@pytest.mark.parametrize("s_frac", [0.0, 0.05])
+def test_osem_count_conservation(oracle_mod, s_frac):
+    """sum_{S_m} H_m f_new = sum_{S_m} y * H_m f / (H_m f + s); for s = 0 that is sum y."""
+    g, y, s = _small_problem(oracle_mod, s_frac)
+    M = 4
+    f = np.ones((g.n, g.n, g.nz))
+    for t in range(6):
+        m = t % M
+        sel = oracle_mod.subset_angles(g.n_angles, M, m)
+        f_new, diag = oracle_mod.osem(y, s, g, M, t, 1, f)
+        lhs = oracle_mod.forward(f_new, g, sel).sum()
+        p = oracle_mod.forward(f, g, sel)
+        ys = y[sel]
+        expect = (ys * p / (p + s)).sum()
+        assert lhs == pytest.approx(expect, rel=1e-12)
+        assert diag[0, 2] == pytest.approx(expect, rel=1e-12)
+        assert diag[0, 1] == pytest.approx(ys.sum(), rel=1e-14)
+        assert diag[0, 0] == pytest.approx((p + s).sum(), rel=1e-12)
+        if s_frac == 0.0:
+            assert lhs == pytest.approx(ys.sum(), rel=1e-12)
+        f = f_new
+
+
+def test_osem_resume_equals_one_call(oracle_mod):
+    g, y, s = _small_problem(oracle_mod, 0.05)
+    f_all, _ = oracle_mod.osem(y, s, g, 4, 0, 5)
+    f_a, _ = oracle_mod.osem(y, s, g, 4, 0, 2)
+    f_b, _ = oracle_mod.osem(y, s, g, 4, 2, 3, f_a)
+    np.testing.assert_array_equal(f_all, f_b)
+
+
+def test_poisson_gradient_matches_finite_differences(oracle_mod):
+    """Table 1: grad L = H^T(y/(Hf+s)) - H^T 1 for L = sum y log(Hf+s) - (Hf+s)."""
+    g, y, s = _small_problem(oracle_mod, 0.05, seed=9)
+    f = _rng(10).uniform(0.5, 2.0, size=(g.n, g.n, g.nz)) * (y.sum() / 16 ** 3 / 16)
+    p = oracle_mod.forward(f, g)
+    grad = oracle_mod.back(y / (p + s), g) - oracle_mod.back(np.ones_like(p), g)
+    rng = _rng(11)
+    for _ in range(6):
+        q = tuple(rng.integers(0, 16, size=3))
+        h = 1e-3 * f[q]
+        fp = f.copy(); fp[q] += h
+        fm = f.copy(); fm[q] -= h
+        lp = oracle_mod.poisson_ll(y, oracle_mod.forward(fp, g), s)
+        lm = oracle_mod.poisson_ll(y, oracle_mod.forward(fm, g), s)
+        fd = (lp - lm) / (2 * h)
+        assert fd == pytest.approx(grad[q], rel=1e-5, abs=1e-6 * np.abs(grad).max())
