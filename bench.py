@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""OSEM throughput benchmark of libspect on the 128^3 x 120-angle workload.
+
+One step = one full OSEM reconstruction of the workload (4 iterations x 8
+subsets = 32 subiterations, attenuation and depth-dependent PSF on, FP32),
+from f0 = 1, with the measured counts y and the attenuation cache already
+resident in HBM.  The metric is subset-iterations per second over the whole
+job (all ranks).  Each timed step is bracketed by CUDA events on the stream
+the library launches on; L2 is flushed (256 MiB write) between steps, outside
+the events.
+
+Extra objects on the JSON line:
+  e2e          the same metric through the C-ABI with host buffers: the
+               copy of y from pinned host memory and the read-back of the
+               image are inside the timed region;
+  roofline     the dominant kernel's algorithmic bytes per launch over its
+               CUDA-event duration (a second, profiled pass of the same
+               steps), against the measured HBM copy bandwidth;
+  cpu_baseline the FP64 CPU oracle on a bounded sample of the workload;
+  clocks       nvidia-smi SM clocks and throttle reasons sampled during the
+               timed region.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+benchmark) on the host cores, one OSEM subiteration per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "OSEM subset-iters/s at 128^3x120 angles vs plain FP32; serve p50/p99 latency"
+UNIT = "subset-iters/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="libspect", choices=["libspect", "reference"])
+    ap.add_argument("--workload", default="osem128")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload_desc(wl) -> dict:
+    return {
+        "workload": "%s: %dx%dx%d FP32 volume (%.2f cm voxels), %d angles over 360 deg, %dx%d bins, %d it x %d subsets, "
+                    "attenuation (0.15/cm water, 0.25/cm bone) + PSF sigma=%.1f+%.2f*d, %.0e counts + %d%% scatter, "
+                    "seed %d" % (wl.name, wl.n, wl.n, wl.nz, wl.voxel_cm, wl.n_angles, wl.n, wl.nz, wl.n_iters,
+                                 wl.n_subsets, wl.sigma0, wl.slope, wl.counts, int(wl.scatter_frac * 100), wl.seed),
+        "step": "one full %d x %d OSEM reconstruction (%d subiterations) from f0 = 1" % (
+            wl.n_iters, wl.n_subsets, wl.n_iters * wl.n_subsets),
+    }
+
+
+# ---------------------------------------------------------------- helpers
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def algorithmic_bytes(kernel: str, wl, n_sel: int) -> float:
+    """Algorithmic bytes of one launch of `kernel` in an OSEM subiteration.
+
+    Per angle (FP32, attenuation cached): the forward reads the volume and
+    A_a and writes a projection, (N^3 + N^3 + N^2) * 4; the back projection
+    reads A_a and the projection ratio and writes its share of the volume,
+    (N^3 + 2 N^2) * 4, split here between the blur (A_a, ratio) and the
+    gather (the rotated-frame volume it reads, which replaces the second
+    read of A_a); the fused update reads f and sens and writes f, 3 N^3 * 4.
+    """
+    n3 = float(wl.n) * wl.n * wl.nz
+    n2 = float(wl.n) * wl.nz
+    if kernel == "forward":
+        return n_sel * (2 * n3 + n2) * 4
+    if kernel == "blur_back":
+        return n_sel * (n3 + n2) * 4
+    if kernel in ("gather_update", "gather"):
+        return (n_sel * n3 + 3 * n3) * 4
+    return 0.0
+
+
+def cpu_baseline(wl, y, s, mu64, seconds: float, steps=None):
+    """Time the FP64 oracle's OSEM on the host cores: whole subiterations until
+    `seconds` have passed (or exactly `steps` of them)."""
+    import oracle
+    og = oracle.Geom(n=wl.n, nz=wl.nz, n_angles=wl.n_angles, mu=mu64, voxel_cm=float(np.float32(wl.voxel_cm)),
+                     sigma0=float(np.float32(wl.sigma0)), slope=float(np.float32(wl.slope)),
+                     nsigma=float(np.float32(wl.nsigma)))
+    f = np.ones((wl.n, wl.n, wl.nz))
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        f, _ = oracle.osem(y, s, og, wl.n_subsets, done, 1, f)
+        done += 1
+        el = time.perf_counter() - t0
+        if steps is not None:
+            if done >= steps:
+                break
+        elif el >= seconds:
+            break
+    return {"value": done / el, "unit": UNIT, "cores": oracle.n_threads(), "kind": "oracle",
+            "sample": "first %d subiteration(s) of the %dx%d OSEM on %s (FP64, %.1f s)" % (
+                done, wl.n_iters, wl.n_subsets, wl.name, el)}
+
+
+def make_inputs_host(wl):
+    from paper_2309_01977_gb300 import phantom
+    f_raw, mu = phantom.make_phantom(wl.n, wl.nz, wl.seed)
+    return f_raw.astype(np.float32), mu.astype(np.float32)
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    from paper_2309_01977_gb300 import phantom
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    wl = phantom.WORKLOADS[args.workload]
+    f_raw, mu = make_inputs_host(wl)
+    mu64 = mu.astype(np.float64)
+    og = oracle.Geom(n=wl.n, nz=wl.nz, n_angles=wl.n_angles, mu=mu64, voxel_cm=float(np.float32(wl.voxel_cm)),
+                     sigma0=float(np.float32(wl.sigma0)), slope=float(np.float32(wl.slope)),
+                     nsigma=float(np.float32(wl.nsigma)))
+    hf = oracle.forward(f_raw.astype(np.float64), og)
+    _, y, s, _ = phantom.make_counts(f_raw.astype(np.float64), hf, wl.counts, wl.scatter_frac, wl.seed)
+    s = float(np.float32(s))
+    f = np.ones((wl.n, wl.n, wl.nz))
+    t = 0
+    for _ in range(args.warmup):
+        f, _ = oracle.osem(y, s, og, wl.n_subsets, t, 1, f)
+        t += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, _ = oracle.osem(y, s, og, wl.n_subsets, t, 1, f)
+        t += 1
+    el = time.perf_counter() - t0
+    value = args.steps / el
+    desc = workload_desc(wl)
+    desc["step"] = "one OSEM subiteration of the %dx%d reconstruction (FP64 CPU oracle)" % (wl.n_iters, wl.n_subsets)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": desc,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.n_threads(), "kind": "oracle",
+                         "sample": "subiterations %d..%d of the %dx%d OSEM on %s" % (
+                             args.warmup, args.warmup + args.steps - 1, wl.n_iters, wl.n_subsets, wl.name)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- libspect arm
+
+def run_libspect(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2309_01977_gb300 import phantom, spect
+
+    world, rank, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    spect.load()  # fails loudly without the CUDA library
+
+    wl = phantom.WORKLOADS[args.workload]
+    f_raw, mu = make_inputs_host(wl)
+    n_sub = wl.n_iters * wl.n_subsets
+    g = spect.Geometry(n=wl.n, nz=wl.nz, n_angles=wl.n_angles, n_subsets=wl.n_subsets, voxel_cm=wl.voxel_cm,
+                       psf_sigma0=wl.sigma0, psf_slope=wl.slope, psf_nsigma=wl.nsigma)
+    plan = spect.Plan(g, torch.from_numpy(mu).to(dev))
+    # measured data: y ~ Poisson(H f_true + s), H from the library itself
+    hf = plan.forward(torch.from_numpy(f_raw).to(dev)).double().cpu().numpy()
+    _, y, s, _ = phantom.make_counts(f_raw.astype(np.float64), hf, wl.counts, wl.scatter_frac, wl.seed)
+    s = float(np.float32(s))
+    y_host = torch.from_numpy(y.astype(np.float32)).pin_memory()
+    y_dev = y_host.to(dev)
+    x = torch.empty((wl.n, wl.n, wl.nz), device=dev)
+    x_host = torch.empty((wl.n, wl.n, wl.nz), dtype=torch.float32).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        x.fill_(1.0)
+        spect.spect_osem_run(plan.handle, y_dev, s, x, 0, n_sub)
+
+    def step_e2e():
+        y_dev.copy_(y_host, non_blocking=True)
+        x.fill_(1.0)
+        spect.spect_osem_run(plan.handle, y_dev, s, x, 0, n_sub)
+        x_host.copy_(x, non_blocking=True)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(fn, k):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        barrier()
+        torch.cuda.synchronize()
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return sum(e0.elapsed_time(e1) for e0, e1 in evs)
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        t = torch.tensor([v], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dev.index if world == 1 else local)
+    clocks.start()
+    launches0 = spect.spect_kernel_launches()
+    ms = timed(step, args.steps)
+    launches = spect.spect_kernel_launches() - launches0
+    clk = clocks.stop()
+    ms = max_over_ranks(ms)
+    value = world * args.steps * n_sub / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers
+    for _ in range(2):
+        step_e2e()
+    ms_e2e = max_over_ranks(timed(step_e2e, args.steps))
+    e2e = {"value": world * args.steps * n_sub / (ms_e2e / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(y_host.numel() * 4), "d2h_bytes_per_step": int(x_host.numel() * 4)}
+
+    # profiled pass: per-kernel CUDA-event durations on the launch stream
+    spect.spect_profile_enable(plan.handle, True)
+    spect.spect_profile_read(plan.handle, reset=True)
+    timed(step, args.steps)
+    prof = spect.spect_profile_read(plan.handle, reset=True)
+    spect.spect_profile_enable(plan.handle, False)
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (n_launch, tot_ms) = top
+    avg_s = tot_ms / n_launch / 1e3
+    n_sel = -(-wl.n_angles // wl.n_subsets)
+    nbytes = algorithmic_bytes(name, wl, n_sel)
+    peaks = measured_peaks()
+    achieved = nbytes / avg_s / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic_%s.json" % wl.name)
+    if os.path.exists(tpath):
+        with open(tpath) as fh:
+            traffic = json.load(fh).get(name)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": name,
+                "peak_source": peaks["source"], "avg_launch_us": avg_s * 1e6,
+                "algorithmic_bytes_per_launch": nbytes,
+                "kernel_share": {k: round(v[1] / sum(t[1] for t in prof.values()), 4) for k, v in prof.items()},
+                "kernel_avg_us": {k: round(1e3 * v[1] / v[0], 2) for k, v in prof.items()}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, y, s, mu.astype(np.float64), args.cpu_seconds)
+
+    if rank == 0:
+        cfg = workload_desc(wl)
+        cfg.update({"l2": "flushed between steps (256 MiB write), attenuation cache %.2f GB streamed"
+                          % (plan.info()["atten_cache_bytes"] / 1e9),
+                    "parallelism": "replicas" if world > 1 else "single GPU"})
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_libspect(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,187 @@
+/*
+ * spect.h -- C ABI of libspect, a GB300 (sm_103a) implementation of the
+ * parallel-hole SPECT system matrix H, its exact transpose H^T and OSEM.
+ *
+ * Method: PyTomography (arXiv 2309.01977).
+ *   - Sec. 2.1.1, Eq. (1): H = sum_n v_n (x) (T_fov P_x T_cdr T_att T_trans T_rot);
+ *     per projection angle n the volume is rotated (bilinear), weighted by
+ *     attenuation, blurred plane by plane by a depth-dependent Gaussian and
+ *     summed along the depth axis +x.  T_trans and T_fov are identities.
+ *   - Sec. 2.1.1: forward projection is H f, back projection is H^T g.
+ *   - Table 1: Poisson gradient H^T(g/(Hf+s)) - H^T 1 and the OSEM
+ *     preconditioner f / (H_m^T 1), which give the update
+ *     f <- f * H_m^T(g/(H_m f + s)) / H_m^T 1 over subsets m.
+ *   - Sec. 2.2 (Projectors): forward, backward, compute_normalization_factor,
+ *     set_n_subsets, get_projection_subset map to spect_forward, spect_back,
+ *     spect_sensitivity, spect_geom.n_subsets and the subset argument.
+ *
+ * Conventions (the paper leaves them open; the library fixes them):
+ *   volume   f[x][y][z], z fastest, nx == ny == n, float32, contiguous;
+ *   rotation about c = (n-1)/2; angle theta_a = 2*pi*a/n_angles unless given;
+ *            rotated voxel (i, j) samples f at
+ *              u = c + cos(t)(i-c) - sin(t)(j-c),  v = c + sin(t)(i-c) + cos(t)(j-c)
+ *            bilinearly, zero outside the grid; i is depth, j the detector bin;
+ *   attenuation  A[i] = exp(-(sum_{i'>i} tau[i'] + tau[i]/2)), tau = voxel_cm * (R mu),
+ *            detector on the +x side;
+ *   PSF      d_i = n - i - 0.5 + det_offset, sigma_i = psf_sigma0 + psf_slope * d_i
+ *            (voxels), taps exp(-t^2/(2 sigma_i^2)) for |t| <= ceil(psf_nsigma*sigma_i),
+ *            normalised to sum 1, applied along y and z with zero padding;
+ *   projections p[a][y][z] (angle, detector bin along y, axial bin z);
+ *   subsets  S_m = { a : a mod n_subsets == m }, angles in ascending order.
+ *
+ * Ownership: the caller owns every buffer it passes.  Device buffers are
+ * float32, contiguous and 16-byte aligned, else SPECT_EINVAL.  A plan owns
+ * its tables, attenuation cache, sensitivities and scratch.  Calls on one
+ * plan share that scratch: issue them in one stream (or order them with
+ * events); calls on different plans are independent.
+ *
+ * Errors: every call returns SPECT_OK (0) or a negative status; nothing
+ * aborts or throws across the ABI.  spect_last_error() gives a thread-local
+ * message for the last failure on the calling thread.
+ *
+ * Asynchrony: device work is queued on `stream` (a cudaStream_t; NULL is
+ * the legacy default stream) and the call returns without waiting, except
+ * where stated.
+ */
+#ifndef SPECT_H
+#define SPECT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define SPECT_OK 0
+#define SPECT_EINVAL (-1)      /* bad argument, size, alignment or geometry */
+#define SPECT_ENOMEM (-2)      /* device or host allocation failed */
+#define SPECT_ECUDA (-3)       /* a CUDA runtime call failed */
+#define SPECT_EBUDGET (-4)     /* request does not fit the memory budget */
+#define SPECT_ETIMEDOUT (-5)   /* a bounded wait ran out */
+#define SPECT_ECANCELLED (-6)  /* request was cancelled */
+#define SPECT_ESTATE (-7)      /* call not valid in the object's state */
+#define SPECT_ENOTFOUND (-8)   /* unknown request id */
+
+/* ---------------------------------------------------------------- geometry */
+#define SPECT_FLAG_ATTEN 1u      /* model attenuation (needs mu at plan creation) */
+#define SPECT_FLAG_PSF 2u        /* model the depth-dependent collimator blur */
+#define SPECT_FLAG_PSF_BF16 4u   /* PSF as banded-Toeplitz BF16 tensor-core GEMMs */
+#define SPECT_FLAG_ATTEN_F64 8u  /* attenuation prefix sums in FP64 (else compensated FP32) */
+
+typedef struct spect_geom {
+    int nx, ny, nz;           /* volume size; nx == ny required, nz % 4 == 0 */
+    float voxel_cm;           /* voxel edge in cm (scales mu to optical depth) */
+    int n_angles;             /* projections over 360 degrees */
+    const double* angles_rad; /* host array [n_angles] or NULL for 2*pi*a/n_angles */
+    float psf_sigma0;         /* sigma at the detector face, voxels */
+    float psf_slope;          /* d sigma / d distance, voxels per voxel */
+    float psf_nsigma;         /* truncation radius in sigmas (3 in the configs) */
+    float det_offset;         /* extra detector distance, voxels */
+    int n_subsets;            /* M >= 1 (ordered subsets) */
+    unsigned flags;           /* SPECT_FLAG_* */
+} spect_geom;
+
+typedef struct spect_plan spect_plan;
+
+/* Plan limits and figures the caller may want (spect_plan_query). */
+typedef struct spect_plan_info {
+    int n, nz, n_angles, n_subsets;
+    int max_subset_size;      /* largest |S_m| */
+    int psf_rmax;             /* largest PSF radius over depth planes */
+    size_t device_bytes;      /* device memory owned by the plan */
+    size_t atten_cache_bytes; /* part of it that is the per-angle A cache */
+} spect_plan_info;
+
+/* Create a plan: validates the geometry, builds the angle table, the
+ * per-plane PSF taps (Eq. 1, T_cdr), the subset lists (Sec. 2.2) and, with
+ * SPECT_FLAG_ATTEN, the per-angle attenuation cache A_a (T_att) from the
+ * device mu map [nx][ny][nz] in 1/cm, and the per-subset sensitivities
+ * H_m^T 1 (compute_normalization_factor).  Work is queued on `stream`;
+ * the call synchronises that stream before it returns.  mu is only read
+ * during the call.  *out is NULL on failure. */
+int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream, spect_plan** out);
+
+/* Free the plan and its device memory (waits for its work to finish). */
+int spect_plan_destroy(spect_plan* plan);
+
+int spect_plan_query(const spect_plan* plan, spect_plan_info* info);
+
+/* Number of angles of subset m (m == -1: all angles). */
+int spect_subset_size(const spect_plan* plan, int subset);
+
+/* Host copy of subset m's angle indices (ascending) into out[spect_subset_size]. */
+int spect_subset_angles(const spect_plan* plan, int subset, int* out);
+
+/* Forward projection (Eq. 1): proj = H_m x for each of `batch` volumes.
+ * x: device [batch][nx][ny][nz]; proj: device [batch][|S_m|][ny][nz] with
+ * the subset's angles in ascending order (subset == -1: all angles).
+ * Deterministic: the same inputs give bitwise the same output. */
+int spect_forward(spect_plan* plan, const float* x, float* proj, int subset, int batch, void* stream);
+
+/* Back projection, the exact transpose of spect_forward:
+ * x_out = H_m^T proj, overwriting x_out.  Layouts as in spect_forward. */
+int spect_back(spect_plan* plan, const float* proj, float* x_out, int subset, int batch, void* stream);
+
+/* Copy the plan's sensitivity H_m^T 1 of subset m (m == -1: all angles,
+ * computed on the fly) into out [nx][ny][nz]. */
+int spect_sensitivity(spect_plan* plan, int subset, float* out, void* stream);
+
+/* OSEM (Table 1): run subiterations t = first_subiter .. first_subiter +
+ * n_subiters - 1, subset m = t mod n_subsets, each doing
+ *     p = H_m x;  r = y_m / (p + s)  (0 where p + s == 0);
+ *     x <- x * H_m^T r / H_m^T 1    (x unchanged where H_m^T 1 == 0).
+ * y: device [n_angles][ny][nz] measured counts (all angles);
+ * s: constant additive scatter term; x_inout: device image, updated in place.
+ * diag_dev: NULL or device double[3 * n_subiters] receiving, per subiteration
+ * and before its update, the FP64 sums over the subset's bins of (p + s),
+ * y and y * p / (p + s) (the last equals sum of H_m x_new: count conservation).
+ * Resume by calling again with the next first_subiter. */
+int spect_osem_run(spect_plan* plan, const float* y, float s, float* x_inout, int first_subiter,
+                   int n_subiters, double* diag_dev, void* stream);
+
+/* Poisson log-likelihood (Table 1, PoissonLogLikelihood), FP64 sums:
+ *   ll_dev[0] = sum_b y_b log(p_b + s) - (p_b + s)   (log y! dropped)
+ * over `count` bins, and, if grad_proj is not NULL, its gradient with
+ * respect to p: grad_proj[b] = y_b / (p_b + s) - 1 (0 - 1 where p_b + s == 0).
+ * y, p, grad_proj: device float[count]; ll_dev: device double[1].
+ * The plan (required) supplies the scratch for the block partial sums. */
+int spect_poisson_ll(spect_plan* plan, const float* y, const float* p, float s, size_t count,
+                     double* ll_dev, float* grad_proj, void* stream);
+
+/* ---------------------------------------------------------------- profiling */
+
+/* Accumulated device time of one kernel kind launched through a plan. */
+typedef struct spect_kernel_time {
+    char name[32];            /* "forward", "blur_back", "gather", ... */
+    unsigned long long launches;
+    double total_ms;          /* sum of CUDA-event durations on the launch stream */
+} spect_kernel_time;
+
+/* Turn per-launch CUDA-event timing of this plan's kernels on (1) or off (0).
+ * Events are recorded on the stream each kernel is launched on. */
+int spect_profile_enable(spect_plan* plan, int on);
+
+/* Wait for the recorded events, add them up per kernel kind and copy at
+ * most max_entries rows into out.  Returns the number of rows (>= 0) or a
+ * status.  reset != 0 clears the totals afterwards. */
+int spect_profile_read(spect_plan* plan, spect_kernel_time* out, int max_entries, int reset);
+
+/* Number of kernels libspect has launched in this process (all plans). */
+unsigned long long spect_kernel_launches(void);
+
+/* Human-readable name of a status code. */
+const char* spect_status_str(int status);
+
+/* Thread-local description of the last failure ("" if none). */
+const char* spect_last_error(void);
+
+/* Library version string. */
+const char* spect_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPECT_H */

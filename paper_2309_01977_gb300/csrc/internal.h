@@ -1,0 +1,145 @@
+// Internal declarations shared by the libspect translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "spect.h"
+
+namespace spect {
+
+constexpr int kMaxR = 20;            // largest supported PSF radius (taps 2*kMaxR+1)
+constexpr int kTapW = 2 * kMaxR + 1; // row width of the device taps table
+constexpr int kStrip = 16;           // outputs per thread along one blur strip
+constexpr int kFwdThreads = 512;     // threads of the forward / blur kernels
+constexpr int kGatherTile = 8;       // x,y tile edge of the adjoint-rotation gather
+constexpr int kGatherThreads = 256;
+constexpr int kMaxCand = 9;          // rotated-grid samples that can touch one voxel
+constexpr int kMaxIpt = 3;           // largest j-blur strips per thread
+
+// Shape of one plane-blur launch: which columns of z a CTA owns and the
+// shared-memory layout of its two plane buffers.
+struct PlaneTiling {
+    int ktile;    // output columns per z tile (multiple of 16 unless it is nz)
+    int ntiles;   // z tiles
+    int rh;       // halo = largest PSF radius of the plan
+    int ktpad;    // ktile rounded up to 16
+    int npad;     // n rounded up to 16
+    int wp;       // P row stride (odd): ktpad + 2*rh (+1)
+    int qs;       // Q row stride (odd): ktpad (+1)
+    int ipt;      // j-blur strips per thread (1..kMaxIpt)
+    size_t smem;  // dynamic shared memory bytes
+};
+
+struct ForwardArgs {
+    const float* x;        // [batch][n][n][nz]
+    const float* atten;    // [n_angles][n][n][nz] or nullptr
+    const float2* cs;      // [n_angles] (cos, sin)
+    const float* taps;     // [n][kTapW] centred at kMaxR
+    const int* rad;        // [n]
+    const int* sel;        // [n_sel] angle ids
+    int n, nz, n_sel, batch;
+    int chunks, ppc;       // depth chunks and planes per chunk
+    PlaneTiling t;
+    float* out;            // [batch][n_sel][n][nz]
+    float* partials;       // [batch*n_sel*chunks][n][nz] when chunks > 1
+    unsigned* counters;    // [batch*n_sel*ntiles] when chunks > 1 (zero between launches)
+    const float* y;        // [n_angles][n][nz] -> write the OSEM ratio y/(p+s) instead of p
+    float s;
+    double* diag;          // [batch*n_sel*ntiles][3] FP64 partial sums (ratio mode)
+};
+
+struct BlurBackArgs {
+    const float* proj;     // first projection of the group, or nullptr for all-ones projections
+    size_t proj_bstride;   // elements between batch entries of proj
+    const float* atten;    // [n_angles][n][n][nz] or nullptr
+    const float* taps;
+    const int* rad;
+    const int* sel;        // [n_sel] angle ids
+    int n, nz, n_sel, batch;
+    int chunks, ppc;
+    PlaneTiling t;
+    float* bvol;           // [batch][n_sel][n][n][nz] rotated-frame volumes A . (K_i r)
+};
+
+struct GatherArgs {
+    const float* bvol;     // [batch][n_sel][n][n][nz]
+    const float2* cs;
+    const int* sel;
+    int n, nz, n_sel, batch;
+    int zsplit;            // z ranges per column tile
+    float* out;            // [batch][n][n][nz]
+    int accumulate;        // add into out instead of overwriting
+    const float* sens;     // OSEM update: x <- sens>0 ? x*bp/sens : x (x is `out`)
+};
+
+PlaneTiling plane_tiling(int n, int nz, int rh, size_t smem_cap);
+cudaError_t launch_forward(const ForwardArgs& a, int grid_x, cudaStream_t st);
+cudaError_t launch_blur_back(const BlurBackArgs& a, int grid_x, cudaStream_t st);
+cudaError_t launch_gather(const GatherArgs& a, cudaStream_t st);
+int forward_max_blocks_per_sm(const PlaneTiling& t);
+
+// Per-IPT instantiations (one translation unit each, compiled in parallel).
+template <int IPT> cudaError_t forward_launch_ipt(const ForwardArgs& a, int grid_x, cudaStream_t st);
+template <int IPT> int forward_occupancy_ipt(size_t smem);
+template <int IPT> cudaError_t blur_back_launch_ipt(const BlurBackArgs& a, int grid_x, cudaStream_t st);
+
+// misc kernels
+cudaError_t launch_attenuation(const float* mu, const float2* cs, int n, int nz, int n_angles,
+                               float voxel_cm, int f64, float* atten, cudaStream_t st);
+cudaError_t launch_diag_finalize(const double* part, int n_part, double* out3, cudaStream_t st);
+cudaError_t launch_poisson_ll(const float* y, const float* p, float s, size_t count, double* block_part,
+                              int n_blocks, double* ll, float* grad, cudaStream_t st);
+cudaError_t launch_fill(float* dst, size_t count, float value, cudaStream_t st);
+cudaError_t launch_update(float* x, const float* bp, const float* sens, size_t count, cudaStream_t st);
+
+}  // namespace spect
+
+struct spect_plan {
+    spect_geom geom{};
+    int n = 0, nz = 0, na = 0, M = 1;
+    int rmax = 0;
+    int device = 0, num_sms = 0;
+    std::vector<double> angles;
+    std::vector<std::vector<int>> subsets;  // host angle lists
+    int max_subset = 0;
+    spect::PlaneTiling tiling{};
+    int fwd_occ = 1;         // resident forward CTAs per SM
+
+    // device memory
+    float2* d_cs = nullptr;
+    float* d_taps = nullptr;
+    int* d_rad = nullptr;
+    int* d_sel_all = nullptr;                 // [na] = 0..na-1
+    std::vector<int*> d_sel;                  // per subset
+    float* d_atten = nullptr;                 // [na][vol]
+    float* d_sens = nullptr;                  // [M][vol]
+    float* d_partials = nullptr;              // forward depth-chunk partials
+    size_t partial_planes = 0;
+    unsigned* d_counters = nullptr;
+    size_t n_counters = 0;
+    float* d_bvol = nullptr;                  // back-projection rotated-frame volumes
+    size_t bvol_cap = 0;                      // capacity in volumes
+    float* d_ratio = nullptr;                 // [max_subset][n][nz]
+    float* d_bp = nullptr;                    // one volume: back projection of large subsets
+    double* d_diag_part = nullptr;            // [max_subset*ntiles][3]
+    double* d_ll_part = nullptr;              // poisson block partials
+    size_t device_bytes = 0;
+    size_t atten_bytes = 0;
+    std::vector<void*> allocations;
+
+    // optional per-launch CUDA-event timing (spect_profile_enable)
+    struct ProfRec {
+        const char* name;
+        cudaEvent_t start, stop;
+    };
+    bool prof = false;
+    std::vector<ProfRec> pending;
+    std::vector<cudaEvent_t> event_pool;
+    std::map<std::string, std::pair<unsigned long long, double>> totals;
+};

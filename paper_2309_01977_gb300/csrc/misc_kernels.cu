@@ -1,0 +1,153 @@
+// Attenuation cache, FP64 count reductions and the Poisson likelihood.
+#include <cuda_runtime.h>
+
+#include "geometry.cuh"
+#include "internal.h"
+
+namespace spect {
+
+// T_att of Eq. (1) in the rotated frame of angle a: one thread per detector
+// ray (j, k) walks depth from the detector side (i = n-1) inward,
+//   A[i] = exp(-(sum_{i'>i} tau[i'] + tau[i]/2)),  tau = voxel_cm * bilinear(mu)(u, v, k).
+// The running sum is FP64 (f64 != 0) or Kahan-compensated FP32.
+__global__ void attenuation_kernel(const float* __restrict__ mu, const float2* __restrict__ cs_tab, int n, int nz,
+                                   float voxel_cm, int f64, float* __restrict__ atten)
+{
+    const int angle = blockIdx.y;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * nz) return;
+    const int j = idx / nz, k = idx - j * nz;
+    const float2 cs = cs_tab[angle];
+    const float c = 0.5f * (float)(n - 1);
+    double sum_d = 0.0;
+    float sum = 0.f, comp = 0.f;
+    for (int i = n - 1; i >= 0; --i) {
+        float u, v;
+        sample_point(cs.x, cs.y, c, i, j, u, v);
+        const float fu = floorf(u), fv = floorf(v);
+        const int x0 = (int)fu, y0 = (int)fv;
+        const float ax = u - fu, by = v - fv;
+        float m = 0.f;
+        if (x0 >= 0 && x0 < n && y0 >= 0 && y0 < n) m = fmaf((1.f - ax) * (1.f - by), __ldg(mu + ((size_t)x0 * n + y0) * nz + k), m);
+        if (x0 + 1 >= 0 && x0 + 1 < n && y0 >= 0 && y0 < n) m = fmaf(ax * (1.f - by), __ldg(mu + ((size_t)(x0 + 1) * n + y0) * nz + k), m);
+        if (x0 >= 0 && x0 < n && y0 + 1 >= 0 && y0 + 1 < n) m = fmaf((1.f - ax) * by, __ldg(mu + ((size_t)x0 * n + y0 + 1) * nz + k), m);
+        if (x0 + 1 >= 0 && x0 + 1 < n && y0 + 1 >= 0 && y0 + 1 < n) m = fmaf(ax * by, __ldg(mu + ((size_t)(x0 + 1) * n + y0 + 1) * nz + k), m);
+        const float tau = voxel_cm * m;
+        float a;
+        if (f64) {
+            a = (float)exp(-(sum_d + 0.5 * (double)tau));
+            sum_d += (double)tau;
+        } else {
+            a = expf(-((sum + comp) + 0.5f * tau));
+            // Kahan summation of the optical depth beyond the plane
+            const float yv = tau - comp;
+            const float tv = sum + yv;
+            comp = (tv - sum) - yv;
+            sum = tv;
+        }
+        atten[(((size_t)angle * n + i) * n + j) * nz + k] = a;
+    }
+}
+
+cudaError_t launch_attenuation(const float* mu, const float2* cs, int n, int nz, int n_angles, float voxel_cm, int f64,
+                               float* atten, cudaStream_t st)
+{
+    const int threads = 256;
+    dim3 grid((n * nz + threads - 1) / threads, n_angles);
+    attenuation_kernel<<<grid, threads, 0, st>>>(mu, cs, n, nz, voxel_cm, f64, atten);
+    return cudaGetLastError();
+}
+
+// Sum the per-(angle, tile) FP64 partials of one subiteration in a fixed order.
+__global__ void diag_finalize_kernel(const double* __restrict__ part, int n_part, double* __restrict__ out3)
+{
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int p = 0; p < n_part; ++p) s += part[3 * p + threadIdx.x];
+        out3[threadIdx.x] = s;
+    }
+}
+
+cudaError_t launch_diag_finalize(const double* part, int n_part, double* out3, cudaStream_t st)
+{
+    diag_finalize_kernel<<<1, 32, 0, st>>>(part, n_part, out3);
+    return cudaGetLastError();
+}
+
+// Poisson log-likelihood (Table 1): sum_b y_b log(p_b + s) - (p_b + s), in
+// FP64 per block, plus the gradient with respect to p, y/(p+s) - 1.
+__global__ void poisson_ll_kernel(const float* __restrict__ y, const float* __restrict__ p, float s, size_t count,
+                                  double* __restrict__ block_part, float* __restrict__ grad)
+{
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (size_t b = (size_t)blockIdx.x * blockDim.x + threadIdx.x; b < count; b += (size_t)gridDim.x * blockDim.x) {
+        const float yv = __ldg(y + b);
+        const float lam = __ldg(p + b) + s;
+        double term = -(double)lam;
+        if (yv != 0.f) term += (double)yv * (double)logf(lam);
+        acc += term;
+        if (grad) grad[b] = (lam > 0.f ? yv / lam : 0.f) - 1.f;
+    }
+    const double tot = block_sum_f64(acc, red);
+    if (threadIdx.x == 0) block_part[blockIdx.x] = tot;
+}
+
+__global__ void sum_blocks_kernel(const double* __restrict__ part, int n, double* __restrict__ out)
+{
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < n; ++b) s += part[b];
+        out[0] = s;
+    }
+}
+
+cudaError_t launch_poisson_ll(const float* y, const float* p, float s, size_t count, double* block_part, int n_blocks,
+                              double* ll, float* grad, cudaStream_t st)
+{
+    poisson_ll_kernel<<<n_blocks, 256, 0, st>>>(y, p, s, count, block_part, grad);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sum_blocks_kernel<<<1, 32, 0, st>>>(block_part, n_blocks, ll);
+    return cudaGetLastError();
+}
+
+__global__ void fill_kernel(float* __restrict__ dst, size_t count, float value)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = value;
+}
+
+cudaError_t launch_fill(float* dst, size_t count, float value, cudaStream_t st)
+{
+    size_t blocks = (count + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks == 0) return cudaSuccess;
+    fill_kernel<<<(unsigned)blocks, 256, 0, st>>>(dst, count, value);
+    return cudaGetLastError();
+}
+
+}  // namespace spect
+
+namespace spect {
+
+// OSEM update (Table 1, OSEM row): x <- x * bp / sens where sens > 0.
+__global__ void update_kernel(float* __restrict__ x, const float* __restrict__ bp, const float* __restrict__ sens,
+                              size_t count)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const float sv = sens[i];
+        if (sv > 0.f) x[i] = x[i] * bp[i] / sv;
+    }
+}
+
+cudaError_t launch_update(float* x, const float* bp, const float* sens, size_t count, cudaStream_t st)
+{
+    size_t blocks = (count + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    if (blocks == 0) return cudaSuccess;
+    update_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, bp, sens, count);
+    return cudaGetLastError();
+}
+
+}  // namespace spect

@@ -1,0 +1,643 @@
+// C ABI of libspect: plans, forward/back projection, sensitivity, OSEM and
+// the Poisson likelihood.  Host logic only; the kernels live in
+// proj_kernels.cu and misc_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace spect;
+
+namespace {
+
+thread_local std::string g_last_error;
+std::atomic<unsigned long long> g_launches{0};
+
+cudaEvent_t take_event(spect_plan* p)
+{
+    if (!p->event_pool.empty()) {
+        cudaEvent_t e = p->event_pool.back();
+        p->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Launch `kernels` kernels through `launch`, counting them and, when the
+// plan profiles, bracketing them with CUDA events on the launch stream.
+template <class F>
+cudaError_t timed(spect_plan* p, const char* name, cudaStream_t st, int kernels, F&& launch)
+{
+    cudaEvent_t e0 = nullptr;
+    if (p && p->prof && p->pending.size() < 1000000) {
+        e0 = take_event(p);
+        if (e0) cudaEventRecord(e0, st);
+    }
+    cudaError_t e = launch();
+    if (e == cudaSuccess) g_launches += (unsigned long long)kernels;
+    if (e0) {
+        cudaEvent_t e1 = take_event(p);
+        if (e1) {
+            cudaEventRecord(e1, st);
+            p->pending.push_back({name, e0, e1});
+        } else {
+            p->event_pool.push_back(e0);
+        }
+    }
+    return e;
+}
+
+int fail(int status, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(SPECT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Makes the plan's device current for the duration of a call and restores
+// the caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+int dev_alloc(spect_plan* p, T** out, size_t count)
+{
+    *out = nullptr;
+    if (count == 0) return SPECT_OK;
+    void* ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SPECT_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    }
+    p->allocations.push_back(ptr);
+    p->device_bytes += count * sizeof(T);
+    *out = static_cast<T*>(ptr);
+    return SPECT_OK;
+}
+
+void free_plan(spect_plan* p)
+{
+    if (!p) return;
+    for (auto& r : p->pending) {
+        cudaEventDestroy(r.start);
+        cudaEventDestroy(r.stop);
+    }
+    for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+    for (void* a : p->allocations) cudaFree(a);
+    delete p;
+}
+
+size_t vol_elems(const spect_plan* p) { return (size_t)p->n * p->n * p->nz; }
+size_t plane_elems(const spect_plan* p) { return (size_t)p->n * p->nz; }
+
+// Host PSF table (Eq. 1, T_cdr): sigma_i = sigma0 + slope * (n - i - 0.5 + offset),
+// R_i = ceil(nsigma * sigma_i), taps exp(-t^2 / (2 sigma_i^2)) normalised in FP64.
+void build_psf(const spect_geom& g, int n, bool psf, std::vector<float>& taps, std::vector<int>& rad, int& rmax)
+{
+    taps.assign((size_t)n * kTapW, 0.f);
+    rad.assign(n, 0);
+    rmax = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!psf) {
+            taps[(size_t)i * kTapW + kMaxR] = 1.f;
+            continue;
+        }
+        const double d = (double)n - i - 0.5 + (double)g.det_offset;
+        const double s = (double)g.psf_sigma0 + (double)g.psf_slope * d;
+        const int r = (int)std::ceil((double)g.psf_nsigma * s);
+        rad[i] = r;
+        rmax = std::max(rmax, r);
+        if (r > kMaxR) continue;
+        double w[kTapW];
+        double sum = 0.0;
+        for (int t = -r; t <= r; ++t) {
+            w[t + r] = std::exp(-(double)t * t / (2.0 * s * s));
+            sum += w[t + r];
+        }
+        for (int t = -r; t <= r; ++t) taps[(size_t)i * kTapW + kMaxR + t] = (float)(w[t + r] / sum);
+    }
+}
+
+// ---------------------------------------------------------------- launches
+
+int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, int n_sel, int batch, const float* y,
+                float s, double* diag_part, cudaStream_t st)
+{
+    // The depth split depends on the subset size only (never on the batch),
+    // so a volume projects to bitwise the same values alone or in a batch.
+    const PlaneTiling& t = p->tiling;
+    const long items1 = (long)n_sel * t.ntiles;
+    const long target = (long)p->num_sms * p->fwd_occ;
+    int chunks = 1;
+    if (items1 < target) chunks = (int)std::min<long>(std::max(1, p->n / 4), target / items1);
+    chunks = std::max(chunks, 1);
+    int ppc = (p->n + chunks - 1) / chunks;
+    chunks = (p->n + ppc - 1) / ppc;
+    // Batch entries per launch: the partial planes and arrival counters are
+    // sized for `target` CTAs.
+    int bper = batch;
+    if (chunks > 1) {
+        const long per = std::max<long>(1, std::min<long>((long)p->partial_planes / ((long)n_sel * chunks),
+                                                          (long)p->n_counters / items1));
+        bper = (int)std::min<long>(batch, per);
+    }
+    const size_t vol = vol_elems(p), plane = plane_elems(p);
+    for (int b0 = 0; b0 < batch; b0 += bper) {
+        const int nb = std::min(bper, batch - b0);
+        ForwardArgs a{};
+        a.x = x + (size_t)b0 * vol;
+        a.atten = p->d_atten;
+        a.cs = p->d_cs;
+        a.taps = p->d_taps;
+        a.rad = p->d_rad;
+        a.sel = sel_dev;
+        a.n = p->n;
+        a.nz = p->nz;
+        a.n_sel = n_sel;
+        a.batch = nb;
+        a.chunks = chunks;
+        a.ppc = ppc;
+        a.t = t;
+        a.out = out + (size_t)b0 * n_sel * plane;
+        a.partials = p->d_partials;
+        a.counters = p->d_counters;
+        a.y = y;
+        a.s = s;
+        a.diag = diag_part;
+        cudaError_t e = timed(p, "forward", st, 1, [&] { return launch_forward(a, chunks * t.ntiles, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "forward kernel launch");
+    }
+    return SPECT_OK;
+}
+
+int blur_back_chunks(const spect_plan* p, long items)
+{
+    const long target = (long)p->num_sms * p->fwd_occ;
+    int chunks = 1;
+    if (items < target) chunks = (int)std::min<long>(std::max(1, p->n / 4), target / items);
+    return std::max(chunks, 1);
+}
+
+// x_out (per batch entry) = sum over sel of H_a^T proj_a, optionally fused with
+// the OSEM update x_out <- x_out * bp / sens (then batch must be 1).
+int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev, int n_sel, int batch,
+             const float* sens_update, cudaStream_t st)
+{
+    const size_t vol = vol_elems(p), plane = plane_elems(p);
+    const int gmax = (int)std::min<size_t>(16, p->bvol_cap);
+    const bool fused = sens_update && n_sel <= gmax;
+    // Angle groups of a fixed size (independent of the batch, so that each
+    // volume is summed in the same order alone or in a batch), and as many
+    // batch entries per launch as the rotated-frame buffer holds.
+    const int G = std::min(gmax, n_sel);
+    const int bper = std::max(1, std::min(batch, (int)(p->bvol_cap / G)));
+    for (int b0 = 0; b0 < batch; b0 += bper) {
+        float* out_b = (sens_update && !fused) ? p->d_bp : x_out + (size_t)b0 * vol;
+        const int nb = std::min(bper, batch - b0);
+        for (int g0 = 0; g0 < n_sel; g0 += G) {
+            const int ng = std::min(G, n_sel - g0);
+            BlurBackArgs bb{};
+            bb.proj = proj ? proj + ((size_t)b0 * n_sel + g0) * plane : nullptr;
+            bb.proj_bstride = (size_t)n_sel * plane;
+            bb.atten = p->d_atten;
+            bb.taps = p->d_taps;
+            bb.rad = p->d_rad;
+            bb.sel = sel_dev + g0;
+            bb.n = p->n;
+            bb.nz = p->nz;
+            bb.n_sel = ng;
+            bb.batch = nb;
+            bb.t = p->tiling;
+            int chunks = blur_back_chunks(p, (long)nb * ng * p->tiling.ntiles);
+            int ppc = (p->n + chunks - 1) / chunks;
+            chunks = (p->n + ppc - 1) / ppc;
+            bb.chunks = chunks;
+            bb.ppc = ppc;
+            bb.bvol = p->d_bvol;
+            cudaError_t e = timed(p, "blur_back", st, 1, [&] { return launch_blur_back(bb, chunks * p->tiling.ntiles, st); });
+            if (e != cudaSuccess) return cuda_fail(e, "blur_back kernel launch");
+            GatherArgs ga{};
+            ga.bvol = p->d_bvol;
+            ga.cs = p->d_cs;
+            ga.sel = sel_dev + g0;
+            ga.n = p->n;
+            ga.nz = p->nz;
+            ga.n_sel = ng;
+            ga.batch = nb;
+            const int tiles = (p->n + kGatherTile - 1) / kGatherTile;
+            const long ctas = (long)tiles * tiles * nb;
+            ga.zsplit = (int)std::max<long>(1, std::min<long>(p->nz / 4 / 8, (3L * p->num_sms + ctas - 1) / ctas));
+            ga.out = out_b;
+            ga.accumulate = g0 > 0;
+            ga.sens = fused ? sens_update : nullptr;
+            e = timed(p, ga.sens ? "gather_update" : "gather", st, 1, [&] { return launch_gather(ga, st); });
+            if (e != cudaSuccess) return cuda_fail(e, "gather kernel launch");
+        }
+        if (sens_update && !fused) {
+            cudaError_t e = timed(p, "update", st, 1, [&] { return launch_update(x_out + (size_t)b0 * vol, p->d_bp, sens_update, vol, st); });
+            if (e != cudaSuccess) return cuda_fail(e, "update kernel launch");
+        }
+    }
+    return SPECT_OK;
+}
+
+int check_plan(const spect_plan* p)
+{
+    if (!p) return fail(SPECT_EINVAL, "plan is NULL");
+    return SPECT_OK;
+}
+
+int subset_of(const spect_plan* p, int subset, const int** sel_dev, int* n_sel)
+{
+    if (subset == -1) {
+        *sel_dev = p->d_sel_all;
+        *n_sel = p->na;
+        return SPECT_OK;
+    }
+    if (subset < 0 || subset >= p->M) return fail(SPECT_EINVAL, "subset %d out of range [-1, %d)", subset, p->M);
+    *sel_dev = p->d_sel[subset];
+    *n_sel = (int)p->subsets[subset].size();
+    return SPECT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* spect_version(void) { return "libspect 0.1 (sm_103a)"; }
+
+const char* spect_last_error(void) { return g_last_error.c_str(); }
+
+const char* spect_status_str(int status)
+{
+    switch (status) {
+        case SPECT_OK: return "SPECT_OK";
+        case SPECT_EINVAL: return "SPECT_EINVAL";
+        case SPECT_ENOMEM: return "SPECT_ENOMEM";
+        case SPECT_ECUDA: return "SPECT_ECUDA";
+        case SPECT_EBUDGET: return "SPECT_EBUDGET";
+        case SPECT_ETIMEDOUT: return "SPECT_ETIMEDOUT";
+        case SPECT_ECANCELLED: return "SPECT_ECANCELLED";
+        case SPECT_ESTATE: return "SPECT_ESTATE";
+        case SPECT_ENOTFOUND: return "SPECT_ENOTFOUND";
+        default: return "SPECT_UNKNOWN";
+    }
+}
+
+int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream, spect_plan** out)
+{
+    if (!out) return fail(SPECT_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!geom) return fail(SPECT_EINVAL, "geom is NULL");
+    const spect_geom& g = *geom;
+    if (g.nx != g.ny) return fail(SPECT_EINVAL, "nx (%d) != ny (%d): square transaxial grid required", g.nx, g.ny);
+    if (g.nx < 2 || g.nx > 1024) return fail(SPECT_EINVAL, "nx = %d outside [2, 1024]", g.nx);
+    if (g.nz < 4 || g.nz > 4096 || g.nz % 4 != 0) return fail(SPECT_EINVAL, "nz = %d must be a multiple of 4 in [4, 4096]", g.nz);
+    if (g.n_angles < 1 || g.n_angles > 4096) return fail(SPECT_EINVAL, "n_angles = %d outside [1, 4096]", g.n_angles);
+    if (g.n_subsets < 1 || g.n_subsets > g.n_angles)
+        return fail(SPECT_EINVAL, "n_subsets = %d outside [1, n_angles]", g.n_subsets);
+    const unsigned known = SPECT_FLAG_ATTEN | SPECT_FLAG_PSF | SPECT_FLAG_PSF_BF16 | SPECT_FLAG_ATTEN_F64;
+    if (g.flags & ~known) return fail(SPECT_EINVAL, "unknown flag bits 0x%x", g.flags & ~known);
+    if (g.flags & SPECT_FLAG_PSF_BF16) return fail(SPECT_EINVAL, "SPECT_FLAG_PSF_BF16 is not available in this build");
+    const bool atten = (g.flags & SPECT_FLAG_ATTEN) != 0;
+    const bool psf = (g.flags & SPECT_FLAG_PSF) != 0;
+    if (atten) {
+        if (!mu_dev) return fail(SPECT_EINVAL, "SPECT_FLAG_ATTEN needs a mu map");
+        if (!aligned16(mu_dev)) return fail(SPECT_EINVAL, "mu must be 16-byte aligned");
+        if (!(g.voxel_cm > 0.f) || !std::isfinite(g.voxel_cm)) return fail(SPECT_EINVAL, "voxel_cm must be > 0");
+    }
+    if (psf) {
+        if (!(g.psf_sigma0 > 0.f) || !(g.psf_slope >= 0.f) || !(g.psf_nsigma > 0.f) || !std::isfinite(g.psf_slope) ||
+            !std::isfinite(g.psf_sigma0) || !std::isfinite(g.psf_nsigma) || !std::isfinite(g.det_offset))
+            return fail(SPECT_EINVAL, "PSF needs sigma0 > 0, slope >= 0, nsigma > 0 (finite)");
+        if ((double)g.psf_sigma0 + (double)g.psf_slope * ((double)g.nx - 0.5 + (double)g.det_offset) <= 0.0 ||
+            (double)g.psf_sigma0 + (double)g.psf_slope * (0.5 + (double)g.det_offset) <= 0.0)
+            return fail(SPECT_EINVAL, "PSF sigma must stay positive over depth");
+    }
+
+    spect_plan* p = new (std::nothrow) spect_plan();
+    if (!p) return fail(SPECT_ENOMEM, "host allocation failed");
+    p->geom = g;
+    p->geom.angles_rad = nullptr;
+    p->n = g.nx;
+    p->nz = g.nz;
+    p->na = g.n_angles;
+    p->M = g.n_subsets;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = SPECT_OK;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&p->device)) != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaGetDevice"); }
+    if ((e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device)) != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(e, "cudaDeviceGetAttribute");
+    }
+
+    // angles and their FP32 cos/sin (computed in FP64)
+    p->angles.resize(p->na);
+    std::vector<float2> cs(p->na);
+    for (int a = 0; a < p->na; ++a) {
+        const double th = g.angles_rad ? g.angles_rad[a] : 2.0 * M_PI * (double)a / (double)p->na;
+        if (!std::isfinite(th)) { free_plan(p); return fail(SPECT_EINVAL, "angle %d is not finite", a); }
+        p->angles[a] = th;
+        cs[a] = make_float2((float)std::cos(th), (float)std::sin(th));
+    }
+    std::vector<float> taps;
+    std::vector<int> rad;
+    build_psf(g, p->n, psf, taps, rad, p->rmax);
+    if (p->rmax > kMaxR) {
+        free_plan(p);
+        return fail(SPECT_EINVAL, "PSF radius %d exceeds the supported %d (reduce psf_nsigma or the slope)", p->rmax, kMaxR);
+    }
+    p->subsets.assign(p->M, {});
+    for (int a = 0; a < p->na; ++a) p->subsets[a % p->M].push_back(a);
+    for (auto& s : p->subsets) p->max_subset = std::max(p->max_subset, (int)s.size());
+
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    const size_t cap = (size_t)std::min(smem_optin, 227 * 1024) - 2048;
+    p->tiling = plane_tiling(p->n, p->nz, p->rmax, cap);
+    if (p->tiling.smem == 0) { free_plan(p); return fail(SPECT_EINVAL, "plane %dx%d too large for shared memory", p->n, p->nz); }
+    p->fwd_occ = std::max(1, forward_max_blocks_per_sm(p->tiling));
+
+    const size_t vol = vol_elems(p), plane = plane_elems(p);
+    const size_t target = (size_t)p->num_sms * p->fwd_occ;
+    p->partial_planes = 2 * target;
+    p->n_counters = target;
+    p->bvol_cap = (size_t)std::max(p->max_subset, 16);
+    if ((rc = dev_alloc(p, &p->d_cs, p->na)) ||
+        (rc = dev_alloc(p, &p->d_taps, taps.size())) ||
+        (rc = dev_alloc(p, &p->d_rad, (size_t)p->n)) ||
+        (rc = dev_alloc(p, &p->d_sel_all, (size_t)p->na)) ||
+        (rc = dev_alloc(p, &p->d_sens, (size_t)p->M * vol)) ||
+        (rc = dev_alloc(p, &p->d_partials, p->partial_planes * plane)) ||
+        (rc = dev_alloc(p, &p->d_counters, p->n_counters)) ||
+        (rc = dev_alloc(p, &p->d_bvol, p->bvol_cap * vol)) ||
+        (rc = dev_alloc(p, &p->d_ratio, (size_t)p->max_subset * plane)) ||
+        (rc = dev_alloc(p, &p->d_bp, vol)) ||
+        (rc = dev_alloc(p, &p->d_diag_part, (size_t)p->max_subset * p->tiling.ntiles * 3)) ||
+        (rc = dev_alloc(p, &p->d_ll_part, 1024))) {
+        free_plan(p);
+        return rc;
+    }
+    if (atten) {
+        if ((rc = dev_alloc(p, &p->d_atten, (size_t)p->na * vol))) { free_plan(p); return rc; }
+        p->atten_bytes = (size_t)p->na * vol * sizeof(float);
+    }
+    p->d_sel.assign(p->M, nullptr);
+    for (int m = 0; m < p->M; ++m)
+        if ((rc = dev_alloc(p, &p->d_sel[m], p->subsets[m].size()))) { free_plan(p); return rc; }
+
+    std::vector<int> all(p->na);
+    for (int a = 0; a < p->na; ++a) all[a] = a;
+#define SPECT_CK(call, what)                                   \
+    do {                                                       \
+        cudaError_t _e = (call);                               \
+        if (_e != cudaSuccess) {                               \
+            cudaStreamSynchronize(st);                         \
+            free_plan(p);                                      \
+            return cuda_fail(_e, what);                        \
+        }                                                      \
+    } while (0)
+    SPECT_CK(cudaMemcpyAsync(p->d_cs, cs.data(), cs.size() * sizeof(float2), cudaMemcpyHostToDevice, st), "copy angles");
+    SPECT_CK(cudaMemcpyAsync(p->d_taps, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice, st), "copy taps");
+    SPECT_CK(cudaMemcpyAsync(p->d_rad, rad.data(), rad.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy radii");
+    SPECT_CK(cudaMemcpyAsync(p->d_sel_all, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy angles");
+    for (int m = 0; m < p->M; ++m)
+        SPECT_CK(cudaMemcpyAsync(p->d_sel[m], p->subsets[m].data(), p->subsets[m].size() * sizeof(int),
+                                 cudaMemcpyHostToDevice, st), "copy subsets");
+    SPECT_CK(cudaMemsetAsync(p->d_counters, 0, p->n_counters * sizeof(unsigned), st), "clear counters");
+    if (atten)
+        SPECT_CK(timed(p, "attenuation", st, 1, [&] {
+                     return launch_attenuation(mu_dev, p->d_cs, p->n, p->nz, p->na, g.voxel_cm,
+                                               (g.flags & SPECT_FLAG_ATTEN_F64) ? 1 : 0, p->d_atten, st);
+                 }), "attenuation kernel");
+    // sensitivities H_m^T 1 (compute_normalization_factor)
+    for (int m = 0; m < p->M; ++m) {
+        rc = run_back(p, nullptr, p->d_sens + (size_t)m * vol, p->d_sel[m], (int)p->subsets[m].size(), 1, nullptr, st);
+        if (rc) { cudaStreamSynchronize(st); free_plan(p); return rc; }
+    }
+    SPECT_CK(cudaStreamSynchronize(st), "plan creation");
+    SPECT_CK(cudaGetLastError(), "plan creation");
+#undef SPECT_CK
+    *out = p;
+    return SPECT_OK;
+}
+
+int spect_plan_destroy(spect_plan* plan)
+{
+    if (!plan) return SPECT_OK;
+    DeviceGuard guard(plan->device);
+    free_plan(plan);
+    return SPECT_OK;
+}
+
+int spect_plan_query(const spect_plan* plan, spect_plan_info* info)
+{
+    if (int rc = check_plan(plan)) return rc;
+    if (!info) return fail(SPECT_EINVAL, "info is NULL");
+    info->n = plan->n;
+    info->nz = plan->nz;
+    info->n_angles = plan->na;
+    info->n_subsets = plan->M;
+    info->max_subset_size = plan->max_subset;
+    info->psf_rmax = plan->rmax;
+    info->device_bytes = plan->device_bytes;
+    info->atten_cache_bytes = plan->atten_bytes;
+    return SPECT_OK;
+}
+
+int spect_subset_size(const spect_plan* plan, int subset)
+{
+    if (int rc = check_plan(plan)) return rc;
+    if (subset == -1) return plan->na;
+    if (subset < 0 || subset >= plan->M) return fail(SPECT_EINVAL, "subset %d out of range", subset);
+    return (int)plan->subsets[subset].size();
+}
+
+int spect_subset_angles(const spect_plan* plan, int subset, int* out)
+{
+    if (int rc = check_plan(plan)) return rc;
+    if (!out) return fail(SPECT_EINVAL, "out is NULL");
+    if (subset == -1) {
+        for (int a = 0; a < plan->na; ++a) out[a] = a;
+        return SPECT_OK;
+    }
+    if (subset < 0 || subset >= plan->M) return fail(SPECT_EINVAL, "subset %d out of range", subset);
+    std::copy(plan->subsets[subset].begin(), plan->subsets[subset].end(), out);
+    return SPECT_OK;
+}
+
+int spect_forward(spect_plan* plan, const float* x, float* proj, int subset, int batch, void* stream)
+{
+    if (int rc = check_plan(plan)) return rc;
+    if (!x || !proj) return fail(SPECT_EINVAL, "x and proj must be device pointers");
+    if (!aligned16(x) || !aligned16(proj)) return fail(SPECT_EINVAL, "x and proj must be 16-byte aligned");
+    if (batch < 1 || batch > 65535) return fail(SPECT_EINVAL, "batch = %d outside [1, 65535]", batch);
+    const int* sel;
+    int ns;
+    if (int rc = subset_of(plan, subset, &sel, &ns)) return rc;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
+    return run_forward(plan, x, proj, sel, ns, batch, nullptr, 0.f, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+int spect_back(spect_plan* plan, const float* proj, float* x_out, int subset, int batch, void* stream)
+{
+    if (int rc = check_plan(plan)) return rc;
+    if (!proj || !x_out) return fail(SPECT_EINVAL, "proj and x_out must be device pointers");
+    if (!aligned16(proj) || !aligned16(x_out)) return fail(SPECT_EINVAL, "proj and x_out must be 16-byte aligned");
+    if (batch < 1 || batch > 65535) return fail(SPECT_EINVAL, "batch = %d outside [1, 65535]", batch);
+    const int* sel;
+    int ns;
+    if (int rc = subset_of(plan, subset, &sel, &ns)) return rc;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
+    return run_back(plan, proj, x_out, sel, ns, batch, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+int spect_sensitivity(spect_plan* plan, int subset, float* out, void* stream)
+{
+    if (int rc = check_plan(plan)) return rc;
+    if (!out || !aligned16(out)) return fail(SPECT_EINVAL, "out must be a 16-byte aligned device pointer");
+    const int* sel;
+    int ns;
+    if (int rc = subset_of(plan, subset, &sel, &ns)) return rc;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t vol = vol_elems(plan);
+    if (subset >= 0) {
+        cudaError_t e = cudaMemcpyAsync(out, plan->d_sens + (size_t)subset * vol, vol * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "copy sensitivity");
+        return SPECT_OK;
+    }
+    return run_back(plan, nullptr, out, sel, ns, 1, nullptr, st);
+}
+
+int spect_osem_run(spect_plan* plan, const float* y, float s, float* x_inout, int first_subiter, int n_subiters,
+                   double* diag_dev, void* stream)
+{
+    if (int rc = check_plan(plan)) return rc;
+    if (!y || !x_inout) return fail(SPECT_EINVAL, "y and x_inout must be device pointers");
+    if (!aligned16(y) || !aligned16(x_inout)) return fail(SPECT_EINVAL, "y and x_inout must be 16-byte aligned");
+    if (first_subiter < 0 || n_subiters < 0) return fail(SPECT_EINVAL, "negative subiteration range");
+    if (!std::isfinite(s) || s < 0.f) return fail(SPECT_EINVAL, "s must be finite and >= 0");
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t vol = vol_elems(plan);
+    for (int t = first_subiter; t < first_subiter + n_subiters; ++t) {
+        const int m = t % plan->M;
+        const int ns = (int)plan->subsets[m].size();
+        int rc = run_forward(plan, x_inout, plan->d_ratio, plan->d_sel[m], ns, 1, y, s, plan->d_diag_part, st);
+        if (rc) return rc;
+        if (diag_dev) {
+            cudaError_t e = timed(plan, "diag", st, 1, [&] {
+                return launch_diag_finalize(plan->d_diag_part, ns * plan->tiling.ntiles,
+                                            diag_dev + 3 * (size_t)(t - first_subiter), st);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "diag kernel launch");
+        }
+        rc = run_back(plan, plan->d_ratio, x_inout, plan->d_sel[m], ns, 1, plan->d_sens + (size_t)m * vol, st);
+        if (rc) return rc;
+    }
+    return SPECT_OK;
+}
+
+int spect_poisson_ll(spect_plan* plan, const float* y, const float* p, float s, size_t count, double* ll_dev,
+                     float* grad_proj, void* stream)
+{
+    if (int rc = check_plan(plan)) return rc;
+    if (!y || !p || !ll_dev) return fail(SPECT_EINVAL, "y, p and ll must be device pointers");
+    if (!aligned16(y) || !aligned16(p) || (grad_proj && !aligned16(grad_proj)))
+        return fail(SPECT_EINVAL, "y, p and grad must be 16-byte aligned");
+    if (!std::isfinite(s)) return fail(SPECT_EINVAL, "s must be finite");
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
+    const int blocks = (int)std::max<size_t>(1, std::min<size_t>(1024, (count + 255) / 256));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = timed(plan, "poisson_ll", st, 2, [&] {
+        return launch_poisson_ll(y, p, s, count, plan->d_ll_part, blocks, ll_dev, grad_proj, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "poisson kernel launch");
+    return SPECT_OK;
+}
+
+int spect_profile_enable(spect_plan* plan, int on)
+{
+    if (int rc = check_plan(plan)) return rc;
+    plan->prof = on != 0;
+    return SPECT_OK;
+}
+
+int spect_profile_read(spect_plan* plan, spect_kernel_time* out, int max_entries, int reset)
+{
+    if (int rc = check_plan(plan)) return rc;
+    if (max_entries < 0 || (max_entries > 0 && !out)) return fail(SPECT_EINVAL, "bad output array");
+    DeviceGuard guard(plan->device);
+    for (auto& r : plan->pending) {
+        cudaError_t e = cudaEventSynchronize(r.stop);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.start, r.stop);
+        if (e != cudaSuccess) return cuda_fail(e, "profile events");
+        auto& tot = plan->totals[r.name];
+        tot.first += 1;
+        tot.second += ms;
+        plan->event_pool.push_back(r.start);
+        plan->event_pool.push_back(r.stop);
+    }
+    plan->pending.clear();
+    int n = 0;
+    for (auto& kv : plan->totals) {
+        if (n >= max_entries) break;
+        std::snprintf(out[n].name, sizeof out[n].name, "%s", kv.first.c_str());
+        out[n].launches = kv.second.first;
+        out[n].total_ms = kv.second.second;
+        ++n;
+    }
+    if (reset) plan->totals.clear();
+    return n;
+}
+
+unsigned long long spect_kernel_launches(void) { return g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,331 @@
+"""Thin ctypes binding of libspect (include/spect.h).
+
+Argument marshalling only: every step of the projector and of OSEM runs in
+the library's CUDA kernels.  Tensors must be CUDA float32 (double for the
+diagnostics), contiguous and 16-byte aligned; the binding passes their data
+pointers and the current torch stream.  There is no CPU fallback: a missing
+library raises ``SpectError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspect.so")
+
+SPECT_OK = 0
+SPECT_EINVAL = -1
+SPECT_ENOMEM = -2
+SPECT_ECUDA = -3
+SPECT_EBUDGET = -4
+SPECT_ETIMEDOUT = -5
+SPECT_ECANCELLED = -6
+SPECT_ESTATE = -7
+SPECT_ENOTFOUND = -8
+
+SPECT_FLAG_ATTEN = 1
+SPECT_FLAG_PSF = 2
+SPECT_FLAG_PSF_BF16 = 4
+SPECT_FLAG_ATTEN_F64 = 8
+
+# Every symbol include/spect.h declares (checked by the CPU test suite).
+EXPORTED = [
+    "spect_plan_create", "spect_plan_destroy", "spect_plan_query", "spect_subset_size", "spect_subset_angles",
+    "spect_forward", "spect_back", "spect_sensitivity", "spect_osem_run", "spect_poisson_ll",
+    "spect_status_str", "spect_last_error", "spect_version",
+    "spect_profile_enable", "spect_profile_read", "spect_kernel_launches",
+]
+
+
+class SpectError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(message)
+        self.status = status
+
+
+class _Geom(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("voxel_cm", ctypes.c_float),
+        ("n_angles", ctypes.c_int),
+        ("angles_rad", ctypes.POINTER(ctypes.c_double)),
+        ("psf_sigma0", ctypes.c_float), ("psf_slope", ctypes.c_float),
+        ("psf_nsigma", ctypes.c_float), ("det_offset", ctypes.c_float),
+        ("n_subsets", ctypes.c_int),
+        ("flags", ctypes.c_uint),
+    ]
+
+
+class _KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_ulonglong), ("total_ms", ctypes.c_double)]
+
+
+class _PlanInfo(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int), ("nz", ctypes.c_int), ("n_angles", ctypes.c_int), ("n_subsets", ctypes.c_int),
+        ("max_subset_size", ctypes.c_int), ("psf_rmax", ctypes.c_int),
+        ("device_bytes", ctypes.c_size_t), ("atten_cache_bytes", ctypes.c_size_t),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libspect.so (built by ``paper_2309_01977_gb300.build``); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise SpectError(SPECT_ECUDA, "libspect.so not found at %s: build it with "
+                                          "paper_2309_01977_gb300.build.build()" % path)
+        lib = ctypes.CDLL(path)
+        vp, i, f, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_double
+        lib.spect_plan_create.argtypes = [ctypes.POINTER(_Geom), vp, vp, ctypes.POINTER(vp)]
+        lib.spect_plan_destroy.argtypes = [vp]
+        lib.spect_plan_query.argtypes = [vp, ctypes.POINTER(_PlanInfo)]
+        lib.spect_subset_size.argtypes = [vp, i]
+        lib.spect_subset_angles.argtypes = [vp, i, ctypes.POINTER(ctypes.c_int)]
+        lib.spect_forward.argtypes = [vp, vp, vp, i, i, vp]
+        lib.spect_back.argtypes = [vp, vp, vp, i, i, vp]
+        lib.spect_sensitivity.argtypes = [vp, i, vp, vp]
+        lib.spect_osem_run.argtypes = [vp, vp, f, vp, i, i, vp, vp]
+        lib.spect_poisson_ll.argtypes = [vp, vp, vp, f, ctypes.c_size_t, vp, vp, vp]
+        for name in ("spect_status_str",):
+            getattr(lib, name).restype = ctypes.c_char_p
+            getattr(lib, name).argtypes = [i]
+        lib.spect_last_error.restype = ctypes.c_char_p
+        lib.spect_last_error.argtypes = []
+        lib.spect_version.restype = ctypes.c_char_p
+        lib.spect_version.argtypes = []
+        lib.spect_profile_enable.argtypes = [vp, i]
+        lib.spect_profile_read.argtypes = [vp, ctypes.POINTER(_KernelTime), i, i]
+        lib.spect_kernel_launches.restype = ctypes.c_ulonglong
+        lib.spect_kernel_launches.argtypes = []
+        _lib = lib
+        _ = d
+        return lib
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        lib = load()
+        raise SpectError(rc, "%s: %s" % (lib.spect_status_str(rc).decode(), lib.spect_last_error().decode()))
+    return rc
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _dptr(t: Optional[torch.Tensor], dtype=torch.float32) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise SpectError(SPECT_EINVAL, "expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise SpectError(SPECT_EINVAL, "expected %s, got %s" % (dtype, t.dtype))
+    if not t.is_contiguous():
+        raise SpectError(SPECT_EINVAL, "expected a contiguous tensor")
+    return t.data_ptr()
+
+
+@dataclass
+class Geometry:
+    """Python mirror of ``spect_geom`` (voxel units unless stated)."""
+
+    n: int
+    nz: int
+    n_angles: int
+    n_subsets: int = 1
+    voxel_cm: float = 0.48
+    attenuation: bool = True
+    psf: bool = True
+    psf_sigma0: float = 0.5
+    psf_slope: float = 0.03
+    psf_nsigma: float = 3.0
+    det_offset: float = 0.0
+    atten_f64: bool = False
+    psf_bf16: bool = False
+    angles_rad: Optional[Sequence[float]] = None
+
+    def to_c(self):
+        g = _Geom()
+        g.nx = g.ny = int(self.n)
+        g.nz = int(self.nz)
+        g.voxel_cm = float(self.voxel_cm)
+        g.n_angles = int(self.n_angles)
+        keep = None
+        if self.angles_rad is not None:
+            keep = (ctypes.c_double * len(self.angles_rad))(*[float(a) for a in self.angles_rad])
+            g.angles_rad = ctypes.cast(keep, ctypes.POINTER(ctypes.c_double))
+        g.psf_sigma0 = float(self.psf_sigma0)
+        g.psf_slope = float(self.psf_slope)
+        g.psf_nsigma = float(self.psf_nsigma)
+        g.det_offset = float(self.det_offset)
+        g.n_subsets = int(self.n_subsets)
+        g.flags = ((SPECT_FLAG_ATTEN if self.attenuation else 0) | (SPECT_FLAG_PSF if self.psf else 0)
+                   | (SPECT_FLAG_ATTEN_F64 if self.atten_f64 else 0) | (SPECT_FLAG_PSF_BF16 if self.psf_bf16 else 0))
+        return g, keep
+
+
+# ---------------------------------------------------------------- C-named calls
+
+def spect_plan_create(geom: Geometry, mu: Optional[torch.Tensor] = None, stream=None) -> int:
+    lib = load()
+    g, keep = geom.to_c()
+    out = ctypes.c_void_p()
+    _check(lib.spect_plan_create(ctypes.byref(g), _dptr(mu), _stream(stream), ctypes.byref(out)))
+    del keep
+    return out.value
+
+
+def spect_plan_destroy(plan: int) -> None:
+    _check(load().spect_plan_destroy(plan))
+
+
+def spect_plan_query(plan: int) -> dict:
+    info = _PlanInfo()
+    _check(load().spect_plan_query(plan, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in _PlanInfo._fields_}
+
+
+def spect_subset_size(plan: int, subset: int) -> int:
+    return _check(load().spect_subset_size(plan, subset))
+
+
+def spect_subset_angles(plan: int, subset: int) -> list:
+    n = spect_subset_size(plan, subset)
+    buf = (ctypes.c_int * n)()
+    _check(load().spect_subset_angles(plan, subset, buf))
+    return list(buf)
+
+
+def spect_forward(plan: int, x: torch.Tensor, proj: torch.Tensor, subset: int = -1, batch: int = 1, stream=None):
+    _check(load().spect_forward(plan, _dptr(x), _dptr(proj), subset, batch, _stream(stream)))
+
+
+def spect_back(plan: int, proj: torch.Tensor, x_out: torch.Tensor, subset: int = -1, batch: int = 1, stream=None):
+    _check(load().spect_back(plan, _dptr(proj), _dptr(x_out), subset, batch, _stream(stream)))
+
+
+def spect_sensitivity(plan: int, subset: int, out: torch.Tensor, stream=None):
+    _check(load().spect_sensitivity(plan, subset, _dptr(out), _stream(stream)))
+
+
+def spect_osem_run(plan: int, y: torch.Tensor, s: float, x: torch.Tensor, first_subiter: int, n_subiters: int,
+                   diag: Optional[torch.Tensor] = None, stream=None):
+    _check(load().spect_osem_run(plan, _dptr(y), float(s), _dptr(x), first_subiter, n_subiters,
+                                 _dptr(diag, torch.float64), _stream(stream)))
+
+
+def spect_poisson_ll(plan: int, y: torch.Tensor, p: torch.Tensor, s: float, ll: torch.Tensor,
+                     grad: Optional[torch.Tensor] = None, stream=None):
+    if y.numel() != p.numel() or (grad is not None and grad.numel() != p.numel()):
+        raise SpectError(SPECT_EINVAL, "y, p and grad must have the same size")
+    _check(load().spect_poisson_ll(plan, _dptr(y), _dptr(p), float(s), p.numel(), _dptr(ll, torch.float64),
+                                   _dptr(grad), _stream(stream)))
+
+
+def spect_version() -> str:
+    return load().spect_version().decode()
+
+
+def spect_profile_enable(plan: int, on: bool) -> None:
+    _check(load().spect_profile_enable(plan, int(bool(on))))
+
+
+def spect_profile_read(plan: int, reset: bool = False) -> dict:
+    """{kernel name: (launches, total ms)} from the plan's CUDA-event records (synchronises)."""
+    buf = (_KernelTime * 32)()
+    n = _check(load().spect_profile_read(plan, buf, 32, int(bool(reset))))
+    return {buf[k].name.decode(): (int(buf[k].launches), float(buf[k].total_ms)) for k in range(n)}
+
+
+def spect_kernel_launches() -> int:
+    return int(load().spect_kernel_launches())
+
+
+# ---------------------------------------------------------------- convenience
+
+class Plan:
+    """Owning wrapper of a ``spect_plan``: allocates outputs and frees the plan."""
+
+    def __init__(self, geom: Geometry, mu: Optional[torch.Tensor] = None, stream=None):
+        self.geom = geom
+        if geom.attenuation and mu is None:
+            raise SpectError(SPECT_EINVAL, "attenuation needs a mu map")
+        self.device = (mu.device if mu is not None else torch.device("cuda", torch.cuda.current_device()))
+        self.handle = spect_plan_create(geom, mu.contiguous() if mu is not None else None, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            spect_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        return spect_plan_query(self.handle)
+
+    def subset_angles(self, subset: int) -> list:
+        return spect_subset_angles(self.handle, subset)
+
+    def forward(self, x: torch.Tensor, subset: int = -1, out: Optional[torch.Tensor] = None, stream=None):
+        g = self.geom
+        batch = x.numel() // (g.n * g.n * g.nz)
+        na = spect_subset_size(self.handle, subset)
+        if out is None:
+            out = torch.empty((batch, na, g.n, g.nz) if x.dim() == 4 else (na, g.n, g.nz), device=x.device,
+                              dtype=torch.float32)
+        spect_forward(self.handle, x, out, subset, batch, stream)
+        return out
+
+    def back(self, proj: torch.Tensor, subset: int = -1, out: Optional[torch.Tensor] = None, stream=None):
+        g = self.geom
+        na = spect_subset_size(self.handle, subset)
+        batch = proj.numel() // (na * g.n * g.nz)
+        if out is None:
+            out = torch.empty((batch, g.n, g.n, g.nz) if proj.dim() == 4 else (g.n, g.n, g.nz),
+                              device=proj.device, dtype=torch.float32)
+        spect_back(self.handle, proj, out, subset, batch, stream)
+        return out
+
+    def sensitivity(self, subset: int, stream=None):
+        g = self.geom
+        out = torch.empty((g.n, g.n, g.nz), device=self.device, dtype=torch.float32)
+        spect_sensitivity(self.handle, subset, out, stream)
+        return out
+
+    def osem(self, y: torch.Tensor, s: float, x: torch.Tensor, first: int, count: int, diag: bool = False,
+             stream=None):
+        d = torch.zeros((max(count, 1), 3), device=x.device, dtype=torch.float64) if diag else None
+        spect_osem_run(self.handle, y, s, x, first, count, d, stream)
+        return d
+
+    def poisson_ll(self, y: torch.Tensor, p: torch.Tensor, s: float, grad: bool = False, stream=None):
+        ll = torch.zeros(1, device=p.device, dtype=torch.float64)
+        gr = torch.empty_like(p) if grad else None
+        spect_poisson_ll(self.handle, y, p, s, ll, gr, stream)
+        return ll, gr
+
+
+def uniform_angles(n_angles: int) -> list:
+    return [2.0 * math.pi * a / n_angles for a in range(n_angles)]

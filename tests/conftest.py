@@ -18,3 +18,20 @@ def oracle_mod():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def spect_lib():
+    """The CUDA library, built in-tree if needed (nvcc cross-compiles without a GPU)."""
+    from paper_2309_01977_gb300 import build, spect
+    build.build()
+    spect.load()
+    return spect
+
+
+@pytest.fixture(scope="session")
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda", 0)

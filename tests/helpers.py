@@ -1,0 +1,29 @@
+"""Shared helpers of the GPU parity tests (inputs, oracle geometry, error norms)."""
+import numpy as np
+
+from paper_2309_01977_gb300 import phantom
+
+
+def rel_l2(a, b) -> float:
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def f32(a) -> np.ndarray:
+    """Round to float32 and back, so that the oracle sees exactly the GPU's inputs."""
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def oracle_geom(oracle, g, mu64):
+    """Oracle geometry equal to the library Geometry g (same float32 parameters)."""
+    return oracle.Geom(n=g.n, nz=g.nz, n_angles=g.n_angles, angles=g.angles_rad,
+                       voxel_cm=float(np.float32(g.voxel_cm)), mu=mu64 if g.attenuation else None,
+                       use_psf=g.psf, sigma0=float(np.float32(g.psf_sigma0)),
+                       slope=float(np.float32(g.psf_slope)), nsigma=float(np.float32(g.psf_nsigma)),
+                       det_offset=float(np.float32(g.det_offset)))
+
+
+def phantom_inputs(n, nz, seed):
+    f, mu = phantom.make_phantom(n, nz, seed)
+    return f32(f), f32(mu)

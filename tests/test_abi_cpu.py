@@ -1,0 +1,81 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every
+function include/spect.h declares; host-side validation rejects bad
+geometry before touching the GPU.  No kernel runs here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fname in os.listdir(os.path.join(ROOT, "include")):
+        if not fname.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fname)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][A-Za-z0-9_ ]*[\s*]+(spect_[a-z0-9_]+)\s*\(", text, re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("spect_plan_create", "spect_forward", "spect_back", "spect_osem_run", "spect_sensitivity"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(spect_lib):
+    lib = ctypes.CDLL(spect_lib.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(spect_lib.EXPORTED) <= set(declared_functions())
+
+
+def test_status_strings(spect_lib):
+    lib = spect_lib.load()
+    assert lib.spect_status_str(0) == b"SPECT_OK"
+    assert lib.spect_status_str(-1) == b"SPECT_EINVAL"
+    assert lib.spect_status_str(-5) == b"SPECT_ETIMEDOUT"
+    assert lib.spect_status_str(-99) == b"SPECT_UNKNOWN"
+    assert b"sm_103a" in lib.spect_version()
+
+
+@pytest.mark.parametrize("bad, msg", [
+    (dict(n=16, nz=18), "nz"),
+    (dict(n=1, nz=16), "nx"),
+    (dict(n=16, nz=16, n_angles=0), "n_angles"),
+    (dict(n=16, nz=16, n_subsets=0), "n_subsets"),
+    (dict(n=16, nz=16, n_subsets=40), "n_subsets"),
+    (dict(n=16, nz=16, psf_sigma0=-1.0), "PSF"),
+    (dict(n=16, nz=16, psf_nsigma=0.0), "PSF"),
+])
+def test_geometry_validation(spect_lib, bad, msg):
+    kw = dict(n=16, nz=16, n_angles=12, n_subsets=3, attenuation=False)
+    kw.update(bad)
+    g = spect_lib.Geometry(**kw)
+    with pytest.raises(spect_lib.SpectError) as e:
+        spect_lib.spect_plan_create(g, None, stream=0)
+    assert e.value.status == spect_lib.SPECT_EINVAL
+    assert msg in str(e.value)
+
+
+def test_nonsquare_and_missing_mu_rejected(spect_lib):
+    lib = spect_lib.load()
+    g, _ = spect_lib.Geometry(n=16, nz=16, n_angles=4, attenuation=True).to_c()
+    out = ctypes.c_void_p()
+    assert lib.spect_plan_create(ctypes.byref(g), None, None, ctypes.byref(out)) == spect_lib.SPECT_EINVAL
+    assert b"mu" in lib.spect_last_error()
+    g.ny = 17
+    assert lib.spect_plan_create(ctypes.byref(g), None, None, ctypes.byref(out)) == spect_lib.SPECT_EINVAL
+    assert out.value is None
+
+
+def test_null_plan_rejected(spect_lib):
+    lib = spect_lib.load()
+    assert lib.spect_forward(None, None, None, 0, 1, None) == spect_lib.SPECT_EINVAL
+    assert lib.spect_osem_run(None, None, ctypes.c_float(0.0), None, 0, 1, None, None) == spect_lib.SPECT_EINVAL
+    assert lib.spect_plan_destroy(None) == 0
