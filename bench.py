@@ -335,7 +335,8 @@ def run_libspect(args):
                 "peak_source": peaks["source"], "avg_launch_us": avg_s * 1e6,
                 "algorithmic_bytes_per_launch": nbytes,
                 "kernel_share": {k: round(v[1] / sum(t[1] for t in prof.values()), 4) for k, v in prof.items()},
-                "kernel_avg_us": {k: round(1e3 * v[1] / v[0], 2) for k, v in prof.items()}}
+                "kernel_avg_us": {k: round(1e3 * v[1] / v[0], 2) for k, v in prof.items()},
+                "plane_tiling": {k: plan.info()[k] for k in ("ztile", "n_ztiles", "threads", "smem_bytes")}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -92,6 +92,10 @@ typedef struct spect_plan_info {
     int psf_rmax;             /* largest PSF radius over depth planes */
     size_t device_bytes;      /* device memory owned by the plan */
     size_t atten_cache_bytes; /* part of it that is the per-angle A cache */
+    int ztile;                /* axial columns per CTA of the plane kernels */
+    int n_ztiles;             /* axial tiles per plane */
+    int threads;              /* CTA size of the plane kernels */
+    int smem_bytes;           /* their dynamic shared memory per CTA */
 } spect_plan_info;
 
 /* Create a plan: validates the geometry, builds the angle table, the

@@ -3,5 +3,5 @@
 
 namespace spect {
 template cudaError_t forward_launch_ipt<1>(const ForwardArgs&, int, cudaStream_t);
-template int forward_occupancy_ipt<1>(size_t);
+template int forward_occupancy_ipt<1>(int, size_t);
 }  // namespace spect

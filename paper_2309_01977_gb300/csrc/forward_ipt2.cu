@@ -3,5 +3,5 @@
 
 namespace spect {
 template cudaError_t forward_launch_ipt<2>(const ForwardArgs&, int, cudaStream_t);
-template int forward_occupancy_ipt<2>(size_t);
+template int forward_occupancy_ipt<2>(int, size_t);
 }  // namespace spect

@@ -3,5 +3,5 @@
 
 namespace spect {
 template cudaError_t forward_launch_ipt<3>(const ForwardArgs&, int, cudaStream_t);
-template int forward_occupancy_ipt<3>(size_t);
+template int forward_occupancy_ipt<3>(int, size_t);
 }  // namespace spect

@@ -1,0 +1,7 @@
+// Forward projector kernel, 4 j-blur strip(s) per thread.
+#include "plane_kernels.cuh"
+
+namespace spect {
+template cudaError_t forward_launch_ipt<4>(const ForwardArgs&, int, cudaStream_t);
+template int forward_occupancy_ipt<4>(int, size_t);
+}  // namespace spect

@@ -16,22 +16,21 @@ namespace spect {
 constexpr int kMaxR = 20;            // largest supported PSF radius (taps 2*kMaxR+1)
 constexpr int kTapW = 2 * kMaxR + 1; // row width of the device taps table
 constexpr int kStrip = 16;           // outputs per thread along one blur strip
-constexpr int kFwdThreads = 512;     // threads of the forward / blur kernels
-constexpr int kGatherTile = 8;       // x,y tile edge of the adjoint-rotation gather
-constexpr int kGatherThreads = 256;
+constexpr int kFwdThreads = 512;     // most threads of the forward / blur kernels
 constexpr int kMaxCand = 9;          // rotated-grid samples that can touch one voxel
-constexpr int kMaxIpt = 3;           // largest j-blur strips per thread
+constexpr int kMaxIpt = 4;           // largest j-blur strips per thread
 
 // Shape of one plane-blur launch: which columns of z a CTA owns and the
 // shared-memory layout of its two plane buffers.
 struct PlaneTiling {
-    int ktile;    // output columns per z tile (multiple of 16 unless it is nz)
+    int ktile;    // output columns per z tile (multiple of kStrip unless it is nz)
     int ntiles;   // z tiles
     int rh;       // halo = largest PSF radius of the plan
-    int ktpad;    // ktile rounded up to 16
-    int npad;     // n rounded up to 16
+    int ktpad;    // ktile rounded up to kStrip
+    int npad;     // n rounded up to kStrip
     int wp;       // P row stride (odd): ktpad + 2*rh (+1)
-    int qs;       // Q row stride (odd): ktpad (+1)
+    int qs;       // transposed Q row stride (odd): npad + 2*rh (+1); ktpad rows
+    int threads;  // CTA size (multiple of 32, <= kFwdThreads)
     int ipt;      // j-blur strips per thread (1..kMaxIpt)
     size_t smem;  // dynamic shared memory bytes
 };
@@ -46,12 +45,22 @@ struct ForwardArgs {
     int n, nz, n_sel, batch;
     int chunks, ppc;       // depth chunks and planes per chunk
     PlaneTiling t;
-    float* out;            // [batch][n_sel][n][nz]
-    float* partials;       // [batch*n_sel*chunks][n][nz] when chunks > 1
-    unsigned* counters;    // [batch*n_sel*ntiles] when chunks > 1 (zero between launches)
-    const float* y;        // [n_angles][n][nz] -> write the OSEM ratio y/(p+s) instead of p
+    float* out;            // [batch][n_sel][n][nz] raw depth sums when partials == nullptr
+    float* partials;       // else [batch*n_sel*chunks][n][nz] per-chunk sums
+};
+
+// Sum of the depth-chunk partials in chunk order, and optionally the OSEM
+// ratio r = y / (p + s) with FP64 count sums.
+struct ReduceArgs {
+    const float* partials; // [items*chunks][plane]
+    int chunks;
+    int items, n_sel;      // items = batch * n_sel
+    int plane;             // n * nz (multiple of 4)
+    float* out;            // [items][plane]: p, or r in ratio mode
+    const float* y;        // [n_angles][plane] or nullptr
+    const int* sel;        // angle ids (ratio mode)
     float s;
-    double* diag;          // [batch*n_sel*ntiles][3] FP64 partial sums (ratio mode)
+    double* diag_blocks;   // [gridDim.x][3] or nullptr: sums of (p+s), y, y*p/(p+s)
 };
 
 struct BlurBackArgs {
@@ -69,30 +78,33 @@ struct BlurBackArgs {
 
 struct GatherArgs {
     const float* bvol;     // [batch][n_sel][n][n][nz]
-    const float2* cs;
-    const int* sel;
+    const int2* tab;       // [n_angles][n*n][kMaxCand] (row offset, weight bits)
+    const int* sel;        // [n_sel] angle ids
     int n, nz, n_sel, batch;
-    int zsplit;            // z ranges per column tile
+    int lanes_per_col;     // 32, or the power of two >= nz/4 when nz/4 < 32
     float* out;            // [batch][n][n][nz]
     int accumulate;        // add into out instead of overwriting
     const float* sens;     // OSEM update: x <- sens>0 ? x*bp/sens : x (x is `out`)
 };
 
-PlaneTiling plane_tiling(int n, int nz, int rh, size_t smem_cap);
+PlaneTiling plane_tiling(int n, int nz, int rh, size_t cap1, size_t cap2);
 cudaError_t launch_forward(const ForwardArgs& a, int grid_x, cudaStream_t st);
 cudaError_t launch_blur_back(const BlurBackArgs& a, int grid_x, cudaStream_t st);
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t st);
+cudaError_t launch_gather_tables(const float2* cs, int n, int nz, int n_angles, int2* tab, cudaStream_t st);
 int forward_max_blocks_per_sm(const PlaneTiling& t);
 
 // Per-IPT instantiations (one translation unit each, compiled in parallel).
 template <int IPT> cudaError_t forward_launch_ipt(const ForwardArgs& a, int grid_x, cudaStream_t st);
-template <int IPT> int forward_occupancy_ipt(size_t smem);
+template <int IPT> int forward_occupancy_ipt(int threads, size_t smem);
 template <int IPT> cudaError_t blur_back_launch_ipt(const BlurBackArgs& a, int grid_x, cudaStream_t st);
 
 // misc kernels
 cudaError_t launch_attenuation(const float* mu, const float2* cs, int n, int nz, int n_angles,
                                float voxel_cm, int f64, float* atten, cudaStream_t st);
 cudaError_t launch_diag_finalize(const double* part, int n_part, double* out3, cudaStream_t st);
+cudaError_t launch_forward_reduce(const ReduceArgs& a, int blocks, cudaStream_t st);
+constexpr int kReduceBlocks = 1024;  // largest grid of the reduction kernel
 cudaError_t launch_poisson_ll(const float* y, const float* p, float s, size_t count, double* block_part,
                               int n_blocks, double* ll, float* grad, cudaStream_t st);
 cudaError_t launch_fill(float* dst, size_t count, float value, cudaStream_t st);
@@ -121,13 +133,12 @@ struct spect_plan {
     float* d_sens = nullptr;                  // [M][vol]
     float* d_partials = nullptr;              // forward depth-chunk partials
     size_t partial_planes = 0;
-    unsigned* d_counters = nullptr;
-    size_t n_counters = 0;
+    int2* d_gtab = nullptr;                   // [na][n*n][kMaxCand] adjoint-rotation gather tables
     float* d_bvol = nullptr;                  // back-projection rotated-frame volumes
     size_t bvol_cap = 0;                      // capacity in volumes
     float* d_ratio = nullptr;                 // [max_subset][n][nz]
     float* d_bp = nullptr;                    // one volume: back projection of large subsets
-    double* d_diag_part = nullptr;            // [max_subset*ntiles][3]
+    double* d_diag_part = nullptr;            // [kReduceBlocks][3]
     double* d_ll_part = nullptr;              // poisson block partials
     size_t device_bytes = 0;
     size_t atten_bytes = 0;

@@ -74,6 +74,64 @@ cudaError_t launch_diag_finalize(const double* part, int n_part, double* out3, c
     return cudaGetLastError();
 }
 
+// Sum of the depth-chunk partial projections (chunk order, deterministic)
+// and, with y, the OSEM ratio r = y / (p + s) (0 where p + s == 0) and the
+// FP64 count sums of (p + s), y and y * p / (p + s) per block.
+__global__ void forward_reduce_kernel(ReduceArgs a)
+{
+    __shared__ double red[32];
+    const int plane4 = a.plane >> 2;
+    const size_t total4 = (size_t)a.items * plane4;
+    double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total4; e += (size_t)gridDim.x * blockDim.x) {
+        const int item = (int)(e / plane4);
+        const int off4 = (int)(e - (size_t)item * plane4);
+        const float4* src = reinterpret_cast<const float4*>(a.partials) + (size_t)item * a.chunks * plane4 + off4;
+        float4 p = __ldcg(src);
+        for (int c = 1; c < a.chunks; ++c) {
+            const float4 v = __ldcg(src + (size_t)c * plane4);
+            p.x += v.x;
+            p.y += v.y;
+            p.z += v.z;
+            p.w += v.w;
+        }
+        float4 o = p;
+        if (a.y) {
+            const int angle = a.sel[item % a.n_sel];
+            const float4 yv = __ldg(reinterpret_cast<const float4*>(a.y) + (size_t)angle * plane4 + off4);
+            const float pv[4] = {p.x, p.y, p.z, p.w};
+            const float yy[4] = {yv.x, yv.y, yv.z, yv.w};
+            float rv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float den = pv[q] + a.s;
+                rv[q] = den > 0.f ? yy[q] / den : 0.f;
+                d0 += (double)den;
+                d1 += (double)yy[q];
+                d2 += (double)(rv[q] * pv[q]);
+            }
+            o = make_float4(rv[0], rv[1], rv[2], rv[3]);
+        }
+        reinterpret_cast<float4*>(a.out)[e] = o;
+    }
+    if (a.diag_blocks) {
+        const double s0 = block_sum_f64(d0, red);
+        const double s1 = block_sum_f64(d1, red);
+        const double s2 = block_sum_f64(d2, red);
+        if (threadIdx.x == 0) {
+            a.diag_blocks[3 * blockIdx.x + 0] = s0;
+            a.diag_blocks[3 * blockIdx.x + 1] = s1;
+            a.diag_blocks[3 * blockIdx.x + 2] = s2;
+        }
+    }
+}
+
+cudaError_t launch_forward_reduce(const ReduceArgs& a, int blocks, cudaStream_t st)
+{
+    forward_reduce_kernel<<<blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 // Poisson log-likelihood (Table 1): sum_b y_b log(p_b + s) - (p_b + s), in
 // FP64 per block, plus the gradient with respect to p, y/(p+s) - 1.
 __global__ void poisson_ll_kernel(const float* __restrict__ y, const float* __restrict__ p, float s, size_t count,

@@ -158,28 +158,34 @@ void build_psf(const spect_geom& g, int n, bool psf, std::vector<float>& taps, s
 
 // ---------------------------------------------------------------- launches
 
-int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, int n_sel, int batch, const float* y,
-                float s, double* diag_part, cudaStream_t st)
+int forward_chunks(const spect_plan* p, int n_sel, int* ppc_out)
 {
-    // The depth split depends on the subset size only (never on the batch),
-    // so a volume projects to bitwise the same values alone or in a batch.
-    const PlaneTiling& t = p->tiling;
-    const long items1 = (long)n_sel * t.ntiles;
+    const long items1 = (long)n_sel * p->tiling.ntiles;
     const long target = (long)p->num_sms * p->fwd_occ;
     int chunks = 1;
     if (items1 < target) chunks = (int)std::min<long>(std::max(1, p->n / 4), target / items1);
     chunks = std::max(chunks, 1);
-    int ppc = (p->n + chunks - 1) / chunks;
-    chunks = (p->n + ppc - 1) / ppc;
-    // Batch entries per launch: the partial planes and arrival counters are
-    // sized for `target` CTAs.
-    int bper = batch;
-    if (chunks > 1) {
-        const long per = std::max<long>(1, std::min<long>((long)p->partial_planes / ((long)n_sel * chunks),
-                                                          (long)p->n_counters / items1));
-        bper = (int)std::min<long>(batch, per);
-    }
+    const int ppc = (p->n + chunks - 1) / chunks;
+    *ppc_out = ppc;
+    return (p->n + ppc - 1) / ppc;
+}
+
+// proj (or, with y, the ratio y / (p + s)) = H_sel x.  The depth split
+// depends on the subset size only (never on the batch), so a volume
+// projects to bitwise the same values alone or in a batch.  diag_blocks
+// (ratio mode only) receives per-block FP64 sums; *n_diag their count.
+int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, int n_sel, int batch, const float* y,
+                float s, double* diag_blocks, int* n_diag, cudaStream_t st)
+{
+    const PlaneTiling& t = p->tiling;
+    int ppc = 0;
+    const int chunks = forward_chunks(p, n_sel, &ppc);
+    const bool use_partials = chunks > 1 || y != nullptr;
     const size_t vol = vol_elems(p), plane = plane_elems(p);
+    int bper = batch;
+    if (use_partials)
+        bper = (int)std::max<size_t>(1, std::min<size_t>(batch, p->partial_planes / ((size_t)n_sel * chunks)));
+    if (n_diag) *n_diag = 0;
     for (int b0 = 0; b0 < batch; b0 += bper) {
         const int nb = std::min(bper, batch - b0);
         ForwardArgs a{};
@@ -197,13 +203,26 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
         a.ppc = ppc;
         a.t = t;
         a.out = out + (size_t)b0 * n_sel * plane;
-        a.partials = p->d_partials;
-        a.counters = p->d_counters;
-        a.y = y;
-        a.s = s;
-        a.diag = diag_part;
+        a.partials = use_partials ? p->d_partials : nullptr;
         cudaError_t e = timed(p, "forward", st, 1, [&] { return launch_forward(a, chunks * t.ntiles, st); });
         if (e != cudaSuccess) return cuda_fail(e, "forward kernel launch");
+        if (!use_partials) continue;
+        ReduceArgs r{};
+        r.partials = p->d_partials;
+        r.chunks = chunks;
+        r.items = nb * n_sel;
+        r.n_sel = n_sel;
+        r.plane = (int)plane;
+        r.out = out + (size_t)b0 * n_sel * plane;
+        r.y = y;
+        r.sel = sel_dev;
+        r.s = s;
+        r.diag_blocks = (y && diag_blocks) ? diag_blocks : nullptr;
+        const size_t total4 = (size_t)r.items * plane / 4;
+        const int blocks = (int)std::max<size_t>(1, std::min<size_t>(kReduceBlocks, (total4 + 255) / 256));
+        e = timed(p, "forward_reduce", st, 1, [&] { return launch_forward_reduce(r, blocks, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "reduce kernel launch");
+        if (n_diag) *n_diag = blocks;
     }
     return SPECT_OK;
 }
@@ -256,15 +275,17 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
             if (e != cudaSuccess) return cuda_fail(e, "blur_back kernel launch");
             GatherArgs ga{};
             ga.bvol = p->d_bvol;
-            ga.cs = p->d_cs;
+            ga.tab = p->d_gtab;
             ga.sel = sel_dev + g0;
             ga.n = p->n;
             ga.nz = p->nz;
             ga.n_sel = ng;
             ga.batch = nb;
-            const int tiles = (p->n + kGatherTile - 1) / kGatherTile;
-            const long ctas = (long)tiles * tiles * nb;
-            ga.zsplit = (int)std::max<long>(1, std::min<long>(p->nz / 4 / 8, (3L * p->num_sms + ctas - 1) / ctas));
+            {
+                int l = 1;
+                while (l < p->nz / 4 && l < 32) l <<= 1;
+                ga.lanes_per_col = l;
+            }
             ga.out = out_b;
             ga.accumulate = g0 > 0;
             ga.sens = fused ? sens_update : nullptr;
@@ -332,6 +353,8 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     if (g.nx < 2 || g.nx > 1024) return fail(SPECT_EINVAL, "nx = %d outside [2, 1024]", g.nx);
     if (g.nz < 4 || g.nz > 4096 || g.nz % 4 != 0) return fail(SPECT_EINVAL, "nz = %d must be a multiple of 4 in [4, 4096]", g.nz);
     if (g.n_angles < 1 || g.n_angles > 4096) return fail(SPECT_EINVAL, "n_angles = %d outside [1, 4096]", g.n_angles);
+    if ((long long)g.nx * g.ny * g.nz * 16 >= (1ll << 31))
+        return fail(SPECT_EINVAL, "volume %dx%dx%d too large (element offsets of 16 volumes must fit 31 bits)", g.nx, g.ny, g.nz);
     if (g.n_subsets < 1 || g.n_subsets > g.n_angles)
         return fail(SPECT_EINVAL, "n_subsets = %d outside [1, n_angles]", g.n_subsets);
     const unsigned known = SPECT_FLAG_ATTEN | SPECT_FLAG_PSF | SPECT_FLAG_PSF_BF16 | SPECT_FLAG_ATTEN_F64;
@@ -390,17 +413,19 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     for (int a = 0; a < p->na; ++a) p->subsets[a % p->M].push_back(a);
     for (auto& s : p->subsets) p->max_subset = std::max(p->max_subset, (int)s.size());
 
-    int smem_optin = 0;
+    int smem_optin = 0, smem_sm = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
-    const size_t cap = (size_t)std::min(smem_optin, 227 * 1024) - 2048;
-    p->tiling = plane_tiling(p->n, p->nz, p->rmax, cap);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device);
+    // leave room for the 1 KB the hardware reserves per CTA and static shared memory
+    const size_t cap1 = (size_t)std::min(smem_optin, 227 * 1024) - 2048;
+    const size_t cap2 = (size_t)smem_sm / 2 - 2048;
+    p->tiling = plane_tiling(p->n, p->nz, p->rmax, cap1, cap2);
     if (p->tiling.smem == 0) { free_plan(p); return fail(SPECT_EINVAL, "plane %dx%d too large for shared memory", p->n, p->nz); }
     p->fwd_occ = std::max(1, forward_max_blocks_per_sm(p->tiling));
 
     const size_t vol = vol_elems(p), plane = plane_elems(p);
     const size_t target = (size_t)p->num_sms * p->fwd_occ;
-    p->partial_planes = 2 * target;
-    p->n_counters = target;
+    p->partial_planes = std::max<size_t>(2 * target, (size_t)p->max_subset);
     p->bvol_cap = (size_t)std::max(p->max_subset, 16);
     if ((rc = dev_alloc(p, &p->d_cs, p->na)) ||
         (rc = dev_alloc(p, &p->d_taps, taps.size())) ||
@@ -408,11 +433,11 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
         (rc = dev_alloc(p, &p->d_sel_all, (size_t)p->na)) ||
         (rc = dev_alloc(p, &p->d_sens, (size_t)p->M * vol)) ||
         (rc = dev_alloc(p, &p->d_partials, p->partial_planes * plane)) ||
-        (rc = dev_alloc(p, &p->d_counters, p->n_counters)) ||
+        (rc = dev_alloc(p, &p->d_gtab, (size_t)p->na * p->n * p->n * kMaxCand)) ||
         (rc = dev_alloc(p, &p->d_bvol, p->bvol_cap * vol)) ||
         (rc = dev_alloc(p, &p->d_ratio, (size_t)p->max_subset * plane)) ||
         (rc = dev_alloc(p, &p->d_bp, vol)) ||
-        (rc = dev_alloc(p, &p->d_diag_part, (size_t)p->max_subset * p->tiling.ntiles * 3)) ||
+        (rc = dev_alloc(p, &p->d_diag_part, (size_t)kReduceBlocks * 3)) ||
         (rc = dev_alloc(p, &p->d_ll_part, 1024))) {
         free_plan(p);
         return rc;
@@ -440,10 +465,11 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     SPECT_CK(cudaMemcpyAsync(p->d_taps, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice, st), "copy taps");
     SPECT_CK(cudaMemcpyAsync(p->d_rad, rad.data(), rad.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy radii");
     SPECT_CK(cudaMemcpyAsync(p->d_sel_all, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy angles");
+    SPECT_CK(timed(p, "gather_tables", st, 1, [&] { return launch_gather_tables(p->d_cs, p->n, p->nz, p->na, p->d_gtab, st); }),
+             "gather table kernel");
     for (int m = 0; m < p->M; ++m)
         SPECT_CK(cudaMemcpyAsync(p->d_sel[m], p->subsets[m].data(), p->subsets[m].size() * sizeof(int),
                                  cudaMemcpyHostToDevice, st), "copy subsets");
-    SPECT_CK(cudaMemsetAsync(p->d_counters, 0, p->n_counters * sizeof(unsigned), st), "clear counters");
     if (atten)
         SPECT_CK(timed(p, "attenuation", st, 1, [&] {
                      return launch_attenuation(mu_dev, p->d_cs, p->n, p->nz, p->na, g.voxel_cm,
@@ -481,6 +507,10 @@ int spect_plan_query(const spect_plan* plan, spect_plan_info* info)
     info->psf_rmax = plan->rmax;
     info->device_bytes = plan->device_bytes;
     info->atten_cache_bytes = plan->atten_bytes;
+    info->ztile = plan->tiling.ktile;
+    info->n_ztiles = plan->tiling.ntiles;
+    info->threads = plan->tiling.threads;
+    info->smem_bytes = (int)plan->tiling.smem;
     return SPECT_OK;
 }
 
@@ -516,7 +546,7 @@ int spect_forward(spect_plan* plan, const float* x, float* proj, int subset, int
     if (int rc = subset_of(plan, subset, &sel, &ns)) return rc;
     DeviceGuard guard(plan->device);
     if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
-    return run_forward(plan, x, proj, sel, ns, batch, nullptr, 0.f, nullptr, static_cast<cudaStream_t>(stream));
+    return run_forward(plan, x, proj, sel, ns, batch, nullptr, 0.f, nullptr, nullptr, static_cast<cudaStream_t>(stream));
 }
 
 int spect_back(spect_plan* plan, const float* proj, float* x_out, int subset, int batch, void* stream)
@@ -568,12 +598,13 @@ int spect_osem_run(spect_plan* plan, const float* y, float s, float* x_inout, in
     for (int t = first_subiter; t < first_subiter + n_subiters; ++t) {
         const int m = t % plan->M;
         const int ns = (int)plan->subsets[m].size();
-        int rc = run_forward(plan, x_inout, plan->d_ratio, plan->d_sel[m], ns, 1, y, s, plan->d_diag_part, st);
+        int n_diag = 0;
+        int rc = run_forward(plan, x_inout, plan->d_ratio, plan->d_sel[m], ns, 1, y, s,
+                             diag_dev ? plan->d_diag_part : nullptr, &n_diag, st);
         if (rc) return rc;
         if (diag_dev) {
             cudaError_t e = timed(plan, "diag", st, 1, [&] {
-                return launch_diag_finalize(plan->d_diag_part, ns * plan->tiling.ntiles,
-                                            diag_dev + 3 * (size_t)(t - first_subiter), st);
+                return launch_diag_finalize(plan->d_diag_part, n_diag, diag_dev + 3 * (size_t)(t - first_subiter), st);
             });
             if (e != cudaSuccess) return cuda_fail(e, "diag kernel launch");
         }

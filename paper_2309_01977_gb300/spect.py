@@ -72,6 +72,7 @@ class _PlanInfo(ctypes.Structure):
         ("n", ctypes.c_int), ("nz", ctypes.c_int), ("n_angles", ctypes.c_int), ("n_subsets", ctypes.c_int),
         ("max_subset_size", ctypes.c_int), ("psf_rmax", ctypes.c_int),
         ("device_bytes", ctypes.c_size_t), ("atten_cache_bytes", ctypes.c_size_t),
+        ("ztile", ctypes.c_int), ("n_ztiles", ctypes.c_int), ("threads", ctypes.c_int), ("smem_bytes", ctypes.c_int),
     ]
 
 
