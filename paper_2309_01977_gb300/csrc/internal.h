@@ -20,6 +20,7 @@ constexpr int kFwdThreads = 512;     // most threads of the forward / blur kerne
 constexpr int kMaxCand = 9;          // rotated-grid samples that can touch one voxel
 constexpr int kMaxIpt = 4;           // largest j-blur strips per thread
 
+
 // Shape of one plane-blur launch: which columns of z a CTA owns and the
 // shared-memory layout of its two plane buffers.
 struct PlaneTiling {
@@ -43,7 +44,7 @@ struct ForwardArgs {
     const int* rad;        // [n]
     const int* sel;        // [n_sel] angle ids
     int n, nz, n_sel, batch;
-    int chunks, ppc;       // depth chunks and planes per chunk
+    int chunks;            // depth chunks: chunk c takes planes c, c + chunks, ...
     PlaneTiling t;
     float* out;            // [batch][n_sel][n][nz] raw depth sums when partials == nullptr
     float* partials;       // else [batch*n_sel*chunks][n][nz] per-chunk sums
@@ -71,7 +72,7 @@ struct BlurBackArgs {
     const int* rad;
     const int* sel;        // [n_sel] angle ids
     int n, nz, n_sel, batch;
-    int chunks, ppc;
+    int chunks;            // depth chunks: chunk c takes planes c, c + chunks, ...
     PlaneTiling t;
     float* bvol;           // [batch][n_sel][n][n][nz] rotated-frame volumes A . (K_i r)
 };
@@ -119,6 +120,7 @@ struct spect_plan {
     int device = 0, num_sms = 0;
     std::vector<double> angles;
     std::vector<std::vector<int>> subsets;  // host angle lists
+    std::vector<int> rad;                   // host PSF radius per depth plane
     int max_subset = 0;
     spect::PlaneTiling tiling{};
     int fwd_occ = 1;         // resident forward CTAs per SM

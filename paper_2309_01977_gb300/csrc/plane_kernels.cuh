@@ -270,8 +270,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1) forward_kernel(ForwardArgs a)
         for (int r = 0; r < kStrip; ++r) acc[q][r] = 0.f;
 
     const float* xb = a.x + (size_t)b * n * n * nz;
-    const int i0 = chunk * a.ppc, i1 = min(n, i0 + a.ppc);
-    for (int i = i0; i < i1; ++i) {
+    // planes chunk, chunk + chunks, ...: every chunk mixes planes near and
+    // far from the detector, whose blur widths differ several-fold
+    for (int i = chunk; i < n; i += a.chunks) {
         // ---- stage the rotated, attenuated plane (T_rot, T_att)
         const float* arow = a.atten ? a.atten + ((size_t)angle * n + i) * n * nz : nullptr;
         tap_rows(rows, n, nz, i, cs, c);
@@ -384,8 +385,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1) blur_back_kernel(BlurBackArgs 
     __syncthreads();
     float* bvol = a.bvol + item * (size_t)n * n * nz;
     const ZItem z0 = z_item(t, n, tid);
-    const int i0 = chunk * a.ppc, i1 = min(n, i0 + a.ppc);
-    for (int i = i0; i < i1; ++i) {
+    // planes chunk, chunk + chunks, ...: every chunk mixes planes near and
+    // far from the detector, whose blur widths differ several-fold
+    for (int i = chunk; i < n; i += a.chunks) {
         switch (__ldg(a.rad + i)) {
 #define SPECT_BACK_CASE(RR) \
     case RR: back_blur_plane<RR, IPT>(P, Q, t, a, z0, i, angle, kt0, KT, bvol); break;

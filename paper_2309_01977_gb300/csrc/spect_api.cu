@@ -158,16 +158,11 @@ void build_psf(const spect_geom& g, int n, bool psf, std::vector<float>& taps, s
 
 // ---------------------------------------------------------------- launches
 
-int forward_chunks(const spect_plan* p, int n_sel, int* ppc_out)
+int chunk_target(const spect_plan* p, long items)
 {
-    const long items1 = (long)n_sel * p->tiling.ntiles;
     const long target = (long)p->num_sms * p->fwd_occ;
-    int chunks = 1;
-    if (items1 < target) chunks = (int)std::min<long>(std::max(1, p->n / 4), target / items1);
-    chunks = std::max(chunks, 1);
-    const int ppc = (p->n + chunks - 1) / chunks;
-    *ppc_out = ppc;
-    return (p->n + ppc - 1) / ppc;
+    if (items >= target) return 1;
+    return (int)std::max<long>(1, std::min<long>(std::max(1, p->n / 2), target / items));
 }
 
 // proj (or, with y, the ratio y / (p + s)) = H_sel x.  The depth split
@@ -178,8 +173,7 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
                 float s, double* diag_blocks, int* n_diag, cudaStream_t st)
 {
     const PlaneTiling& t = p->tiling;
-    int ppc = 0;
-    const int chunks = forward_chunks(p, n_sel, &ppc);
+    const int chunks = chunk_target(p, (long)n_sel * t.ntiles);
     const bool use_partials = chunks > 1 || y != nullptr;
     const size_t vol = vol_elems(p), plane = plane_elems(p);
     int bper = batch;
@@ -200,7 +194,6 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
         a.n_sel = n_sel;
         a.batch = nb;
         a.chunks = chunks;
-        a.ppc = ppc;
         a.t = t;
         a.out = out + (size_t)b0 * n_sel * plane;
         a.partials = use_partials ? p->d_partials : nullptr;
@@ -225,14 +218,6 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
         if (n_diag) *n_diag = blocks;
     }
     return SPECT_OK;
-}
-
-int blur_back_chunks(const spect_plan* p, long items)
-{
-    const long target = (long)p->num_sms * p->fwd_occ;
-    int chunks = 1;
-    if (items < target) chunks = (int)std::min<long>(std::max(1, p->n / 4), target / items);
-    return std::max(chunks, 1);
 }
 
 // x_out (per batch entry) = sum over sel of H_a^T proj_a, optionally fused with
@@ -265,11 +250,8 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
             bb.n_sel = ng;
             bb.batch = nb;
             bb.t = p->tiling;
-            int chunks = blur_back_chunks(p, (long)nb * ng * p->tiling.ntiles);
-            int ppc = (p->n + chunks - 1) / chunks;
-            chunks = (p->n + ppc - 1) / ppc;
+            const int chunks = chunk_target(p, (long)nb * ng * p->tiling.ntiles);
             bb.chunks = chunks;
-            bb.ppc = ppc;
             bb.bvol = p->d_bvol;
             cudaError_t e = timed(p, "blur_back", st, 1, [&] { return launch_blur_back(bb, chunks * p->tiling.ntiles, st); });
             if (e != cudaSuccess) return cuda_fail(e, "blur_back kernel launch");
@@ -405,6 +387,7 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     std::vector<float> taps;
     std::vector<int> rad;
     build_psf(g, p->n, psf, taps, rad, p->rmax);
+    p->rad = rad;
     if (p->rmax > kMaxR) {
         free_plan(p);
         return fail(SPECT_EINVAL, "PSF radius %d exceeds the supported %d (reduce psf_nsigma or the slope)", p->rmax, kMaxR);
