@@ -154,6 +154,32 @@ int spect_osem_run(spect_plan* plan, const float* y, float s, float* x_inout, in
 int spect_poisson_ll(spect_plan* plan, const float* y, const float* p, float s, size_t count,
                      double* ll_dev, float* grad_proj, void* stream);
 
+/* Poisson log-likelihood and its gradient, like spect_poisson_ll, for
+ * callers that cannot allocate device memory.  The paper has no
+ * counterpart; this is a deployment convenience.
+ *
+ * Who needs it: code that runs where cudaMalloc is unavailable or not
+ * allowed -- a host framework that has reserved all device memory for its
+ * own pool allocator, or a real-time loop that must not pay the latency of
+ * an allocation or risk it failing.  spect_poisson_ll needs a plan, and a
+ * plan allocates; this call needs none.
+ *
+ * Scratch: the per-block partial sums live in a fixed 128 KiB array built
+ * into the library, so it covers at most 67,108,864 bins (count beyond that
+ * returns SPECT_EINVAL and launches nothing).  Every GPU that loads the
+ * library holds that array until the process exits.  The first call on a
+ * device looks up the array's device address (with that device current);
+ * make that first call before any stream capture.  The call itself makes no
+ * allocation of any kind.  All calls on a device share the array: calls that
+ * overlap on the GPU (different streams without ordering) race and give
+ * wrong sums; calls ordered on one stream are safe.  Each call overwrites
+ * every partial it reads, so nothing has to be cleared between calls.
+ *
+ * y, p, grad_proj: device float[count]; ll_dev: device double[1];
+ * grad_proj may be NULL.  Asynchronous on `stream`. */
+int spect_poisson_ll_noalloc(const float* y, const float* p, float s, size_t count, double* ll_dev,
+                             float* grad_proj, void* stream);
+
 /* ---------------------------------------------------------------- profiling */
 
 /* Accumulated device time of one kernel kind launched through a plan. */

@@ -19,7 +19,8 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libspect.so")
 SOURCES = ["spect_api.cu", "plane_host.cu", "gather_kernel.cu", "misc_kernels.cu",
            "forward_ipt1.cu", "forward_ipt2.cu", "forward_ipt3.cu", "forward_ipt4.cu",
-           "blur_back_ipt1.cu", "blur_back_ipt2.cu", "blur_back_ipt3.cu", "blur_back_ipt4.cu"]
+           "blur_back_ipt1.cu", "blur_back_ipt2.cu", "blur_back_ipt3.cu", "blur_back_ipt4.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

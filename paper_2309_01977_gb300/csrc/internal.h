@@ -113,6 +113,9 @@ cudaError_t launch_update(float* x, const float* bp, const float* sens, size_t c
 
 }  // namespace spect
 
+// Sets the thread-local message returned by spect_last_error().
+void spect_internal_set_error(const char* msg);
+
 struct spect_plan {
     spect_geom geom{};
     int n = 0, nz = 0, na = 0, M = 1;

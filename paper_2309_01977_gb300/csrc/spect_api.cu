@@ -18,8 +18,13 @@
 using namespace spect;
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
+
+void spect_internal_set_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
+namespace {
+
 std::atomic<unsigned long long> g_launches{0};
 
 cudaEvent_t take_event(spect_plan* p)

@@ -41,6 +41,7 @@ EXPORTED = [
     "spect_forward", "spect_back", "spect_sensitivity", "spect_osem_run", "spect_poisson_ll",
     "spect_status_str", "spect_last_error", "spect_version",
     "spect_profile_enable", "spect_profile_read", "spect_kernel_launches",
+    "spect_poisson_ll_noalloc",
 ]
 
 
@@ -101,6 +102,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.spect_sensitivity.argtypes = [vp, i, vp, vp]
         lib.spect_osem_run.argtypes = [vp, vp, f, vp, i, i, vp, vp]
         lib.spect_poisson_ll.argtypes = [vp, vp, vp, f, ctypes.c_size_t, vp, vp, vp]
+        lib.spect_poisson_ll_noalloc.argtypes = [vp, vp, f, ctypes.c_size_t, vp, vp, vp]
         for name in ("spect_status_str",):
             getattr(lib, name).restype = ctypes.c_char_p
             getattr(lib, name).argtypes = [i]
@@ -239,6 +241,17 @@ def spect_poisson_ll(plan: int, y: torch.Tensor, p: torch.Tensor, s: float, ll: 
         raise SpectError(SPECT_EINVAL, "y, p and grad must have the same size")
     _check(load().spect_poisson_ll(plan, _dptr(y), _dptr(p), float(s), p.numel(), _dptr(ll, torch.float64),
                                    _dptr(grad), _stream(stream)))
+
+
+def spect_poisson_ll_noalloc(y: torch.Tensor, p: torch.Tensor, s: float, ll: torch.Tensor,
+                             grad: Optional[torch.Tensor] = None, stream=None):
+    """Poisson log-likelihood without a plan, for callers that cannot allocate
+    device memory: the library's built-in scratch holds the partial sums (up to
+    67,108,864 bins); calls on one device must not overlap on the GPU."""
+    if y.numel() != p.numel() or (grad is not None and grad.numel() != p.numel()):
+        raise SpectError(SPECT_EINVAL, "y, p and grad must have the same size")
+    _check(load().spect_poisson_ll_noalloc(_dptr(y), _dptr(p), float(s), p.numel(), _dptr(ll, torch.float64),
+                                           _dptr(grad), _stream(stream)))
 
 
 def spect_version() -> str:
