@@ -7,7 +7,7 @@ generators work on machines without the compiled library.
 """
 import importlib
 
-__all__ = ["phantom", "spect"]
+__all__ = ["autograd", "phantom", "spect"]
 
 
 def __getattr__(name):
