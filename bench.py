@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--workload", default="osem128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--psf", default="fp32", choices=["fp32", "bf16"],
+                    help="bf16: PSF as BF16 tensor-core GEMMs, FP64 attenuation sums")
     return ap.parse_args()
 
 
@@ -244,8 +246,10 @@ def run_libspect(args):
     wl = phantom.WORKLOADS[args.workload]
     f_raw, mu = make_inputs_host(wl)
     n_sub = wl.n_iters * wl.n_subsets
+    bf16 = args.psf == "bf16"
     g = spect.Geometry(n=wl.n, nz=wl.nz, n_angles=wl.n_angles, n_subsets=wl.n_subsets, voxel_cm=wl.voxel_cm,
-                       psf_sigma0=wl.sigma0, psf_slope=wl.slope, psf_nsigma=wl.nsigma)
+                       psf_sigma0=wl.sigma0, psf_slope=wl.slope, psf_nsigma=wl.nsigma,
+                       psf_bf16=bf16, atten_f64=bf16)
     plan = spect.Plan(g, torch.from_numpy(mu).to(dev))
     # measured data: y ~ Poisson(H f_true + s), H from the library itself
     hf = plan.forward(torch.from_numpy(f_raw).to(dev)).double().cpu().numpy()
@@ -350,7 +354,8 @@ def run_libspect(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 PSF, f32" if bf16 else "f32", "data": "synthetic",
+            "config": cfg,
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": int(launches),
             "clocks": clk,
         }

@@ -67,7 +67,9 @@ extern "C" {
 /* ---------------------------------------------------------------- geometry */
 #define SPECT_FLAG_ATTEN 1u      /* model attenuation (needs mu at plan creation) */
 #define SPECT_FLAG_PSF 2u        /* model the depth-dependent collimator blur */
-#define SPECT_FLAG_PSF_BF16 4u   /* PSF as banded-Toeplitz BF16 tensor-core GEMMs */
+#define SPECT_FLAG_PSF_BF16 4u   /* PSF as banded-Toeplitz BF16 tensor-core GEMMs (FP32
+                                    accumulate; needs nx % 32 == 0, nx <= 128,
+                                    nz % 8 == 0, nz <= 128) */
 #define SPECT_FLAG_ATTEN_F64 8u  /* attenuation prefix sums in FP64 (else compensated FP32) */
 
 typedef struct spect_geom {
@@ -111,6 +113,10 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
 int spect_plan_destroy(spect_plan* plan);
 
 int spect_plan_query(const spect_plan* plan, spect_plan_info* info);
+
+/* Wait for the device and report whether any kernel of this plan gave up a
+ * bounded wait (SPECT_ETIMEDOUT; the flag is then cleared).  Synchronous. */
+int spect_plan_check(spect_plan* plan);
 
 /* Number of angles of subset m (m == -1: all angles). */
 int spect_subset_size(const spect_plan* plan, int subset);

@@ -88,6 +88,40 @@ struct GatherArgs {
     const float* sens;     // OSEM update: x <- sens>0 ? x*bp/sens : x (x is `out`)
 };
 
+// Tensor-core PSF path (SPECT_FLAG_PSF_BF16): n % 32 == 0, n <= 128,
+// nz % 8 == 0, nz <= 128; per-plane Toeplitz tiles ttab[i][hi|lo][128*128]
+// (BF16 bits, K-major core-matrix layout).
+struct ForwardBf16Args {
+    const float* x;
+    const float* atten;
+    const float2* cs;
+    const uint16_t* ttab;
+    const int* sel;
+    int n, nz, n_sel, batch, chunks;
+    uint32_t tmem_cols;
+    float* out;            // raw depth sums when partials == nullptr
+    float* partials;       // else [batch*n_sel*chunks][n][nz]
+    int* err;              // SPECT_ETIMEDOUT when a bounded wait runs out
+};
+
+struct BlurBackBf16Args {
+    const float* proj;
+    size_t proj_bstride;
+    const float* atten;
+    const uint16_t* ttab;
+    const int* sel;
+    int n, nz, n_sel, batch, chunks;
+    uint32_t tmem_cols;
+    float* bvol;
+    int* err;
+};
+
+cudaError_t launch_forward_bf16(const ForwardBf16Args& a, cudaStream_t st);
+cudaError_t launch_blur_back_bf16(const BlurBackBf16Args& a, cudaStream_t st);
+size_t bf16_smem_bytes(int n);
+uint32_t bf16_tmem_cols(int n);
+int bf16_occupancy(int n);
+
 PlaneTiling plane_tiling(int n, int nz, int rh, size_t cap1, size_t cap2);
 cudaError_t launch_forward(const ForwardArgs& a, int grid_x, cudaStream_t st);
 cudaError_t launch_blur_back(const BlurBackArgs& a, int grid_x, cudaStream_t st);
@@ -139,6 +173,9 @@ struct spect_plan {
     float* d_partials = nullptr;              // forward depth-chunk partials
     size_t partial_planes = 0;
     int2* d_gtab = nullptr;                   // [na][n*n][kMaxCand] adjoint-rotation gather tables
+    bool bf16 = false;                        // tensor-core PSF path
+    uint16_t* d_ttab = nullptr;               // [n][2][128*128] BF16 Toeplitz tiles (hi, lo)
+    int* d_err = nullptr;                     // kernel status word (bounded waits)
     float* d_bvol = nullptr;                  // back-projection rotated-frame volumes
     size_t bvol_cap = 0;                      // capacity in volumes
     float* d_ratio = nullptr;                 // [max_subset][n][nz]

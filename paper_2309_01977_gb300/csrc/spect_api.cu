@@ -131,6 +131,53 @@ void free_plan(spect_plan* p)
 }
 
 size_t vol_elems(const spect_plan* p) { return (size_t)p->n * p->n * p->nz; }
+
+// Round-to-nearest-even FP32 -> BF16 bits (finite inputs).
+uint16_t bf16_bits(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+float bf16_value(uint16_t h)
+{
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// Per-plane banded Toeplitz tiles T_i[r][c] = w_i(r - c) (|r - c| <= R_i) of
+// the tensor-core PSF path, as BF16 hi and lo parts (w = hi + lo to ~2^-17),
+// in the K-major no-swizzle core-matrix layout of a 128 x 128 tile:
+// element (r, c) at ((r/8)*16 + c/8)*64 + (r%8)*8 + c%8.
+void build_toeplitz_bf16(const spect_geom& g, int n, std::vector<uint16_t>& out)
+{
+    const int T = 128;
+    out.assign((size_t)n * 2 * T * T, 0);
+    for (int i = 0; i < n; ++i) {
+        const double d = (double)n - i - 0.5 + (double)g.det_offset;
+        const double s = (double)g.psf_sigma0 + (double)g.psf_slope * d;
+        const int r = (int)std::ceil((double)g.psf_nsigma * s);
+        std::vector<double> w(2 * r + 1);
+        double sum = 0.0;
+        for (int t = -r; t <= r; ++t) sum += (w[t + r] = std::exp(-(double)t * t / (2.0 * s * s)));
+        for (double& v : w) v /= sum;
+        uint16_t* hi = out.data() + (size_t)i * 2 * T * T;
+        uint16_t* lo = hi + (size_t)T * T;
+        for (int row = 0; row < T; ++row)
+            for (int col = std::max(0, row - r); col <= std::min(T - 1, row + r); ++col) {
+                const double wv = w[row - col + r];
+                const uint16_t h = bf16_bits((float)wv);
+                const uint16_t l = bf16_bits((float)(wv - (double)bf16_value(h)));
+                const size_t e = ((size_t)((row >> 3) * (T >> 3) + (col >> 3)) << 6) + ((row & 7) << 3) + (col & 7);
+                hi[e] = h;
+                lo[e] = l;
+            }
+    }
+}
 size_t plane_elems(const spect_plan* p) { return (size_t)p->n * p->nz; }
 
 // Host PSF table (Eq. 1, T_cdr): sigma_i = sigma0 + slope * (n - i - 0.5 + offset),
@@ -178,7 +225,7 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
                 float s, double* diag_blocks, int* n_diag, cudaStream_t st)
 {
     const PlaneTiling& t = p->tiling;
-    const int chunks = chunk_target(p, (long)n_sel * t.ntiles);
+    const int chunks = chunk_target(p, (long)n_sel * (p->bf16 ? 1 : t.ntiles));
     const bool use_partials = chunks > 1 || y != nullptr;
     const size_t vol = vol_elems(p), plane = plane_elems(p);
     int bper = batch;
@@ -187,22 +234,42 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
     if (n_diag) *n_diag = 0;
     for (int b0 = 0; b0 < batch; b0 += bper) {
         const int nb = std::min(bper, batch - b0);
-        ForwardArgs a{};
-        a.x = x + (size_t)b0 * vol;
-        a.atten = p->d_atten;
-        a.cs = p->d_cs;
-        a.taps = p->d_taps;
-        a.rad = p->d_rad;
-        a.sel = sel_dev;
-        a.n = p->n;
-        a.nz = p->nz;
-        a.n_sel = n_sel;
-        a.batch = nb;
-        a.chunks = chunks;
-        a.t = t;
-        a.out = out + (size_t)b0 * n_sel * plane;
-        a.partials = use_partials ? p->d_partials : nullptr;
-        cudaError_t e = timed(p, "forward", st, 1, [&] { return launch_forward(a, chunks * t.ntiles, st); });
+        cudaError_t e;
+        if (p->bf16) {
+            ForwardBf16Args a{};
+            a.x = x + (size_t)b0 * vol;
+            a.atten = p->d_atten;
+            a.cs = p->d_cs;
+            a.ttab = p->d_ttab;
+            a.sel = sel_dev;
+            a.n = p->n;
+            a.nz = p->nz;
+            a.n_sel = n_sel;
+            a.batch = nb;
+            a.chunks = chunks;
+            a.tmem_cols = bf16_tmem_cols(p->n);
+            a.out = out + (size_t)b0 * n_sel * plane;
+            a.partials = use_partials ? p->d_partials : nullptr;
+            a.err = p->d_err;
+            e = timed(p, "forward_bf16", st, 1, [&] { return launch_forward_bf16(a, st); });
+        } else {
+            ForwardArgs a{};
+            a.x = x + (size_t)b0 * vol;
+            a.atten = p->d_atten;
+            a.cs = p->d_cs;
+            a.taps = p->d_taps;
+            a.rad = p->d_rad;
+            a.sel = sel_dev;
+            a.n = p->n;
+            a.nz = p->nz;
+            a.n_sel = n_sel;
+            a.batch = nb;
+            a.chunks = chunks;
+            a.t = t;
+            a.out = out + (size_t)b0 * n_sel * plane;
+            a.partials = use_partials ? p->d_partials : nullptr;
+            e = timed(p, "forward", st, 1, [&] { return launch_forward(a, chunks * t.ntiles, st); });
+        }
         if (e != cudaSuccess) return cuda_fail(e, "forward kernel launch");
         if (!use_partials) continue;
         ReduceArgs r{};
@@ -243,22 +310,41 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
         const int nb = std::min(bper, batch - b0);
         for (int g0 = 0; g0 < n_sel; g0 += G) {
             const int ng = std::min(G, n_sel - g0);
-            BlurBackArgs bb{};
-            bb.proj = proj ? proj + ((size_t)b0 * n_sel + g0) * plane : nullptr;
-            bb.proj_bstride = (size_t)n_sel * plane;
-            bb.atten = p->d_atten;
-            bb.taps = p->d_taps;
-            bb.rad = p->d_rad;
-            bb.sel = sel_dev + g0;
-            bb.n = p->n;
-            bb.nz = p->nz;
-            bb.n_sel = ng;
-            bb.batch = nb;
-            bb.t = p->tiling;
-            const int chunks = chunk_target(p, (long)nb * ng * p->tiling.ntiles);
-            bb.chunks = chunks;
-            bb.bvol = p->d_bvol;
-            cudaError_t e = timed(p, "blur_back", st, 1, [&] { return launch_blur_back(bb, chunks * p->tiling.ntiles, st); });
+            cudaError_t e;
+            if (p->bf16) {
+                BlurBackBf16Args bb{};
+                bb.proj = proj ? proj + ((size_t)b0 * n_sel + g0) * plane : nullptr;
+                bb.proj_bstride = (size_t)n_sel * plane;
+                bb.atten = p->d_atten;
+                bb.ttab = p->d_ttab;
+                bb.sel = sel_dev + g0;
+                bb.n = p->n;
+                bb.nz = p->nz;
+                bb.n_sel = ng;
+                bb.batch = nb;
+                bb.chunks = chunk_target(p, (long)nb * ng);
+                bb.tmem_cols = bf16_tmem_cols(p->n);
+                bb.bvol = p->d_bvol;
+                bb.err = p->d_err;
+                e = timed(p, "blur_back_bf16", st, 1, [&] { return launch_blur_back_bf16(bb, st); });
+            } else {
+                BlurBackArgs bb{};
+                bb.proj = proj ? proj + ((size_t)b0 * n_sel + g0) * plane : nullptr;
+                bb.proj_bstride = (size_t)n_sel * plane;
+                bb.atten = p->d_atten;
+                bb.taps = p->d_taps;
+                bb.rad = p->d_rad;
+                bb.sel = sel_dev + g0;
+                bb.n = p->n;
+                bb.nz = p->nz;
+                bb.n_sel = ng;
+                bb.batch = nb;
+                bb.t = p->tiling;
+                const int chunks = chunk_target(p, (long)nb * ng * p->tiling.ntiles);
+                bb.chunks = chunks;
+                bb.bvol = p->d_bvol;
+                e = timed(p, "blur_back", st, 1, [&] { return launch_blur_back(bb, chunks * p->tiling.ntiles, st); });
+            }
             if (e != cudaSuccess) return cuda_fail(e, "blur_back kernel launch");
             GatherArgs ga{};
             ga.bvol = p->d_bvol;
@@ -346,7 +432,12 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
         return fail(SPECT_EINVAL, "n_subsets = %d outside [1, n_angles]", g.n_subsets);
     const unsigned known = SPECT_FLAG_ATTEN | SPECT_FLAG_PSF | SPECT_FLAG_PSF_BF16 | SPECT_FLAG_ATTEN_F64;
     if (g.flags & ~known) return fail(SPECT_EINVAL, "unknown flag bits 0x%x", g.flags & ~known);
-    if (g.flags & SPECT_FLAG_PSF_BF16) return fail(SPECT_EINVAL, "SPECT_FLAG_PSF_BF16 is not available in this build");
+    if (g.flags & SPECT_FLAG_PSF_BF16) {
+        if (!(g.flags & SPECT_FLAG_PSF)) return fail(SPECT_EINVAL, "SPECT_FLAG_PSF_BF16 needs SPECT_FLAG_PSF");
+        if (g.nx % 32 != 0 || g.nx > 128 || g.nz % 8 != 0 || g.nz > 128)
+            return fail(SPECT_EINVAL, "the BF16 tensor-core PSF needs nx %% 32 == 0, nx <= 128, nz %% 8 == 0, nz <= 128 "
+                                      "(got %d x %d)", g.nx, g.nz);
+    }
     const bool atten = (g.flags & SPECT_FLAG_ATTEN) != 0;
     const bool psf = (g.flags & SPECT_FLAG_PSF) != 0;
     if (atten) {
@@ -409,7 +500,8 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     const size_t cap2 = (size_t)smem_sm / 2 - 2048;
     p->tiling = plane_tiling(p->n, p->nz, p->rmax, cap1, cap2);
     if (p->tiling.smem == 0) { free_plan(p); return fail(SPECT_EINVAL, "plane %dx%d too large for shared memory", p->n, p->nz); }
-    p->fwd_occ = std::max(1, forward_max_blocks_per_sm(p->tiling));
+    p->bf16 = (g.flags & SPECT_FLAG_PSF_BF16) != 0;
+    p->fwd_occ = p->bf16 ? bf16_occupancy(p->n) : std::max(1, forward_max_blocks_per_sm(p->tiling));
 
     const size_t vol = vol_elems(p), plane = plane_elems(p);
     const size_t target = (size_t)p->num_sms * p->fwd_occ;
@@ -426,7 +518,8 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
         (rc = dev_alloc(p, &p->d_ratio, (size_t)p->max_subset * plane)) ||
         (rc = dev_alloc(p, &p->d_bp, vol)) ||
         (rc = dev_alloc(p, &p->d_diag_part, (size_t)kReduceBlocks * 3)) ||
-        (rc = dev_alloc(p, &p->d_ll_part, 1024))) {
+        (rc = dev_alloc(p, &p->d_ll_part, 1024)) ||
+        (rc = dev_alloc(p, &p->d_err, 1))) {
         free_plan(p);
         return rc;
     }
@@ -449,7 +542,16 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
             return cuda_fail(_e, what);                        \
         }                                                      \
     } while (0)
+    std::vector<uint16_t> ttab;
+    if (p->bf16) {
+        build_toeplitz_bf16(g, p->n, ttab);
+        if ((rc = dev_alloc(p, &p->d_ttab, ttab.size()))) { free_plan(p); return rc; }
+    }
     SPECT_CK(cudaMemcpyAsync(p->d_cs, cs.data(), cs.size() * sizeof(float2), cudaMemcpyHostToDevice, st), "copy angles");
+    SPECT_CK(cudaMemsetAsync(p->d_err, 0, sizeof(int), st), "clear status");
+    if (p->bf16)
+        SPECT_CK(cudaMemcpyAsync(p->d_ttab, ttab.data(), ttab.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st),
+                 "copy Toeplitz tiles");
     SPECT_CK(cudaMemcpyAsync(p->d_taps, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice, st), "copy taps");
     SPECT_CK(cudaMemcpyAsync(p->d_rad, rad.data(), rad.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy radii");
     SPECT_CK(cudaMemcpyAsync(p->d_sel_all, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy angles");
@@ -618,6 +720,20 @@ int spect_poisson_ll(spect_plan* plan, const float* y, const float* p, float s, 
         return launch_poisson_ll(y, p, s, count, plan->d_ll_part, blocks, ll_dev, grad_proj, st);
     });
     if (e != cudaSuccess) return cuda_fail(e, "poisson kernel launch");
+    return SPECT_OK;
+}
+
+int spect_plan_check(spect_plan* plan)
+{
+    if (int rc = check_plan(plan)) return rc;
+    DeviceGuard guard(plan->device);
+    int err = 0;
+    cudaError_t e = cudaMemcpy(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read kernel status");
+    if (err != 0) {
+        cudaMemset(plan->d_err, 0, sizeof(int));
+        return fail(err, "a kernel of this plan gave up a bounded wait (%s)", spect_status_str(err));
+    }
     return SPECT_OK;
 }
 

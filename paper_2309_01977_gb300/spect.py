@@ -41,7 +41,7 @@ EXPORTED = [
     "spect_forward", "spect_back", "spect_sensitivity", "spect_osem_run", "spect_poisson_ll",
     "spect_status_str", "spect_last_error", "spect_version",
     "spect_profile_enable", "spect_profile_read", "spect_kernel_launches",
-    "spect_poisson_ll_noalloc",
+    "spect_poisson_ll_noalloc", "spect_plan_check",
 ]
 
 
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.spect_plan_create.argtypes = [ctypes.POINTER(_Geom), vp, vp, ctypes.POINTER(vp)]
         lib.spect_plan_destroy.argtypes = [vp]
         lib.spect_plan_query.argtypes = [vp, ctypes.POINTER(_PlanInfo)]
+        lib.spect_plan_check.argtypes = [vp]
         lib.spect_subset_size.argtypes = [vp, i]
         lib.spect_subset_angles.argtypes = [vp, i, ctypes.POINTER(ctypes.c_int)]
         lib.spect_forward.argtypes = [vp, vp, vp, i, i, vp]
@@ -200,6 +201,11 @@ def spect_plan_destroy(plan: int) -> None:
     _check(load().spect_plan_destroy(plan))
 
 
+def spect_plan_check(plan: int) -> None:
+    """Raise if a kernel of the plan gave up a bounded wait (synchronises)."""
+    _check(load().spect_plan_check(plan))
+
+
 def spect_plan_query(plan: int) -> dict:
     info = _PlanInfo()
     _check(load().spect_plan_query(plan, ctypes.byref(info)))
@@ -298,6 +304,9 @@ class Plan:
 
     def info(self) -> dict:
         return spect_plan_query(self.handle)
+
+    def check(self) -> None:
+        spect_plan_check(self.handle)
 
     def subset_angles(self, subset: int) -> list:
         return spect_subset_angles(self.handle, subset)
