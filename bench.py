@@ -145,9 +145,9 @@ def algorithmic_bytes(kernel: str, wl, n_sel: int) -> float:
     """
     n3 = float(wl.n) * wl.n * wl.nz
     n2 = float(wl.n) * wl.nz
-    if kernel == "forward":
+    if kernel in ("forward", "forward_bf16"):
         return n_sel * (2 * n3 + n2) * 4
-    if kernel == "blur_back":
+    if kernel in ("blur_back", "blur_back_bf16"):
         return n_sel * (n3 + n2) * 4
     if kernel in ("gather_update", "gather"):
         return (n_sel * n3 + 3 * n3) * 4

@@ -15,10 +15,10 @@
 // Rotation, attenuation, the ratio and the update stay FP32 on the CUDA
 // cores.
 //
-// Shared-memory operands use the no-swizzle K-major core-matrix layout: 8x8
-// BF16 core matrices of 128 contiguous bytes, K-adjacent core matrices 128 B
-// apart (leading byte offset), 8-row groups (K/8)*128 B apart (stride byte
-// offset).  The per-plane Toeplitz pair (64 KB) arrives by one TMA bulk copy.
+// Shared-memory operands are K-major tiles with the 128-byte swizzle (see
+// sw_off), so that both the staging (lanes along z) and the TMEM read-back
+// (lanes along the tile rows) store without bank conflicts.  The per-plane
+// Toeplitz pair (64 KB) arrives by one TMA bulk copy.
 //
 // Every wait on an mbarrier is bounded: when the bound runs out the kernel
 // records SPECT_ETIMEDOUT in the plan's error word, releases its tensor
@@ -34,7 +34,7 @@ namespace spect {
 
 namespace {
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;                 // 16 warps: 4 TMEM lane quadrants x 4 column parts
 constexpr int kTcM = 128;                       // MMA M = axial size padded to 128
 constexpr int kTile = kTcM * kTcM * 2;          // one 128x128 BF16 tile, bytes
 constexpr long long kWaitCycles = 4000000000LL; // bounded mbarrier waits (~2 s)
@@ -44,23 +44,34 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p)
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Byte offset of element (r, k) of a K-major tile with K columns.
-__device__ __forceinline__ uint32_t cm_off(int r, int k, int K)
+// K-major operand tiles with the 128-byte swizzle: rows of 64 BF16 (128 B);
+// 8 rows form a 1 KB atom in which 16-byte chunk c of row r is stored at
+// chunk c ^ (r % 8); K beyond 64 continues in the next K block, R rows * 128 B
+// further.  Tiles start on 1 KB boundaries.  Byte offset of element (r, k):
+__device__ __forceinline__ uint32_t sw_off(int r, int k, int R)
 {
-    return (uint32_t)((((r >> 3) * (K >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+    const int kb = k >> 6, kk = k & 63;
+    return (uint32_t)(kb * R * 128 + ((r >> 3) << 10) + ((r & 7) << 7) + ((((kk >> 3) ^ (r & 7))) << 4) +
+                      ((kk & 7) << 1));
 }
 
-// Shared-memory matrix descriptor: no swizzle, K-major, LBO = 128 B,
-// SBO = (K/8) * 128 B, descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, int K)
+// Shared-memory matrix descriptor of such a tile: start address, stride
+// between 8-row groups (SBO) 1024 B, leading offset unused for swizzled
+// K-major tiles, descriptor version 1, layout SWIZZLE_128B.
+__device__ __forceinline__ uint64_t sw_desc(uint32_t addr)
 {
-    const uint64_t lbo = 128, sbo = (uint64_t)(K >> 3) * 128;
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-    d |= (uint64_t)(lbo >> 4) << 16;
-    d |= (uint64_t)(sbo >> 4) << 32;
+    uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
     d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
     return d;
+}
+
+// Start address of K step ks (16 elements) of a tile with R rows.
+__device__ __forceinline__ uint32_t sw_kstep(uint32_t tile, int ks, int R)
+{
+    return tile + (uint32_t)((ks >> 2) * R * 128 + (ks & 3) * 32);
 }
 
 // Instruction descriptor of kind::f16: D F32, A and B BF16, both K-major.
@@ -158,7 +169,7 @@ __device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uin
 }
 
 // GEMM 1: D1 = T_hi B_hi^T + T_lo B_hi^T + T_hi B_lo^T over K = 128.
-__device__ __forceinline__ void issue_gemm1(const TcSmem& s, uint32_t d1, uint32_t idesc)
+__device__ __forceinline__ void issue_gemm1(const TcSmem& s, uint32_t d1, uint32_t idesc, int n)
 {
     tc_fence_after();
     for (int h = 0; h < 3; ++h) {
@@ -166,7 +177,7 @@ __device__ __forceinline__ void issue_gemm1(const TcSmem& s, uint32_t d1, uint32
         const uint32_t tb = s.b1 + (h == 2 ? s.b1_lo : 0);
 #pragma unroll
         for (int ks = 0; ks < kTcM / 16; ++ks)
-            tc_mma(d1, smem_desc(ta + ks * 256, kTcM), smem_desc(tb + ks * 256, kTcM), idesc, (h | ks) != 0);
+            tc_mma(d1, sw_desc(sw_kstep(ta, ks, kTcM)), sw_desc(sw_kstep(tb, ks, n)), idesc, (h | ks) != 0);
     }
     tc_commit(s.bar_1);
 }
@@ -179,32 +190,37 @@ __device__ __forceinline__ void issue_gemm2(const TcSmem& s, uint32_t d2, uint32
         const uint32_t ta = s.a2 + (h == 2 ? s.a2_lo : 0);
         const uint32_t tb = s.tap + (h == 1 ? kTile : 0);
         for (int ks = 0; ks < n / 16; ++ks)
-            tc_mma(d2, smem_desc(ta + ks * 256, n), smem_desc(tb + ks * 256, kTcM), idesc,
+            tc_mma(d2, sw_desc(sw_kstep(ta, ks, kTcM)), sw_desc(sw_kstep(tb, ks, kTcM)), idesc,
                    (accumulate || h || ks) ? 1u : 0u);
     }
     tc_commit(s.bar_2);
 }
 
-// D1 (TMEM, lanes k, columns j) -> BF16 -> A2 (K-major [k][j], K = n).
-// Warp w reads lanes 32*(w%4).. and the column half w/4.
+// D1 (TMEM, lanes k, columns j) -> BF16 hi/lo -> A2 (K-major [k][j], K = n).
+// Warp w reads TMEM lanes 32*(w%4).. (its lane quadrant) and the 16-column
+// chunks c with c/16 = w/4 (mod 4).
 __device__ __forceinline__ void d1_to_a2(const TcSmem& s, uint32_t d1, int n)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = 32 * (warp & 3) + lane;
-    const int half = n / 2;  // n % 32 == 0 for this path
-    const int c0 = (warp >> 2) * half;
-    for (int c = c0; c < c0 + half; c += 16) {
+    for (int c = 16 * (warp >> 2); c < n; c += 64) {
         float v[16];
         tc_ld16(d1 + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c, v);
         uint32_t h[8], l[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) split_bf16x2(v[2 * q], v[2 * q + 1], h[q], l[q]);
-        const uint32_t o0 = s.a2 + cm_off(k, c, n), o1 = s.a2 + cm_off(k, c + 8, n);
+        const uint32_t o0 = s.a2 + sw_off(k, c, kTcM), o1 = s.a2 + sw_off(k, c + 8, kTcM);
         st_shared_v4(o0, h[0], h[1], h[2], h[3]);
         st_shared_v4(o1, h[4], h[5], h[6], h[7]);
         st_shared_v4(o0 + s.a2_lo, l[0], l[1], l[2], l[3]);
         st_shared_v4(o1 + s.a2_lo, l[4], l[5], l[6], l[7]);
     }
+}
+
+// Byte offset of the barriers after the operand tiles.
+__host__ __device__ constexpr int bf16_tail_offset(int n)
+{
+    return 2 * kTile + 2 * n * kTcM * 2 + 2 * kTcM * ((n + 63) / 64 * 64) * 2;
 }
 
 struct TcState {
@@ -215,12 +231,14 @@ struct TcState {
 
 __device__ __forceinline__ bool tc_setup(TcState& st, unsigned char* smem, int n, uint32_t ncols)
 {
+    // tiles: T_hi, T_lo (128 x 128); B1 hi, lo (n x 128); A2 hi, lo (128 x K
+    // with K = n rounded up to whole 64-column swizzle blocks); all 1 KB aligned
     st.s.tap = smem_u32(smem);
     st.s.b1 = st.s.tap + 2 * kTile;
     st.s.b1_lo = n * kTcM * 2;
-    st.s.a2 = st.s.b1 + 2 * n * kTcM * 2;
-    st.s.a2_lo = n * kTcM * 2;
-    unsigned char* tail = smem + 2 * kTile + 4 * n * kTcM * 2;
+    st.s.a2 = st.s.b1 + 2 * st.s.b1_lo;
+    st.s.a2_lo = kTcM * ((n + 63) / 64 * 64) * 2;
+    unsigned char* tail = smem + bf16_tail_offset(n);
     uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
     st.tmem_slot = reinterpret_cast<uint32_t*>(tail + 32);
     st.s.bar_t = smem_u32(bars + 0);
@@ -301,66 +319,74 @@ __device__ __forceinline__ void fma4(float4& acc, float w, const float4& v)
     acc.w = fmaf(w, v.w, acc.w);
 }
 
-// B1[j][k'] = A[j][k'] * bilinear(f)[j][k'] for k' < nz, 0 for k' >= nz, as
-// BF16 hi and lo parts: one task = (row j, 8 consecutive k'), rows fastest
-// across lanes.
+__device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t b)
+{
+    asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+}
+
+// Four values as BF16 hi and lo parts into row j, columns 4l..4l+3, of B1.
+__device__ __forceinline__ void put4(uint32_t b1, uint32_t b1_lo, int j, int k, int n, float4 v)
+{
+    uint32_t h0, l0, h1, l1;
+    split_bf16x2(v.x, v.y, h0, l0);
+    split_bf16x2(v.z, v.w, h1, l1);
+    const uint32_t o = b1 + sw_off(j, k, n);
+    st_shared_v2(o, h0, h1);
+    st_shared_v2(o + b1_lo, l0, l1);
+}
+
+// B1[j][k] = A[j][k] * bilinear(f)[j][k] for k < nz, 0 for nz <= k < 128, as
+// BF16 hi and lo parts.  A warp stages whole rows, lane l covering k = 4l..4l+3
+// with 128-bit loads (one 512-byte row per load instruction), two rows at a
+// time.
 __device__ __forceinline__ void tc_stage_plane(uint32_t b1, uint32_t b1_lo, const TcTapRow* rows,
                                                const float* __restrict__ xb, const float* __restrict__ arow, int n,
                                                int nz)
 {
-    const int tasks = n * (kTcM / 8);
-    for (int t = threadIdx.x; t < tasks; t += blockDim.x) {
-        const int j = t % n, kc = (t / n) * 8;
-        uint32_t h[4] = {0u, 0u, 0u, 0u}, l[4] = {0u, 0u, 0u, 0u};
-        if (kc < nz) {
-            const TcTapRow tr = rows[j];
-            float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int k = 4 * lane;
+    const bool in = k < nz;
+    for (int j0 = warp; j0 < n; j0 += 2 * nw) {
+        const int j1 = j0 + nw;
+        const bool has1 = j1 < n;
+        const TcTapRow t0 = rows[j0];
+        const TcTapRow t1 = rows[has1 ? j1 : j0];
+        float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+        if (in) {
+            float4 f0[4], f1[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4* src = reinterpret_cast<const float4*>(xb + tr.off[q] + kc);
-                fma4(lo, tr.w[q], __ldg(src));
-                fma4(hi, tr.w[q], __ldg(src + 1));
+                f0[q] = __ldg(reinterpret_cast<const float4*>(xb + t0.off[q] + k));
+                f1[q] = __ldg(reinterpret_cast<const float4*>(xb + t1.off[q] + k));
             }
+            float4 a0 = make_float4(1.f, 1.f, 1.f, 1.f), a1 = a0;
             if (arow) {
-                const float4* ap = reinterpret_cast<const float4*>(arow + (size_t)j * nz + kc);
-                const float4 a0 = __ldg(ap), a1 = __ldg(ap + 1);
-                lo.x *= a0.x; lo.y *= a0.y; lo.z *= a0.z; lo.w *= a0.w;
-                hi.x *= a1.x; hi.y *= a1.y; hi.z *= a1.z; hi.w *= a1.w;
+                a0 = __ldg(reinterpret_cast<const float4*>(arow + (size_t)j0 * nz + k));
+                a1 = __ldg(reinterpret_cast<const float4*>(arow + (size_t)(has1 ? j1 : j0) * nz + k));
             }
-            split_bf16x2(lo.x, lo.y, h[0], l[0]);
-            split_bf16x2(lo.z, lo.w, h[1], l[1]);
-            split_bf16x2(hi.x, hi.y, h[2], l[2]);
-            split_bf16x2(hi.z, hi.w, h[3], l[3]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                fma4(v0, t0.w[q], f0[q]);
+                fma4(v1, t1.w[q], f1[q]);
+            }
+            v0.x *= a0.x; v0.y *= a0.y; v0.z *= a0.z; v0.w *= a0.w;
+            v1.x *= a1.x; v1.y *= a1.y; v1.z *= a1.z; v1.w *= a1.w;
         }
-        const uint32_t o = b1 + cm_off(j, kc, kTcM);
-        st_shared_v4(o, h[0], h[1], h[2], h[3]);
-        st_shared_v4(o + b1_lo, l[0], l[1], l[2], l[3]);
+        put4(b1, b1_lo, j0, k, n, v0);
+        if (has1) put4(b1, b1_lo, j1, k, n, v1);
     }
 }
 
-// B1[j][k'] = proj[j][k'] (all ones when proj is NULL) for k' < nz, as BF16
-// hi and lo parts.
+// B1[j][k] = proj[j][k] (all ones when proj is NULL) for k < nz, as BF16 hi
+// and lo parts; lanes along k as above.
 __device__ __forceinline__ void tc_stage_proj(uint32_t b1, uint32_t b1_lo, const float* __restrict__ pr, int n, int nz)
 {
-    const int tasks = n * (kTcM / 8);
-    for (int t = threadIdx.x; t < tasks; t += blockDim.x) {
-        const int j = t % n, kc = (t / n) * 8;
-        uint32_t h[4] = {0u, 0u, 0u, 0u}, l[4] = {0u, 0u, 0u, 0u};
-        if (kc < nz) {
-            float4 lo = make_float4(1.f, 1.f, 1.f, 1.f), hi = lo;
-            if (pr) {
-                const float4* src = reinterpret_cast<const float4*>(pr + (size_t)j * nz + kc);
-                lo = __ldg(src);
-                hi = __ldg(src + 1);
-            }
-            split_bf16x2(lo.x, lo.y, h[0], l[0]);
-            split_bf16x2(lo.z, lo.w, h[1], l[1]);
-            split_bf16x2(hi.x, hi.y, h[2], l[2]);
-            split_bf16x2(hi.z, hi.w, h[3], l[3]);
-        }
-        const uint32_t o = b1 + cm_off(j, kc, kTcM);
-        st_shared_v4(o, h[0], h[1], h[2], h[3]);
-        st_shared_v4(o + b1_lo, l[0], l[1], l[2], l[3]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int k = 4 * lane;
+    for (int j = warp; j < n; j += nw) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < nz) v = pr ? __ldg(reinterpret_cast<const float4*>(pr + (size_t)j * nz + k)) : make_float4(1.f, 1.f, 1.f, 1.f);
+        put4(b1, b1_lo, j, k, n, v);
     }
 }
 
@@ -381,25 +407,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
     const uint32_t ncols = a.tmem_cols;
     TcState st;
     tc_setup(st, tsm, n, ncols);
-    TcTapRow* rows = reinterpret_cast<TcTapRow*>(tsm + 2 * kTile + 4 * n * kTcM * 2 + 64);
+    TcTapRow* rows = reinterpret_cast<TcTapRow*>(tsm + bf16_tail_offset(n) + 64);
     const uint32_t d1 = st.tmem, d2 = st.tmem + (uint32_t)n;
     const uint32_t idesc = idesc_bf16(kTcM, n);
     const float* xb = a.x + (size_t)b * n * n * nz;
-    uint32_t phase = 0;
+    const size_t item = (size_t)b * a.n_sel + sidx;
+    float* dst = a.partials ? a.partials + (item * a.chunks + chunk) * (size_t)n * nz : a.out + item * (size_t)n * nz;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     bool ok = true;
-    bool first = true;
-    for (int i = chunk; i < n && ok; i += a.chunks) {
-        // taps of this plane (the previous GEMM 2, which read them, has completed)
-        if (threadIdx.x == 0) tma_load_1d(st.s.tap, a.ttab + (size_t)i * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
+
+    // Pipeline per plane i (next plane i' = i + chunks):
+    //   GEMM 1(i) done -> D1 to A2 -> issue GEMM 2(i)
+    //   stage plane i' into B1 while GEMM 2(i) runs
+    //   GEMM 2(i) done -> TMA the Toeplitz tiles of i' -> issue GEMM 1(i')
+    uint32_t ph_t = 0, ph_1 = 0, ph_2 = 0;
+    int i = chunk;
+    if (i < n) {
         const float* arow = a.atten ? a.atten + ((size_t)angle * n + i) * n * nz : nullptr;
+        if (threadIdx.x == 0) tma_load_1d(st.s.tap, a.ttab + (size_t)i * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
         tc_tap_rows(rows, n, nz, i, cs, c);
         __syncthreads();
         tc_stage_plane(st.s.b1, st.s.b1_lo, rows, xb, arow, n, nz);
         fence_async_smem();
-        ok = all_ok(mbar_wait(st.s.bar_t, phase), a.err);
-        if (!ok) break;
-        if (threadIdx.x == 0) issue_gemm1(st.s, d1, idesc);
-        ok = all_ok(mbar_wait(st.s.bar_1, phase), a.err);
+        ok = all_ok(mbar_wait(st.s.bar_t, ph_t), a.err);
+        ph_t ^= 1u;
+        if (ok && threadIdx.x == 0) issue_gemm1(st.s, d1, idesc, n);
+    }
+    bool first = true;
+    for (; i < n && ok; i += a.chunks) {
+        const int inext = i + a.chunks;
+        ok = all_ok(mbar_wait(st.s.bar_1, ph_1), a.err);
+        ph_1 ^= 1u;
         if (!ok) break;
         tc_fence_after();
         d1_to_a2(st.s, d1, n);
@@ -407,19 +445,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
         tc_fence_before();
         __syncthreads();
         if (threadIdx.x == 0) issue_gemm2(st.s, d2, idesc, n, !first);
-        ok = all_ok(mbar_wait(st.s.bar_2, phase), a.err);
-        phase ^= 1u;
         first = false;
+        if (inext < n) {
+            // GEMM 1(i) has finished with B1; stage the next plane meanwhile
+            const float* arow = a.atten ? a.atten + ((size_t)angle * n + inext) * n * nz : nullptr;
+            tc_tap_rows(rows, n, nz, inext, cs, c);
+            __syncthreads();
+            tc_stage_plane(st.s.b1, st.s.b1_lo, rows, xb, arow, n, nz);
+            fence_async_smem();
+        }
+        ok = all_ok(mbar_wait(st.s.bar_2, ph_2), a.err);
+        ph_2 ^= 1u;
+        if (!ok || inext >= n) break;
+        if (threadIdx.x == 0) tma_load_1d(st.s.tap, a.ttab + (size_t)inext * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
+        ok = all_ok(mbar_wait(st.s.bar_t, ph_t), a.err);
+        ph_t ^= 1u;
+        if (ok && threadIdx.x == 0) issue_gemm1(st.s, d1, idesc, n);
     }
     if (ok && !first) {
         // D2 = (sum over the chunk's planes)^T: lanes k, columns j
         tc_fence_after();
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const int k = 32 * (warp & 3) + lane;
-        const size_t item = (size_t)b * a.n_sel + sidx;
-        float* dst = a.partials ? a.partials + (item * a.chunks + chunk) * (size_t)n * nz : a.out + item * (size_t)n * nz;
-        const int half = n / 2, c0 = (warp >> 2) * half;
-        for (int cc = c0; cc < c0 + half; cc += 16) {
+        for (int cc = 16 * (warp >> 2); cc < n; cc += 64) {
             float v[16];
             tc_ld16(d2 + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)cc, v);
             if (k < nz) {
@@ -429,8 +476,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
         }
     } else if (ok && first) {
         // a chunk without planes (more chunks than planes): its sum is zero
-        const size_t item = (size_t)b * a.n_sel + sidx;
-        float* dst = a.partials ? a.partials + (item * a.chunks + chunk) * (size_t)n * nz : a.out + item * (size_t)n * nz;
         for (int e = threadIdx.x; e < n * nz; e += blockDim.x) dst[e] = 0.f;
     }
     tc_teardown(st, ncols);
@@ -451,21 +496,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
     const uint32_t idesc = idesc_bf16(kTcM, n);
     const size_t item = (size_t)b * a.n_sel + sidx;
     const float* pr = a.proj ? a.proj + (size_t)b * a.proj_bstride + (size_t)sidx * n * nz : nullptr;
-    tc_stage_proj(st.s.b1, st.s.b1_lo, pr, n, nz);
-    fence_async_smem();
-    __syncthreads();
     float* bvol = a.bvol + item * (size_t)n * n * nz;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = 32 * (warp & 3) + lane;
-    const int half = n / 2, c0 = (warp >> 2) * half;
-    uint32_t phase = 0;
     bool ok = true;
-    for (int i = chunk; i < n && ok; i += a.chunks) {
-        if (threadIdx.x == 0) tma_load_1d(st.s.tap, a.ttab + (size_t)i * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
-        ok = all_ok(mbar_wait(st.s.bar_t, phase), a.err);
-        if (!ok) break;
-        if (threadIdx.x == 0) issue_gemm1(st.s, d1, idesc);
-        ok = all_ok(mbar_wait(st.s.bar_1, phase), a.err);
+    uint32_t ph_t = 0, ph_1 = 0, ph_2 = 0;
+
+    // the projection of this angle is the B operand of every plane's GEMM 1
+    int i = chunk;
+    if (i < n && threadIdx.x == 0)
+        tma_load_1d(st.s.tap, a.ttab + (size_t)i * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
+    tc_stage_proj(st.s.b1, st.s.b1_lo, pr, n, nz);
+    fence_async_smem();
+    if (i < n) {
+        ok = all_ok(mbar_wait(st.s.bar_t, ph_t), a.err);
+        ph_t ^= 1u;
+        if (ok && threadIdx.x == 0) issue_gemm1(st.s, d1, idesc, n);
+    }
+    // Pipeline per plane i: GEMM 1(i) done -> D1 to A2 -> GEMM 2(i);
+    // GEMM 2(i) done -> TMA of the next tiles, then the epilogue of plane i
+    // (attenuation and store of B) while the copy is in flight -> GEMM 1(i').
+    for (; i < n && ok; i += a.chunks) {
+        const int inext = i + a.chunks;
+        ok = all_ok(mbar_wait(st.s.bar_1, ph_1), a.err);
+        ph_1 ^= 1u;
         if (!ok) break;
         tc_fence_after();
         d1_to_a2(st.s, d1, n);
@@ -473,26 +527,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
         tc_fence_before();
         __syncthreads();
         if (threadIdx.x == 0) issue_gemm2(st.s, d2, idesc, n, false);
-        ok = all_ok(mbar_wait(st.s.bar_2, phase), a.err);
+        ok = all_ok(mbar_wait(st.s.bar_2, ph_2), a.err);
+        ph_2 ^= 1u;
         if (!ok) break;
+        if (inext < n && threadIdx.x == 0)
+            tma_load_1d(st.s.tap, a.ttab + (size_t)inext * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
         tc_fence_after();
         // B[i][j][k] = A[i][j][k] * (K_i r)[j][k]; D2 holds (K_i r)^T (lanes k)
         const float* arow = a.atten ? a.atten + ((size_t)angle * n + i) * n * nz : nullptr;
         float* brow = bvol + (size_t)i * n * nz;
-        for (int cc = c0; cc < c0 + half; cc += 16) {
+        for (int cc = 16 * (warp >> 2); cc < n; cc += 64) {
+            float aw[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) aw[q] = (arow && k < nz) ? __ldg(arow + (size_t)(cc + q) * nz + k) : 1.f;
             float v[16];
             tc_ld16(d2 + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)cc, v);
             if (k < nz) {
-                float aw[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) aw[q] = arow ? __ldg(arow + (size_t)(cc + q) * nz + k) : 1.f;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) brow[(size_t)(cc + q) * nz + k] = v[q] * aw[q];
             }
         }
         tc_fence_before();
-        __syncthreads();  // TMEM and the tap tiles are reused by the next plane
-        phase ^= 1u;
+        __syncthreads();  // D2 is overwritten by the next GEMM 2
+        if (inext >= n) break;
+        ok = all_ok(mbar_wait(st.s.bar_t, ph_t), a.err);
+        ph_t ^= 1u;
+        if (ok && threadIdx.x == 0) issue_gemm1(st.s, d1, idesc, n);
     }
     tc_teardown(st, ncols);
 }
@@ -510,7 +570,7 @@ int bf16_occupancy(int n)
     return blocks > 0 ? blocks : 1;
 }
 
-size_t bf16_smem_bytes(int n) { return (size_t)2 * kTile + (size_t)4 * n * kTcM * 2 + 64 + 32 * (size_t)n; }
+size_t bf16_smem_bytes(int n) { return (size_t)bf16_tail_offset(n) + 64 + 32 * (size_t)n; }
 
 uint32_t bf16_tmem_cols(int n)
 {

@@ -151,8 +151,9 @@ float bf16_value(uint16_t h)
 
 // Per-plane banded Toeplitz tiles T_i[r][c] = w_i(r - c) (|r - c| <= R_i) of
 // the tensor-core PSF path, as BF16 hi and lo parts (w = hi + lo to ~2^-17),
-// in the K-major no-swizzle core-matrix layout of a 128 x 128 tile:
-// element (r, c) at ((r/8)*16 + c/8)*64 + (r%8)*8 + c%8.
+// in the K-major 128-byte-swizzled layout of a 128 x 128 tile: K blocks of
+// 64 columns (16 KB apart), rows of 128 B, 8-row atoms of 1 KB in which the
+// 16-byte chunk c of row r sits at chunk c ^ (r % 8).
 void build_toeplitz_bf16(const spect_geom& g, int n, std::vector<uint16_t>& out)
 {
     const int T = 128;
@@ -172,7 +173,10 @@ void build_toeplitz_bf16(const spect_geom& g, int n, std::vector<uint16_t>& out)
                 const double wv = w[row - col + r];
                 const uint16_t h = bf16_bits((float)wv);
                 const uint16_t l = bf16_bits((float)(wv - (double)bf16_value(h)));
-                const size_t e = ((size_t)((row >> 3) * (T >> 3) + (col >> 3)) << 6) + ((row & 7) << 3) + (col & 7);
+                const int kb = col >> 6, kk = col & 63;
+                const size_t byte = (size_t)kb * T * 128 + ((size_t)(row >> 3) << 10) + ((row & 7) << 7) +
+                                    ((((kk >> 3) ^ (row & 7))) << 4) + ((kk & 7) << 1);
+                const size_t e = byte >> 1;
                 hi[e] = h;
                 lo[e] = l;
             }
