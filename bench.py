@@ -55,6 +55,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--psf", default="fp32", choices=["fp32", "bf16"],
                     help="bf16: PSF as BF16 tensor-core GEMMs, FP64 attenuation sums")
+    ap.add_argument("--serve-requests", type=int, default=256,
+                    help="requests of the serving leg (0 skips it)")
+    ap.add_argument("--serve-budget-gib", type=float, default=8.0)
     return ap.parse_args()
 
 
@@ -228,6 +231,83 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- serving leg
+
+SERVE_CLASSES = [(64, 60), (96, 96), (128, 120)]
+
+
+def make_serving_requests(spect, dev, count, seed0=1000):
+    """Seeded request stream: size class uniform over 64^3/60, 96^3/96 and
+    128^3/120 angles, 2-6 iterations x 8 subsets, counts log-uniform in
+    [1e6, 1e7], a phantom and mu map per request; y ~ Poisson(H f + s) with H
+    from the library (FP32)."""
+    import torch
+
+    from paper_2309_01977_gb300 import phantom
+    rng = np.random.Generator(np.random.PCG64(seed0))
+    reqs = []
+    for r in range(count):
+        n, na = SERVE_CLASSES[int(rng.integers(0, 3))]
+        iters = int(rng.integers(2, 7))
+        counts = float(10.0 ** rng.uniform(6.0, 7.0))
+        f, mu = phantom.make_phantom(n, n, seed0 + r)
+        g = spect.Geometry(n=n, nz=n, n_angles=na, n_subsets=8)
+        plan = spect.Plan(g, torch.from_numpy(mu.astype(np.float32)).to(dev))
+        hf = plan.forward(torch.from_numpy(f.astype(np.float32)).to(dev)).double().cpu().numpy()
+        plan.close()
+        _, y, s, _ = phantom.make_counts(f, hf, counts, 0.05, seed0 + r)
+        reqs.append({"n": n, "na": na, "iters": iters, "mu": mu.astype(np.float32), "y": y.astype(np.float32),
+                     "s": float(np.float32(s))})
+    return reqs
+
+
+def serve_stream(spect, reqs, bf16, budget, rate, seed=7):
+    """Submit the requests with exponential inter-arrival times at `rate`
+    (requests/s; None: all at once), wait for all; return stats and images."""
+    sv = spect.Server(budget, max_slots=8, n_streams=8)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate, size=len(reqs)) if rate else np.zeros(len(reqs))
+    t0 = time.perf_counter()
+    t_next = t0
+    ids = []
+    for q, gap in zip(reqs, gaps):
+        t_next += gap
+        delay = t_next - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        g = spect.Geometry(n=q["n"], nz=q["n"], n_angles=q["na"], n_subsets=8, psf_bf16=bf16, atten_f64=bf16)
+        ids.append(sv.submit(g, q["mu"], q["y"], q["s"], q["iters"]))
+    images = [sv.wait(i)[0] for i in ids]
+    st = sv.stats()
+    sv.close()
+    return st, images
+
+
+def run_serving(spect, dev, args):
+    reqs = make_serving_requests(spect, dev, args.serve_requests)
+    budget = int(args.serve_budget_gib * (1 << 30))
+    out = {"requests": len(reqs), "hbm_budget_gib": args.serve_budget_gib, "max_slots": 8, "streams": 8,
+           "classes": "64^3/60, 96^3/96, 128^3/120 angles; 2-6 it x 8 subsets; 1e6-1e7 counts; seeds 1000+i"}
+    # saturation throughput of each form (all requests at once)
+    cap = {}
+    imgs = {}
+    for form, bf16 in (("fp32", False), ("bf16", True)):
+        st, im = serve_stream(spect, reqs, bf16, budget, None)
+        cap[form] = st["recon_per_s"]
+        imgs[form] = im
+    # latency under Poisson arrivals at 80% of the FP32 saturation throughput
+    rate = 0.8 * cap["fp32"]
+    out["arrival_rate_per_s"] = rate
+    for form, bf16 in (("fp32", False), ("bf16", True)):
+        st, _ = serve_stream(spect, reqs, bf16, budget, rate)
+        out[form] = {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "recon_per_s": st["recon_per_s"],
+                     "saturation_recon_per_s": cap[form], "peak_active": st["peak_active"],
+                     "peak_gib": st["peak_bytes"] / (1 << 30)}
+    diffs = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(imgs["bf16"], imgs["fp32"])]
+    out["bf16_vs_fp32_image_rel_l2_max"] = max(diffs)
+    return out
+
+
 # ---------------------------------------------------------------- libspect arm
 
 def run_libspect(args):
@@ -342,6 +422,10 @@ def run_libspect(args):
                 "kernel_avg_us": {k: round(1e3 * v[1] / v[0], 2) for k, v in prof.items()},
                 "plane_tiling": {k: plan.info()[k] for k in ("ztile", "n_ztiles", "threads", "smem_bytes")}}
 
+    serving = None
+    if args.serve_requests > 0:
+        serving = run_serving(spect, dev, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, y, s, mu.astype(np.float64), args.cpu_seconds)
@@ -357,7 +441,7 @@ def run_libspect(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16 PSF, f32" if bf16 else "f32", "data": "synthetic",
             "config": cfg,
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": int(launches),
-            "clocks": clk,
+            "clocks": clk, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     plan.close()

@@ -20,7 +20,7 @@ LIB = os.path.join(PKG, "libspect.so")
 SOURCES = ["spect_api.cu", "plane_host.cu", "gather_kernel.cu", "misc_kernels.cu",
            "forward_ipt1.cu", "forward_ipt2.cu", "forward_ipt3.cu", "forward_ipt4.cu",
            "blur_back_ipt1.cu", "blur_back_ipt2.cu", "blur_back_ipt3.cu", "blur_back_ipt4.cu",
-           "noalloc.cu", "psf_bf16.cu"]
+           "noalloc.cu", "psf_bf16.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -32,7 +32,8 @@ def nvcc() -> str:
 
 
 def _deps_mtime() -> float:
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "spect.h"), __file__]
+    files = ([os.path.join(CSRC, f) for f in os.listdir(CSRC)] +
+             [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)] + [__file__])
     return max(os.path.getmtime(f) for f in files if os.path.isfile(f))
 
 

@@ -42,6 +42,8 @@ EXPORTED = [
     "spect_status_str", "spect_last_error", "spect_version",
     "spect_profile_enable", "spect_profile_read", "spect_kernel_launches",
     "spect_poisson_ll_noalloc", "spect_plan_check",
+    "spect_serve_create", "spect_serve_submit", "spect_serve_poll", "spect_serve_wait",
+    "spect_serve_cancel", "spect_serve_stats_get", "spect_serve_destroy",
 ]
 
 
@@ -352,3 +354,103 @@ class Plan:
 
 def uniform_angles(n_angles: int) -> list:
     return [2.0 * math.pi * a / n_angles for a in range(n_angles)]
+
+
+# ---------------------------------------------------------------- serving (include/spect_serve.h)
+
+SPECT_REQ_QUEUED, SPECT_REQ_RUNNING, SPECT_REQ_DONE, SPECT_REQ_FAILED, SPECT_REQ_CANCELLED = range(5)
+
+SERVE_EXPORTED = ["spect_serve_create", "spect_serve_submit", "spect_serve_poll", "spect_serve_wait",
+                  "spect_serve_cancel", "spect_serve_stats_get", "spect_serve_destroy"]
+
+
+class _ServeCfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("n_streams", ctypes.c_int),
+                ("wait_timeout_ms", ctypes.c_int)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("geom", _Geom), ("mu_host", ctypes.c_void_p), ("y_host", ctypes.c_void_p), ("s", ctypes.c_float),
+                ("n_iters", ctypes.c_int), ("tag", ctypes.c_uint64)]
+
+
+class _ServeStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "admitted", "completed", "failed", "cancelled",
+                                                "rejected", "queued", "active", "peak_active", "bytes_in_use",
+                                                "peak_bytes")] + \
+               [(k, ctypes.c_double) for k in ("p50_ms", "p99_ms", "max_ms", "recon_per_s")]
+
+
+def _serve_lib():
+    lib = load()
+    if not getattr(lib, "_serve_bound", False):
+        vp = ctypes.c_void_p
+        lib.spect_serve_create.argtypes = [ctypes.POINTER(_ServeCfg), ctypes.POINTER(vp)]
+        lib.spect_serve_submit.argtypes = [vp, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_uint64)]
+        lib.spect_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]
+        lib.spect_serve_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double)]
+        lib.spect_serve_cancel.argtypes = [vp, ctypes.c_uint64]
+        lib.spect_serve_stats_get.argtypes = [vp, ctypes.POINTER(_ServeStats)]
+        lib.spect_serve_destroy.argtypes = [vp]
+        lib._serve_bound = True
+    return lib
+
+
+class Server:
+    """Continuous-batching reconstruction server (host numpy float32 in and out)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 8, n_streams: int = 8, wait_timeout_ms: int = 600000):
+        lib = _serve_lib()
+        cfg = _ServeCfg(int(hbm_budget_bytes), int(max_slots), int(n_streams), int(wait_timeout_ms))
+        h = ctypes.c_void_p()
+        _check(lib.spect_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h.value
+        self._shapes = {}
+
+    def submit(self, geom: Geometry, mu, y, s: float, n_iters: int, tag: int = 0) -> int:
+        import numpy as np
+        lib = _serve_lib()
+        g, keep = geom.to_c()
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        mu = None if mu is None else np.ascontiguousarray(mu, dtype=np.float32)
+        req = _Request(g, None if mu is None else mu.ctypes.data, y.ctypes.data, float(s), int(n_iters), int(tag))
+        rid = ctypes.c_uint64()
+        _check(lib.spect_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(rid)))
+        self._shapes[rid.value] = (geom.n, geom.n, geom.nz)
+        del keep
+        return rid.value
+
+    def poll(self, rid: int) -> int:
+        st = ctypes.c_int()
+        _check(_serve_lib().spect_serve_poll(self.handle, rid, ctypes.byref(st)))
+        return st.value
+
+    def wait(self, rid: int, timeout_ms: int = 0):
+        """(image [n][n][nz] float32, latency ms)."""
+        import numpy as np
+        x = np.empty(self._shapes[rid], dtype=np.float32)
+        lat = ctypes.c_double()
+        rc = _serve_lib().spect_serve_wait(self.handle, rid, int(timeout_ms), x.ctypes.data, ctypes.byref(lat))
+        if rc != SPECT_ETIMEDOUT:
+            self._shapes.pop(rid, None)
+        _check(rc)
+        return x, lat.value
+
+    def cancel(self, rid: int) -> None:
+        _check(_serve_lib().spect_serve_cancel(self.handle, rid))
+
+    def stats(self) -> dict:
+        st = _ServeStats()
+        _check(_serve_lib().spect_serve_stats_get(self.handle, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in _ServeStats._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            _serve_lib().spect_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -79,3 +79,17 @@ def test_null_plan_rejected(spect_lib):
     assert lib.spect_forward(None, None, None, 0, 1, None) == spect_lib.SPECT_EINVAL
     assert lib.spect_osem_run(None, None, ctypes.c_float(0.0), None, 0, 1, None, None) == spect_lib.SPECT_EINVAL
     assert lib.spect_plan_destroy(None) == 0
+
+
+def test_serve_config_validation(spect_lib):
+    lib = spect_lib._serve_lib()
+    out = ctypes.c_void_p()
+    for cfg in [(0, 4, 4, 1000), (1 << 30, 0, 4, 1000), (1 << 30, 4, 0, 1000), (1 << 30, 4, 4, 0)]:
+        c = spect_lib._ServeCfg(*cfg)
+        assert lib.spect_serve_create(ctypes.byref(c), ctypes.byref(out)) == spect_lib.SPECT_EINVAL
+        assert out.value is None
+    rid = ctypes.c_uint64()
+    assert lib.spect_serve_submit(None, None, ctypes.byref(rid)) == spect_lib.SPECT_EINVAL
+    st = ctypes.c_int()
+    assert lib.spect_serve_poll(None, 1, ctypes.byref(st)) == spect_lib.SPECT_EINVAL
+    assert lib.spect_serve_destroy(None) == 0
