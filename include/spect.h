@@ -70,7 +70,8 @@ extern "C" {
 #define SPECT_FLAG_PSF_BF16 4u   /* PSF as banded-Toeplitz BF16 tensor-core GEMMs (FP32
                                     accumulate; needs nx % 32 == 0, nx <= 128,
                                     nz % 8 == 0, nz <= 128) */
-#define SPECT_FLAG_ATTEN_F64 8u  /* attenuation prefix sums in FP64 (else compensated FP32) */
+#define SPECT_FLAG_ATTEN_F64 8u  /* attenuation prefix sums in FP64 (else compensated FP32);
+                                    the exponential is FP32 either way */
 
 typedef struct spect_geom {
     int nx, ny, nz;           /* volume size; nx == ny required, nz % 4 == 0 */
@@ -150,6 +151,17 @@ int spect_sensitivity(spect_plan* plan, int subset, float* out, void* stream);
  * Resume by calling again with the next first_subiter. */
 int spect_osem_run(spect_plan* plan, const float* y, float s, float* x_inout, int first_subiter,
                    int n_subiters, double* diag_dev, void* stream);
+
+/* spect_osem_run with the scatter term read from device memory (*s_dev)
+ * when the kernels run, so that a captured CUDA graph of the run can be
+ * replayed for a new s. */
+int spect_osem_run_dev(spect_plan* plan, const float* y, const float* s_dev, float* x_inout, int first_subiter,
+                       int n_subiters, double* diag_dev, void* stream);
+
+/* Reuse a plan for a new attenuation map: recompute the attenuation cache
+ * and the subset sensitivities from mu_dev [nx][ny][nz] (1/cm), queued on
+ * `stream` (no synchronisation).  The geometry tables are kept. */
+int spect_plan_set_mu(spect_plan* plan, const float* mu_dev, void* stream);
 
 /* Poisson log-likelihood (Table 1, PoissonLogLikelihood), FP64 sums:
  *   ll_dev[0] = sum_b y_b log(p_b + s) - (p_b + s)   (log y! dropped)

@@ -4,11 +4,15 @@
  * The paper reconstructs one acquisition at a time (Sec. 3, OSEM with the
  * Poisson gradient of Table 1).  This server runs many such reconstructions
  * of different sizes, angle counts and iteration budgets as they arrive:
- * requests wait in a queue and are admitted while a slot is free and their
- * device footprint fits a fixed HBM budget; each admitted request keeps its
- * own plan (attenuation cache, sensitivities), image and counts on the
- * device, and its OSEM run is captured as a CUDA graph and launched on one
- * of the server's streams, overlapping the others.  Results are bitwise the
+ * requests wait in a queue and are admitted while fewer than max_slots run
+ * and their device footprint fits a fixed HBM budget.  Device state lives in
+ * slots, one per acquisition geometry in use, reused by later requests of the
+ * same geometry: a plan (tables, attenuation cache, sensitivities), the
+ * image, counts and scatter buffers, and a CUDA graph of one OSEM iteration
+ * captured when the slot is built and replayed n_iters times per request.
+ * Admitting a request uploads its counts and mu and recomputes the slot's
+ * attenuation cache and sensitivities; slots run on the server's streams and
+ * overlap on the device.  Results are bitwise the
  * same alone or in any mix (no state is shared between requests).
  *
  * Threading: the server owns one scheduler thread; every call below is
@@ -52,6 +56,8 @@ typedef struct spect_serve_stats {
     uint64_t submitted, admitted, completed, failed, cancelled, rejected;
     uint64_t queued, active, peak_active;
     uint64_t bytes_in_use, peak_bytes;
+    uint64_t slots_created;        /* device slots built (one per geometry in use, reused) */
+    uint64_t graph_slots;          /* of which replay a captured CUDA graph per iteration */
     double p50_ms, p99_ms, max_ms; /* latency, submit to result on the host */
     double recon_per_s;            /* completed / (last completion - first submit) */
 } spect_serve_stats;

@@ -61,6 +61,7 @@ struct ReduceArgs {
     const float* y;        // [n_angles][plane] or nullptr
     const int* sel;        // angle ids (ratio mode)
     float s;
+    const float* s_ptr;    // when not NULL, s is read from this device word
     double* diag_blocks;   // [gridDim.x][3] or nullptr: sums of (p+s), y, y*p/(p+s)
 };
 

@@ -9,7 +9,10 @@ namespace spect {
 // T_att of Eq. (1) in the rotated frame of angle a: one thread per detector
 // ray (j, k) walks depth from the detector side (i = n-1) inward,
 //   A[i] = exp(-(sum_{i'>i} tau[i'] + tau[i]/2)),  tau = voxel_cm * bilinear(mu)(u, v, k).
-// The running sum is FP64 (f64 != 0) or Kahan-compensated FP32.
+// The running sum is FP64 (f64 != 0) or Kahan-compensated FP32; the
+// exponential is FP32 in both (its argument carries the sum's precision).
+// The mu loads do not depend on the sum, so the unrolled walk keeps several
+// in flight.
 __global__ void attenuation_kernel(const float* __restrict__ mu, const float2* __restrict__ cs_tab, int n, int nz,
                                    float voxel_cm, int f64, float* __restrict__ atten)
 {
@@ -21,6 +24,8 @@ __global__ void attenuation_kernel(const float* __restrict__ mu, const float2* _
     const float c = 0.5f * (float)(n - 1);
     double sum_d = 0.0;
     float sum = 0.f, comp = 0.f;
+    float* out = atten + ((size_t)angle * n * n + j) * nz + k;
+#pragma unroll 8
     for (int i = n - 1; i >= 0; --i) {
         float u, v;
         sample_point(cs.x, cs.y, c, i, j, u, v);
@@ -35,7 +40,7 @@ __global__ void attenuation_kernel(const float* __restrict__ mu, const float2* _
         const float tau = voxel_cm * m;
         float a;
         if (f64) {
-            a = (float)exp(-(sum_d + 0.5 * (double)tau));
+            a = expf(-(float)(sum_d + 0.5 * (double)tau));
             sum_d += (double)tau;
         } else {
             a = expf(-((sum + comp) + 0.5f * tau));
@@ -45,7 +50,7 @@ __global__ void attenuation_kernel(const float* __restrict__ mu, const float2* _
             comp = (tv - sum) - yv;
             sum = tv;
         }
-        atten[(((size_t)angle * n + i) * n + j) * nz + k] = a;
+        out[(size_t)i * n * nz] = a;
     }
 }
 
@@ -82,6 +87,7 @@ __global__ void forward_reduce_kernel(ReduceArgs a)
     __shared__ double red[32];
     const int plane4 = a.plane >> 2;
     const size_t total4 = (size_t)a.items * plane4;
+    const float s = a.s_ptr ? __ldg(a.s_ptr) : a.s;
     double d0 = 0.0, d1 = 0.0, d2 = 0.0;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total4; e += (size_t)gridDim.x * blockDim.x) {
         const int item = (int)(e / plane4);
@@ -104,7 +110,7 @@ __global__ void forward_reduce_kernel(ReduceArgs a)
             float rv[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float den = pv[q] + a.s;
+                const float den = pv[q] + s;
                 rv[q] = den > 0.f ? yy[q] / den : 0.f;
                 d0 += (double)den;
                 d1 += (double)yy[q];

@@ -422,11 +422,18 @@ inline cudaError_t allow_big_smem(F fn, unsigned long long& mask)
     return e;
 }
 
+// Devices on which a kernel's shared-memory limit has been raised (shared by
+// the occupancy query at plan creation and the launches, so that launches
+// inside a stream capture find it done).
+template <int IPT>
+unsigned long long g_forward_smem_mask = 0;
+template <int IPT>
+unsigned long long g_blur_back_smem_mask = 0;
+
 template <int IPT>
 cudaError_t forward_launch_ipt(const ForwardArgs& a, int grid_x, cudaStream_t st)
 {
-    static unsigned long long mask = 0;
-    cudaError_t e = allow_big_smem(forward_kernel<IPT>, mask);
+    cudaError_t e = allow_big_smem(forward_kernel<IPT>, g_forward_smem_mask<IPT>);
     if (e != cudaSuccess) return e;
     dim3 grid(grid_x, a.n_sel, a.batch);
     forward_kernel<IPT><<<grid, a.t.threads, a.t.smem, st>>>(a);
@@ -436,8 +443,7 @@ cudaError_t forward_launch_ipt(const ForwardArgs& a, int grid_x, cudaStream_t st
 template <int IPT>
 int forward_occupancy_ipt(int threads, size_t smem)
 {
-    static unsigned long long mask = 0;
-    if (allow_big_smem(forward_kernel<IPT>, mask) != cudaSuccess) {
+    if (allow_big_smem(forward_kernel<IPT>, g_forward_smem_mask<IPT>) != cudaSuccess) {
         cudaGetLastError();  // do not leave the failure to a later launch check
         return 0;
     }
@@ -452,8 +458,7 @@ int forward_occupancy_ipt(int threads, size_t smem)
 template <int IPT>
 cudaError_t blur_back_launch_ipt(const BlurBackArgs& a, int grid_x, cudaStream_t st)
 {
-    static unsigned long long mask = 0;
-    cudaError_t e = allow_big_smem(blur_back_kernel<IPT>, mask);
+    cudaError_t e = allow_big_smem(blur_back_kernel<IPT>, g_blur_back_smem_mask<IPT>);
     if (e != cudaSuccess) return e;
     dim3 grid(grid_x, a.n_sel, a.batch);
     blur_back_kernel<IPT><<<grid, a.t.threads, a.t.smem, st>>>(a);

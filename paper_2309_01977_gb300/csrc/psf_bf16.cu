@@ -557,12 +557,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
     tc_teardown(st, ncols);
 }
 
+namespace {
+// devices on which the kernels' shared-memory limits have been raised
+unsigned long long g_fwd_bf16_mask = 0, g_back_bf16_mask = 0;
+
+template <class F>
+cudaError_t raise_smem(F fn, unsigned long long& mask)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (mask & (1ull << (dev & 63))) return cudaSuccess;
+    // the largest footprint of any supported n, so one setting serves all plans
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf16_smem_bytes(kTcM));
+    if (e == cudaSuccess) mask |= 1ull << (dev & 63);
+    return e;
+}
+}  // namespace
+
 int bf16_occupancy(int n)
 {
     int blocks = 0;
     const size_t smem = bf16_smem_bytes(n);
-    if (cudaFuncSetAttribute(forward_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)bf16_smem_bytes(kTcM)) != cudaSuccess ||
+    if (raise_smem(forward_bf16_kernel, g_fwd_bf16_mask) != cudaSuccess ||
+        raise_smem(blur_back_bf16_kernel, g_back_bf16_mask) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, forward_bf16_kernel, kTcThreads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -581,38 +599,19 @@ uint32_t bf16_tmem_cols(int n)
 
 cudaError_t launch_forward_bf16(const ForwardBf16Args& a, cudaStream_t st)
 {
-    static unsigned long long mask = 0;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    cudaError_t e = raise_smem(forward_bf16_kernel, g_fwd_bf16_mask);
     if (e != cudaSuccess) return e;
-    const size_t smem = bf16_smem_bytes(a.n);
-    if (!(mask & (1ull << (dev & 63)))) {
-        // the largest footprint of any supported n, so one setting serves all plans
-        e = cudaFuncSetAttribute(forward_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)bf16_smem_bytes(kTcM));
-        if (e != cudaSuccess) return e;
-        mask |= 1ull << (dev & 63);
-    }
     dim3 grid(a.chunks, a.n_sel, a.batch);
-    forward_bf16_kernel<<<grid, kTcThreads, smem, st>>>(a);
+    forward_bf16_kernel<<<grid, kTcThreads, bf16_smem_bytes(a.n), st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_blur_back_bf16(const BlurBackBf16Args& a, cudaStream_t st)
 {
-    static unsigned long long mask = 0;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    cudaError_t e = raise_smem(blur_back_bf16_kernel, g_back_bf16_mask);
     if (e != cudaSuccess) return e;
-    const size_t smem = bf16_smem_bytes(a.n);
-    if (!(mask & (1ull << (dev & 63)))) {
-        e = cudaFuncSetAttribute(blur_back_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)bf16_smem_bytes(kTcM));
-        if (e != cudaSuccess) return e;
-        mask |= 1ull << (dev & 63);
-    }
     dim3 grid(a.chunks, a.n_sel, a.batch);
-    blur_back_bf16_kernel<<<grid, kTcThreads, smem, st>>>(a);
+    blur_back_bf16_kernel<<<grid, kTcThreads, bf16_smem_bytes(a.n), st>>>(a);
     return cudaGetLastError();
 }
 

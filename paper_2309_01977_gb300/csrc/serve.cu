@@ -1,17 +1,19 @@
 // Continuous-batching reconstruction server (spect_serve_*).
 //
 // Requests (geometry, mu, counts, iteration budget) arrive at any time and
-// wait in a FIFO queue.  A scheduler thread admits them while a slot is free
-// and their device footprint fits the HBM budget (later, smaller requests
-// may pass a head that does not fit yet).  Each admitted request gets its own
-// plan (attenuation cache, sensitivities, tables), device image, counts and
-// stream; its whole OSEM run is captured once as a CUDA graph and launched on
-// that stream, followed by the read-back of the image into pinned memory.
-// Requests on different streams overlap on the device; every kernel of a
-// request reads and writes only that request's buffers, so its result is
-// bitwise the same alone or in any mix.  When a request's completion event
-// fires, its device memory is returned to the budget and the queue is
-// admitted again.  Latency is measured from submit to completion.
+// wait in a FIFO queue.  The device work happens in slots: a slot holds, for
+// one acquisition geometry, a plan (geometry tables, attenuation cache,
+// sensitivities), the image, counts and scatter buffers, a stream and a CUDA
+// graph of one OSEM iteration (all subsets) captured once.  A scheduler
+// thread admits a request into an idle slot of its geometry, or into a new
+// slot when the slot fits the HBM budget (idle slots of other geometries are
+// released to make room; later, smaller requests may pass a head that does
+// not fit yet).  Admission uploads the request's counts and mu, recomputes
+// the slot's attenuation cache and sensitivities, sets x = 1 and replays the
+// iteration graph n_iters times, then reads the image back into pinned
+// memory.  Slots on different streams overlap on the device; every kernel of
+// a request reads and writes only its slot, so a result is bitwise the same
+// alone or in any mix.  Latency is measured from submit to completion.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -95,15 +97,34 @@ struct Request {
     int status = SPECT_OK;
     bool cancel = false;
     double t_submit = 0, t_admit = 0, t_done = 0;
-    // device state while admitted
+    struct Slot* slot = nullptr;  // while admitted
+};
+
+// Device state for one acquisition geometry, reused by successive requests.
+struct Slot {
+    spect_geom geom{};
+    std::vector<double> angles;
     spect_plan* plan = nullptr;
     float* d_mu = nullptr;
     float* d_y = nullptr;
     float* d_x = nullptr;
+    float* d_s = nullptr;
+    size_t vol = 0, proj = 0, bytes = 0;
     cudaStream_t stream = nullptr;
+    cudaGraphExec_t iter = nullptr;  // one OSEM iteration (all subsets); NULL: launch directly
     cudaEvent_t done = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    bool busy = false;
+    bool fresh = false;  // plan built from the current request's mu
+    Request* req = nullptr;
 };
+
+bool same_geometry(const spect_geom& a, const std::vector<double>& aa, const spect_geom& b,
+                   const std::vector<double>& ba)
+{
+    return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.voxel_cm == b.voxel_cm && a.n_angles == b.n_angles &&
+           a.psf_sigma0 == b.psf_sigma0 && a.psf_slope == b.psf_slope && a.psf_nsigma == b.psf_nsigma &&
+           a.det_offset == b.det_offset && a.n_subsets == b.n_subsets && a.flags == b.flags && aa == ba;
+}
 
 }  // namespace
 
@@ -115,6 +136,7 @@ struct spect_server {
     std::condition_variable cv_work, cv_done;
     std::deque<Request*> queue;
     std::vector<Request*> active;
+    std::vector<Slot*> slots;
     std::map<uint64_t, Request*> all;
     std::vector<cudaStream_t> streams;
     size_t next_stream = 0;
@@ -130,87 +152,115 @@ struct spect_server {
 
 namespace {
 
-// Upper bound of a plan's device memory plus the request's image, counts and mu.
+// Upper bound of a slot's device memory: the plan plus image, counts, mu.
 size_t request_bytes(const spect_geom& g, int num_sms)
 {
     const size_t n = (size_t)g.nx, nz = (size_t)g.nz, na = (size_t)g.n_angles, M = (size_t)g.n_subsets;
     const size_t vol = n * n * nz, plane = n * nz;
     const size_t max_subset = (na + M - 1) / M;
     size_t b = 0;
-    b += M * vol * 4;                                               // sensitivities
+    b += M * vol * 4;                                                    // sensitivities
     b += std::max<size_t>(4 * (size_t)num_sms, max_subset) * plane * 4;  // depth-chunk partials
-    b += na * n * n * spect::kMaxCand * 8;                          // gather tables
-    b += std::max<size_t>(max_subset, 16) * vol * 4;                // rotated-frame volumes
-    b += max_subset * plane * 4 + vol * 4;                          // ratio, back projection
-    if (g.flags & SPECT_FLAG_ATTEN) b += na * vol * 4;              // attenuation cache
-    if (g.flags & SPECT_FLAG_PSF_BF16) b += n * 2 * 128 * 128 * 2;  // Toeplitz tiles
-    b += 3 * vol * 4 + na * plane * 4;                              // mu, x, y
-    b += 1 << 20;                                                   // tables, small scratch
+    b += na * n * n * spect::kMaxCand * 8;                               // gather tables
+    b += std::max<size_t>(max_subset, 16) * vol * 4;                     // rotated-frame volumes
+    b += max_subset * plane * 4 + vol * 4;                               // ratio, back projection
+    if (g.flags & SPECT_FLAG_ATTEN) b += na * vol * 4;                   // attenuation cache
+    if (g.flags & SPECT_FLAG_PSF_BF16) b += n * 2 * 128 * 128 * 2;       // Toeplitz tiles
+    b += 3 * vol * 4 + na * plane * 4;                                   // mu, x, y
+    b += 1 << 20;                                                        // tables, small scratch
     return b;
 }
 
-void release_device(Request* r)
+void destroy_slot(Slot* sl)
 {
-    if (r->exec) cudaGraphExecDestroy(r->exec);
-    if (r->done) cudaEventDestroy(r->done);
-    if (r->plan) spect_plan_destroy(r->plan);
-    if (r->d_mu) cudaFree(r->d_mu);
-    if (r->d_y) cudaFree(r->d_y);
-    if (r->d_x) cudaFree(r->d_x);
-    r->exec = nullptr;
-    r->done = nullptr;
-    r->plan = nullptr;
-    r->d_mu = r->d_y = r->d_x = nullptr;
+    if (sl->done) cudaEventSynchronize(sl->done);  // an idle slot's last work has completed
+    if (sl->iter) cudaGraphExecDestroy(sl->iter);
+    if (sl->done) cudaEventDestroy(sl->done);
+    if (sl->plan) spect_plan_destroy(sl->plan);
+    if (sl->d_mu) cudaFree(sl->d_mu);
+    if (sl->d_y) cudaFree(sl->d_y);
+    if (sl->d_x) cudaFree(sl->d_x);
+    if (sl->d_s) cudaFree(sl->d_s);
+    delete sl;
 }
 
-// Put an admitted request on the device and launch its reconstruction.
-// Called by the scheduler thread without the lock.
-int start_request(spect_server* sv, Request* r)
+// A new slot for r's geometry, its plan built from r's mu.  Called without
+// the lock.
+int create_slot(spect_server* sv, Request* r, cudaStream_t st, Slot** out)
 {
-    cudaStream_t st = r->stream;
-    cudaError_t e;
-    if ((e = cudaMalloc(&r->d_mu, r->vol * sizeof(float))) != cudaSuccess ||
-        (e = cudaMalloc(&r->d_x, r->vol * sizeof(float))) != cudaSuccess ||
-        (e = cudaMalloc(&r->d_y, r->proj * sizeof(float))) != cudaSuccess) {
+    Slot* sl = new (std::nothrow) Slot();
+    if (!sl) return SPECT_ENOMEM;
+    sl->geom = r->geom;
+    sl->angles = r->angles;
+    sl->vol = r->vol;
+    sl->proj = r->proj;
+    sl->bytes = r->bytes;
+    sl->stream = st;
+    if (cudaMalloc(&sl->d_mu, sl->vol * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&sl->d_x, sl->vol * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&sl->d_y, sl->proj * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&sl->d_s, 16) != cudaSuccess || cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
+        destroy_slot(sl);
         return SPECT_ENOMEM;
     }
-    if ((e = cudaMemcpyAsync(r->d_mu, r->h_mu, r->vol * sizeof(float), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(r->d_y, r->h_y, r->proj * sizeof(float), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    if (cudaMemcpyAsync(sl->d_mu, r->h_mu, sl->vol * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        destroy_slot(sl);
         return SPECT_ECUDA;
-    spect_geom g = r->geom;
-    g.angles_rad = r->angles.empty() ? nullptr : r->angles.data();
-    int rc = spect_plan_create(&g, (g.flags & SPECT_FLAG_ATTEN) ? r->d_mu : nullptr, st, &r->plan);
-    if (rc) return rc;
-    // the inputs have reached the device (plan creation synchronised the stream)
-    sv->pinned.give(r->h_mu);
-    r->h_mu = nullptr;
-    const int n_sub = r->n_iters * r->geom.n_subsets;
-    // capture the whole reconstruction as one graph: x = 1, then the OSEM run
+    }
+    spect_geom g = sl->geom;
+    g.angles_rad = sl->angles.empty() ? nullptr : sl->angles.data();
+    int rc = spect_plan_create(&g, (g.flags & SPECT_FLAG_ATTEN) ? sl->d_mu : nullptr, st, &sl->plan);
+    if (rc) {
+        destroy_slot(sl);
+        return rc;
+    }
+    sl->fresh = true;
+    // capture one OSEM iteration (subsets 0..M-1), reading s from d_s
     cudaGraph_t graph = nullptr;
-    bool captured = false;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        const cudaError_t fe = spect::launch_fill(r->d_x, r->vol, 1.f, st);
-        const int orc = fe == cudaSuccess ? spect_osem_run(r->plan, r->d_y, r->s, r->d_x, 0, n_sub, nullptr, st)
-                                          : SPECT_ECUDA;
+        const int orc = spect_osem_run_dev(sl->plan, sl->d_y, sl->d_s, sl->d_x, 0, g.n_subsets, nullptr, st);
         const cudaError_t ee = cudaStreamEndCapture(st, &graph);
-        if (orc == SPECT_OK && ee == cudaSuccess && graph &&
-            cudaGraphInstantiate(&r->exec, graph, 0) == cudaSuccess)
-            captured = true;
+        if (orc != SPECT_OK || ee != cudaSuccess || !graph || cudaGraphInstantiate(&sl->iter, graph, 0) != cudaSuccess)
+            sl->iter = nullptr;  // replay the launches directly instead
         if (graph) cudaGraphDestroy(graph);
         cudaGetLastError();
     }
-    if (captured) {
-        if (cudaGraphLaunch(r->exec, st) != cudaSuccess) return SPECT_ECUDA;
-    } else {
-        // graph capture unavailable: the same launches, issued directly
-        if (spect::launch_fill(r->d_x, r->vol, 1.f, st) != cudaSuccess) return SPECT_ECUDA;
-        if ((rc = spect_osem_run(r->plan, r->d_y, r->s, r->d_x, 0, n_sub, nullptr, st))) return rc;
+    (void)sv;
+    *out = sl;
+    return SPECT_OK;
+}
+
+// Queue request r on its slot: inputs, attenuation and sensitivities (unless
+// the slot was just built from r), x = 1, n_iters iterations, read-back.
+int start_request(spect_server* sv, Request* r, Slot* sl)
+{
+    cudaStream_t st = sl->stream;
+    if (!sl->fresh) {
+        if (cudaMemcpyAsync(sl->d_mu, r->h_mu, sl->vol * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return SPECT_ECUDA;
+        const int rc = spect_plan_set_mu(sl->plan, (sl->geom.flags & SPECT_FLAG_ATTEN) ? sl->d_mu : nullptr, st);
+        if (rc) return rc;
     }
-    if (cudaMemcpyAsync(r->h_x, r->d_x, r->vol * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    sl->fresh = false;
+    if (cudaMemcpyAsync(sl->d_y, r->h_y, sl->proj * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return SPECT_ECUDA;
-    if (cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming) != cudaSuccess) return SPECT_ECUDA;
-    if (cudaEventRecord(r->done, st) != cudaSuccess) return SPECT_ECUDA;
+    if (spect::launch_fill(sl->d_s, 1, r->s, st) != cudaSuccess) return SPECT_ECUDA;
+    if (spect::launch_fill(sl->d_x, sl->vol, 1.f, st) != cudaSuccess) return SPECT_ECUDA;
+    for (int it = 0; it < r->n_iters; ++it) {
+        if (sl->iter) {
+            if (cudaGraphLaunch(sl->iter, st) != cudaSuccess) return SPECT_ECUDA;
+        } else {
+            const int rc = spect_osem_run_dev(sl->plan, sl->d_y, sl->d_s, sl->d_x, 0, sl->geom.n_subsets, nullptr, st);
+            if (rc) return rc;
+        }
+    }
+    if (cudaMemcpyAsync(r->h_x, sl->d_x, sl->vol * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SPECT_ECUDA;
+    if (cudaEventRecord(sl->done, st) != cudaSuccess) return SPECT_ECUDA;
+    // the pinned mu copy is no longer needed once the stream has consumed it;
+    // it is returned when the request finishes (the stream is then past it)
+    (void)sv;
     return SPECT_OK;
 }
 
@@ -220,8 +270,9 @@ void finish(spect_server* sv, Request* r, int status, int state)
     r->status = status;
     r->state = state;
     r->t_done = now_ms();
+    sv->pinned.give(r->h_mu);
+    r->h_mu = nullptr;
     r->h_y = nullptr;  // the same pinned buffer now holds the image (h_x)
-    sv->in_use -= r->bytes;
     if (state == SPECT_REQ_DONE) {
         sv->stats.completed += 1;
         sv->latencies.push_back(r->t_done - r->t_submit);
@@ -237,7 +288,7 @@ void scheduler(spect_server* sv)
     cudaSetDevice(sv->device);
     std::unique_lock<std::mutex> lk(sv->m);
     while (true) {
-        // admit: FIFO, letting requests that fit pass one that does not fit yet
+        // admit: FIFO, letting requests that can start now pass one that cannot
         for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)sv->active.size() < sv->cfg.max_slots;) {
             Request* r = *it;
             if (r->cancel) {
@@ -251,46 +302,84 @@ void scheduler(spect_server* sv)
                 sv->cv_done.notify_all();
                 continue;
             }
-            if (sv->in_use + r->bytes > sv->cfg.hbm_budget_bytes) {
-                ++it;
-                continue;
+            Slot* sl = nullptr;
+            for (Slot* c : sv->slots)
+                if (!c->busy && same_geometry(c->geom, c->angles, r->geom, r->angles)) {
+                    sl = c;
+                    break;
+                }
+            if (!sl) {
+                // release idle slots of other geometries until a new one fits
+                for (size_t k = 0; k < sv->slots.size() && sv->in_use + r->bytes > sv->cfg.hbm_budget_bytes;) {
+                    Slot* c = sv->slots[k];
+                    if (c->busy) {
+                        ++k;
+                        continue;
+                    }
+                    sv->slots.erase(sv->slots.begin() + k);
+                    sv->in_use -= c->bytes;
+                    destroy_slot(c);
+                }
+                if (sv->in_use + r->bytes > sv->cfg.hbm_budget_bytes) {
+                    ++it;
+                    continue;
+                }
+                sv->in_use += r->bytes;
+                const cudaStream_t st = sv->streams[sv->next_stream++ % sv->streams.size()];
+                lk.unlock();
+                const int rc = create_slot(sv, r, st, &sl);
+                lk.lock();
+                if (rc) {
+                    sv->in_use -= r->bytes;
+                    it = sv->queue.erase(std::find(sv->queue.begin(), sv->queue.end(), r));
+                    finish(sv, r, rc, SPECT_REQ_FAILED);
+                    it = sv->queue.begin();
+                    continue;
+                }
+                sv->slots.push_back(sl);
+                sv->stats.slots_created += 1;
+                if (sl->iter) sv->stats.graph_slots += 1;
+                sv->stats.peak_bytes = std::max<uint64_t>(sv->stats.peak_bytes, sv->in_use);
             }
-            it = sv->queue.erase(it);
-            sv->in_use += r->bytes;
-            sv->stats.peak_bytes = std::max<uint64_t>(sv->stats.peak_bytes, sv->in_use);
+            sl->busy = true;
+            sl->req = r;
+            r->slot = sl;
+            sv->queue.erase(std::find(sv->queue.begin(), sv->queue.end(), r));
             r->state = SPECT_REQ_RUNNING;
             r->t_admit = now_ms();
-            r->stream = sv->streams[sv->next_stream++ % sv->streams.size()];
             sv->active.push_back(r);
             sv->stats.peak_active = std::max<uint64_t>(sv->stats.peak_active, sv->active.size());
             lk.unlock();
-            const int rc = start_request(sv, r);
+            const int rc = start_request(sv, r, sl);
             lk.lock();
             if (rc) {
                 sv->active.erase(std::find(sv->active.begin(), sv->active.end(), r));
-                cudaStreamSynchronize(r->stream);
-                release_device(r);
+                cudaStreamSynchronize(sl->stream);
+                sl->busy = false;
+                sl->req = nullptr;
                 finish(sv, r, rc, SPECT_REQ_FAILED);
-                it = sv->queue.begin();
             } else {
                 sv->stats.admitted += 1;
-                it = sv->queue.begin();  // the budget changed: rescan from the head
             }
+            it = sv->queue.begin();  // slots and budget changed: rescan from the head
         }
         // retire finished requests
         bool retired = false;
         for (size_t k = 0; k < sv->active.size();) {
             Request* r = sv->active[k];
-            const cudaError_t q = cudaEventQuery(r->done);
+            Slot* sl = r->slot;
+            const cudaError_t q = cudaEventQuery(sl->done);
             if (q == cudaErrorNotReady) {
                 ++k;
                 continue;
             }
             sv->active.erase(sv->active.begin() + k);
             int status = q == cudaSuccess ? SPECT_OK : SPECT_ECUDA;
-            if (status == SPECT_OK && r->plan && spect_plan_check(r->plan) != SPECT_OK) status = SPECT_ETIMEDOUT;
+            if (status == SPECT_OK && spect_plan_check(sl->plan) != SPECT_OK) status = SPECT_ETIMEDOUT;
             cudaGetLastError();
-            release_device(r);
+            sl->busy = false;
+            sl->req = nullptr;
+            r->slot = nullptr;
             finish(sv, r, status, status == SPECT_OK ? SPECT_REQ_DONE : SPECT_REQ_FAILED);
             retired = true;
         }
@@ -492,6 +581,8 @@ int spect_serve_destroy(spect_server* sv)
         sv->pinned.give(r->h_x);  // also the counts buffer (same allocation)
         delete r;
     }
+    for (Slot* sl : sv->slots) destroy_slot(sl);
+    sv->slots.clear();
     for (cudaStream_t s : sv->streams) cudaStreamDestroy(s);
     delete sv;
     return SPECT_OK;

@@ -226,7 +226,7 @@ int chunk_target(const spect_plan* p, long items)
 // projects to bitwise the same values alone or in a batch.  diag_blocks
 // (ratio mode only) receives per-block FP64 sums; *n_diag their count.
 int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, int n_sel, int batch, const float* y,
-                float s, double* diag_blocks, int* n_diag, cudaStream_t st)
+                float s, double* diag_blocks, int* n_diag, cudaStream_t st, const float* s_ptr = nullptr)
 {
     const PlaneTiling& t = p->tiling;
     const int chunks = chunk_target(p, (long)n_sel * (p->bf16 ? 1 : t.ntiles));
@@ -286,6 +286,7 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
         r.y = y;
         r.sel = sel_dev;
         r.s = s;
+        r.s_ptr = s_ptr;
         r.diag_blocks = (y && diag_blocks) ? diag_blocks : nullptr;
         const size_t total4 = (size_t)r.items * plane / 4;
         const int blocks = (int)std::max<size_t>(1, std::min<size_t>(kReduceBlocks, (total4 + 255) / 256));
@@ -393,6 +394,56 @@ int subset_of(const spect_plan* p, int subset, const int** sel_dev, int* n_sel)
     if (subset < 0 || subset >= p->M) return fail(SPECT_EINVAL, "subset %d out of range [-1, %d)", subset, p->M);
     *sel_dev = p->d_sel[subset];
     *n_sel = (int)p->subsets[subset].size();
+    return SPECT_OK;
+}
+
+int osem_core(spect_plan* plan, const float* y, float s, const float* s_dev, float* x_inout, int first_subiter,
+              int n_subiters, double* diag_dev, void* stream)
+{
+    if (int rc = check_plan(plan)) return rc;
+    if (!y || !x_inout) return fail(SPECT_EINVAL, "y and x_inout must be device pointers");
+    if (!aligned16(y) || !aligned16(x_inout)) return fail(SPECT_EINVAL, "y and x_inout must be 16-byte aligned");
+    if (first_subiter < 0 || n_subiters < 0) return fail(SPECT_EINVAL, "negative subiteration range");
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t vol = vol_elems(plan);
+    for (int t = first_subiter; t < first_subiter + n_subiters; ++t) {
+        const int m = t % plan->M;
+        const int ns = (int)plan->subsets[m].size();
+        int n_diag = 0;
+        int rc = run_forward(plan, x_inout, plan->d_ratio, plan->d_sel[m], ns, 1, y, s,
+                             diag_dev ? plan->d_diag_part : nullptr, &n_diag, st, s_dev);
+        if (rc) return rc;
+        if (diag_dev) {
+            cudaError_t e = timed(plan, "diag", st, 1, [&] {
+                return launch_diag_finalize(plan->d_diag_part, n_diag, diag_dev + 3 * (size_t)(t - first_subiter), st);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "diag kernel launch");
+        }
+        rc = run_back(plan, plan->d_ratio, x_inout, plan->d_sel[m], ns, 1, plan->d_sens + (size_t)m * vol, st);
+        if (rc) return rc;
+    }
+    return SPECT_OK;
+}
+
+// Attenuation cache A_a (T_att) from mu and the per-subset sensitivities
+// H_m^T 1 (compute_normalization_factor); queued on st.
+int refresh_mu(spect_plan* p, const float* mu_dev, cudaStream_t st)
+{
+    const size_t vol = vol_elems(p);
+    if (p->d_atten) {
+        cudaError_t e = timed(p, "attenuation", st, 1, [&] {
+            return launch_attenuation(mu_dev, p->d_cs, p->n, p->nz, p->na, p->geom.voxel_cm,
+                                      (p->geom.flags & SPECT_FLAG_ATTEN_F64) ? 1 : 0, p->d_atten, st);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "attenuation kernel");
+    }
+    for (int m = 0; m < p->M; ++m) {
+        const int rc = run_back(p, nullptr, p->d_sens + (size_t)m * vol, p->d_sel[m], (int)p->subsets[m].size(), 1,
+                                nullptr, st);
+        if (rc) return rc;
+    }
     return SPECT_OK;
 }
 
@@ -564,16 +615,8 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     for (int m = 0; m < p->M; ++m)
         SPECT_CK(cudaMemcpyAsync(p->d_sel[m], p->subsets[m].data(), p->subsets[m].size() * sizeof(int),
                                  cudaMemcpyHostToDevice, st), "copy subsets");
-    if (atten)
-        SPECT_CK(timed(p, "attenuation", st, 1, [&] {
-                     return launch_attenuation(mu_dev, p->d_cs, p->n, p->nz, p->na, g.voxel_cm,
-                                               (g.flags & SPECT_FLAG_ATTEN_F64) ? 1 : 0, p->d_atten, st);
-                 }), "attenuation kernel");
-    // sensitivities H_m^T 1 (compute_normalization_factor)
-    for (int m = 0; m < p->M; ++m) {
-        rc = run_back(p, nullptr, p->d_sens + (size_t)m * vol, p->d_sel[m], (int)p->subsets[m].size(), 1, nullptr, st);
-        if (rc) { cudaStreamSynchronize(st); free_plan(p); return rc; }
-    }
+    rc = refresh_mu(p, mu_dev, st);
+    if (rc) { cudaStreamSynchronize(st); free_plan(p); return rc; }
     SPECT_CK(cudaStreamSynchronize(st), "plan creation");
     SPECT_CK(cudaGetLastError(), "plan creation");
 #undef SPECT_CK
@@ -680,32 +723,25 @@ int spect_sensitivity(spect_plan* plan, int subset, float* out, void* stream)
 int spect_osem_run(spect_plan* plan, const float* y, float s, float* x_inout, int first_subiter, int n_subiters,
                    double* diag_dev, void* stream)
 {
-    if (int rc = check_plan(plan)) return rc;
-    if (!y || !x_inout) return fail(SPECT_EINVAL, "y and x_inout must be device pointers");
-    if (!aligned16(y) || !aligned16(x_inout)) return fail(SPECT_EINVAL, "y and x_inout must be 16-byte aligned");
-    if (first_subiter < 0 || n_subiters < 0) return fail(SPECT_EINVAL, "negative subiteration range");
     if (!std::isfinite(s) || s < 0.f) return fail(SPECT_EINVAL, "s must be finite and >= 0");
+    return osem_core(plan, y, s, nullptr, x_inout, first_subiter, n_subiters, diag_dev, stream);
+}
+
+int spect_osem_run_dev(spect_plan* plan, const float* y, const float* s_dev, float* x_inout, int first_subiter,
+                       int n_subiters, double* diag_dev, void* stream)
+{
+    if (!s_dev) return fail(SPECT_EINVAL, "s_dev must be a device pointer");
+    return osem_core(plan, y, 0.f, s_dev, x_inout, first_subiter, n_subiters, diag_dev, stream);
+}
+
+int spect_plan_set_mu(spect_plan* plan, const float* mu_dev, void* stream)
+{
+    if (int rc = check_plan(plan)) return rc;
+    if (plan->d_atten && (!mu_dev || !aligned16(mu_dev)))
+        return fail(SPECT_EINVAL, "the plan models attenuation: mu must be a 16-byte aligned device pointer");
     DeviceGuard guard(plan->device);
     if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t vol = vol_elems(plan);
-    for (int t = first_subiter; t < first_subiter + n_subiters; ++t) {
-        const int m = t % plan->M;
-        const int ns = (int)plan->subsets[m].size();
-        int n_diag = 0;
-        int rc = run_forward(plan, x_inout, plan->d_ratio, plan->d_sel[m], ns, 1, y, s,
-                             diag_dev ? plan->d_diag_part : nullptr, &n_diag, st);
-        if (rc) return rc;
-        if (diag_dev) {
-            cudaError_t e = timed(plan, "diag", st, 1, [&] {
-                return launch_diag_finalize(plan->d_diag_part, n_diag, diag_dev + 3 * (size_t)(t - first_subiter), st);
-            });
-            if (e != cudaSuccess) return cuda_fail(e, "diag kernel launch");
-        }
-        rc = run_back(plan, plan->d_ratio, x_inout, plan->d_sel[m], ns, 1, plan->d_sens + (size_t)m * vol, st);
-        if (rc) return rc;
-    }
-    return SPECT_OK;
+    return refresh_mu(plan, mu_dev, static_cast<cudaStream_t>(stream));
 }
 
 int spect_poisson_ll(spect_plan* plan, const float* y, const float* p, float s, size_t count, double* ll_dev,

@@ -41,7 +41,7 @@ EXPORTED = [
     "spect_forward", "spect_back", "spect_sensitivity", "spect_osem_run", "spect_poisson_ll",
     "spect_status_str", "spect_last_error", "spect_version",
     "spect_profile_enable", "spect_profile_read", "spect_kernel_launches",
-    "spect_poisson_ll_noalloc", "spect_plan_check",
+    "spect_poisson_ll_noalloc", "spect_plan_check", "spect_plan_set_mu", "spect_osem_run_dev",
     "spect_serve_create", "spect_serve_submit", "spect_serve_poll", "spect_serve_wait",
     "spect_serve_cancel", "spect_serve_stats_get", "spect_serve_destroy",
 ]
@@ -104,6 +104,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.spect_back.argtypes = [vp, vp, vp, i, i, vp]
         lib.spect_sensitivity.argtypes = [vp, i, vp, vp]
         lib.spect_osem_run.argtypes = [vp, vp, f, vp, i, i, vp, vp]
+        lib.spect_osem_run_dev.argtypes = [vp, vp, vp, vp, i, i, vp, vp]
+        lib.spect_plan_set_mu.argtypes = [vp, vp, vp]
         lib.spect_poisson_ll.argtypes = [vp, vp, vp, f, ctypes.c_size_t, vp, vp, vp]
         lib.spect_poisson_ll_noalloc.argtypes = [vp, vp, f, ctypes.c_size_t, vp, vp, vp]
         for name in ("spect_status_str",):
@@ -243,6 +245,16 @@ def spect_osem_run(plan: int, y: torch.Tensor, s: float, x: torch.Tensor, first_
                                  _dptr(diag, torch.float64), _stream(stream)))
 
 
+def spect_osem_run_dev(plan: int, y: torch.Tensor, s_dev: torch.Tensor, x: torch.Tensor, first_subiter: int,
+                       n_subiters: int, diag: Optional[torch.Tensor] = None, stream=None):
+    _check(load().spect_osem_run_dev(plan, _dptr(y), _dptr(s_dev), _dptr(x), first_subiter, n_subiters,
+                                     _dptr(diag, torch.float64), _stream(stream)))
+
+
+def spect_plan_set_mu(plan: int, mu: Optional[torch.Tensor], stream=None):
+    _check(load().spect_plan_set_mu(plan, _dptr(mu), _stream(stream)))
+
+
 def spect_poisson_ll(plan: int, y: torch.Tensor, p: torch.Tensor, s: float, ll: torch.Tensor,
                      grad: Optional[torch.Tensor] = None, stream=None):
     if y.numel() != p.numel() or (grad is not None and grad.numel() != p.numel()):
@@ -377,7 +389,7 @@ class _Request(ctypes.Structure):
 class _ServeStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "admitted", "completed", "failed", "cancelled",
                                                 "rejected", "queued", "active", "peak_active", "bytes_in_use",
-                                                "peak_bytes")] + \
+                                                "peak_bytes", "slots_created", "graph_slots")] + \
                [(k, ctypes.c_double) for k in ("p50_ms", "p99_ms", "max_ms", "recon_per_s")]
 
 

@@ -200,3 +200,22 @@ def test_bad_pointers_rejected(spect_lib, cuda):
         spect_lib.spect_forward(plan.handle, x[:4096], out, 5, 1)
     with pytest.raises(spect_lib.SpectError):
         spect_lib.spect_forward(plan.handle, x[:4096], out, 0, 0)
+
+
+def test_plan_reuse_with_new_mu_and_device_scatter(spect_lib, oracle_mod, cuda):
+    """spect_plan_set_mu equals a fresh plan bitwise; spect_osem_run_dev equals spect_osem_run."""
+    g = spect_lib.Geometry(n=40, nz=36, n_angles=12, n_subsets=3, psf_slope=0.1)
+    f1, mu1 = phantom_inputs(40, 36, 51)
+    f2, mu2 = phantom_inputs(40, 36, 52)
+    p1 = spect_lib.Plan(g, _t(mu1, cuda))
+    p2 = spect_lib.Plan(g, _t(mu2, cuda))
+    spect_lib.spect_plan_set_mu(p1.handle, _t(mu2, cuda))
+    x = _t(f2, cuda)
+    assert torch.equal(p1.forward(x), p2.forward(x))
+    assert torch.equal(p1.sensitivity(1), p2.sensitivity(1))
+    y = p2.forward(x) + 0.5
+    a = torch.ones((40, 40, 36), device=cuda)
+    b = torch.ones((40, 40, 36), device=cuda)
+    p2.osem(y, 0.25, a, 0, 5)
+    spect_lib.spect_osem_run_dev(p1.handle, y, torch.full((1,), 0.25, device=cuda), b, 0, 5)
+    assert torch.equal(a, b)
