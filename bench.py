@@ -74,6 +74,22 @@ def workload_desc(wl) -> dict:
 
 # ---------------------------------------------------------------- helpers
 
+def reduce_max(v: float, world: int, dist=None, device=None) -> float:
+    """Maximum of v over the ranks (the job's time is its slowest rank's)."""
+    if world == 1 or dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world: int, steps: int, units_per_step: int, ms_max: float) -> float:
+    """Whole-job units per second: every rank runs its own replica of the
+    workload (weak scaling), the time is the slowest rank's."""
+    return world * steps * units_per_step / (ms_max / 1e3)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -370,11 +386,7 @@ def run_libspect(args):
         return sum(e0.elapsed_time(e1) for e0, e1 in evs)
 
     def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, world, dist, dev)
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -387,13 +399,13 @@ def run_libspect(args):
     launches = spect.spect_kernel_launches() - launches0
     clk = clocks.stop()
     ms = max_over_ranks(ms)
-    value = world * args.steps * n_sub / (ms / 1e3)
+    value = replica_throughput(world, args.steps, n_sub, ms)
 
     # end to end through the C ABI with host buffers
     for _ in range(2):
         step_e2e()
     ms_e2e = max_over_ranks(timed(step_e2e, args.steps))
-    e2e = {"value": world * args.steps * n_sub / (ms_e2e / 1e3), "unit": UNIT,
+    e2e = {"value": replica_throughput(world, args.steps, n_sub, ms_e2e), "unit": UNIT,
            "h2d_bytes_per_step": int(y_host.numel() * 4), "d2h_bytes_per_step": int(x_host.numel() * 4)}
 
     # profiled pass: per-kernel CUDA-event durations on the launch stream
@@ -423,7 +435,7 @@ def run_libspect(args):
                 "plane_tiling": {k: plan.info()[k] for k in ("ztile", "n_ztiles", "threads", "smem_bytes")}}
 
     serving = None
-    if args.serve_requests > 0:
+    if args.serve_requests > 0 and world == 1:
         serving = run_serving(spect, dev, args)
 
     cpu = None
