@@ -27,6 +27,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -144,12 +145,47 @@ class ClockSampler:
 
 
 def measured_peaks() -> dict:
+    """HBM copy bandwidth and BF16 GEMM rate measured on this GPU type, and
+    the FP32 FMA peak derived from the unit count and the maximum clock:
+    SMs x 128 FP32 lanes x 2 flop x max SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as fh:
             d = json.load(fh)
-        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
-    return {"hbm_gbs": 6800.0, "source": "fallback"}
+        mhz = float(d.get("sm_max_mhz", 2070.0))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops_sustained": float(d["bf16_tflops_sustained"]),
+                "fp32_tflops": sms * 128 * 2 * mhz * 1e6 / 1e12, "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops_sustained": 1700.0, "fp32_tflops": sms * 128 * 2 * 2070e6 / 1e12,
+            "source": "fallback"}
+
+
+def psf_radii(wl) -> list:
+    """Per-plane PSF radius R_i = ceil(nsigma * (sigma0 + slope * d_i)),
+    d_i = n - i - 0.5 (as the plan builds its taps)."""
+    return [int(math.ceil(wl.nsigma * (wl.sigma0 + wl.slope * (wl.n - i - 0.5)))) for i in range(wl.n)]
+
+
+def algorithmic_flops(kernel: str, wl, n_sel: int) -> tuple:
+    """(flops, pipe) of one launch.  FP32 per voxel and angle: forward 7
+    (bilinear) + 1 (attenuation) + 2 (2R_i+1) (z blur) + 2 (2R_i+1) (y blur
+    and depth sum); back blur 4 (2R_i+1) + 1; gather 2 per bilinear weight,
+    4 weights per rotated sample, + 2 per voxel for the update.  BF16 path:
+    per plane two 128 x n x n GEMMs, each as three BF16 products (hi/lo
+    split), 2 flop per multiply-add, on the tensor pipe."""
+    plane = float(wl.n) * wl.nz
+    taps = [2 * r + 1 for r in psf_radii(wl)]
+    if kernel == "forward":
+        return n_sel * plane * sum(8 + 4 * t for t in taps), "fp32"
+    if kernel == "blur_back":
+        return n_sel * plane * sum(1 + 4 * t for t in taps), "fp32"
+    if kernel in ("gather_update", "gather"):
+        n3 = plane * wl.n
+        return n_sel * n3 * 8 + 2 * n3, "fp32"
+    if kernel in ("forward_bf16", "blur_back_bf16"):
+        return n_sel * wl.n * 2 * 3 * 2.0 * 128 * wl.n * wl.n, "tensor"
+    return 0.0, "fp32"
 
 
 def algorithmic_bytes(kernel: str, wl, n_sel: int) -> float:
@@ -419,20 +455,34 @@ def run_libspect(args):
     avg_s = tot_ms / n_launch / 1e3
     n_sel = -(-wl.n_angles // wl.n_subsets)
     nbytes = algorithmic_bytes(name, wl, n_sel)
+    flops, pipe = algorithmic_flops(name, wl, n_sel)
     peaks = measured_peaks()
-    achieved = nbytes / avg_s / 1e9
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic_%s.json" % wl.name)
+    tpath = os.path.join(ROOT, "profiles", "traffic_%s%s.json" % (wl.name, "_bf16" if bf16 else ""))
     if os.path.exists(tpath):
         with open(tpath) as fh:
             traffic = json.load(fh).get(name)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": name,
-                "peak_source": peaks["source"], "avg_launch_us": avg_s * 1e6,
-                "algorithmic_bytes_per_launch": nbytes,
-                "kernel_share": {k: round(v[1] / sum(t[1] for t in prof.values()), 4) for k, v in prof.items()},
-                "kernel_avg_us": {k: round(1e3 * v[1] / v[0], 2) for k, v in prof.items()},
-                "plane_tiling": {k: plan.info()[k] for k in ("ztile", "n_ztiles", "threads", "smem_bytes")}}
+    # the kernel's bound: the larger of its algorithmic HBM time and its
+    # arithmetic time at the measured / derived peaks
+    t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
+    fpeak = peaks["bf16_tflops_sustained"] if pipe == "tensor" else peaks["fp32_tflops"]
+    t_alu = flops / (fpeak * 1e12)
+    if t_hbm >= t_alu:
+        roofline = {"bound": "hbm", "achieved": nbytes / avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    else:
+        roofline = {"bound": "tensor" if pipe == "tensor" else "alu", "achieved": flops / avg_s / 1e12,
+                    "peak": fpeak, "unit": "TFLOP/s"}
+    roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    roofline.update({
+        "traffic": traffic, "kernel": name, "peak_source": peaks["source"] + (
+            " (FP32: SMs x 128 lanes x 2 flop x max clock)" if roofline["bound"] == "alu" else
+            " (BF16 sustained)" if roofline["bound"] == "tensor" else ""),
+        "avg_launch_us": avg_s * 1e6, "algorithmic_bytes_per_launch": nbytes, "algorithmic_flops_per_launch": flops,
+        "hbm_frac": nbytes / avg_s / 1e9 / peaks["hbm_gbs"], "alu_frac": flops / avg_s / 1e12 / fpeak,
+        "t_bound_frac": max(t_hbm, t_alu) / avg_s,
+        "kernel_share": {k: round(v[1] / sum(t[1] for t in prof.values()), 4) for k, v in prof.items()},
+        "kernel_avg_us": {k: round(1e3 * v[1] / v[0], 2) for k, v in prof.items()},
+        "plane_tiling": {k: plan.info()[k] for k in ("ztile", "n_ztiles", "threads", "smem_bytes")}})
 
     serving = None
     if args.serve_requests > 0 and world == 1:

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libspect.so")
-SOURCES = ["spect_api.cu", "plane_host.cu", "gather_kernel.cu", "misc_kernels.cu",
+SOURCES = ["spect_api.cu", "plane_host.cu", "gather_kernel.cu", "gather_tiled.cu", "misc_kernels.cu",
            "forward_ipt1.cu", "forward_ipt2.cu", "forward_ipt3.cu", "forward_ipt4.cu",
            "blur_back_ipt1.cu", "blur_back_ipt2.cu", "blur_back_ipt3.cu", "blur_back_ipt4.cu",
            "noalloc.cu", "psf_bf16.cu", "serve.cu"]
@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [cc, *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

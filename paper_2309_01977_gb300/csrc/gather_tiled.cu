@@ -1,0 +1,331 @@
+// Transpose of the bilinear rotation (T_rot^T of Eq. 1), tiled: the same
+// sums as gather_kernel, with the rotated-frame rows that a tile of output
+// columns needs staged in shared memory by bulk copies.
+//
+// Output columns q = (x, y) are grouped in T x T tiles.  For angle a, the
+// footprint of a tile is the set of rotated-frame rows p = (i, j) with a
+// nonzero bilinear weight toward some column of the tile; for each i it is
+// held as the whole run j in [jlo_i, jlo_i + len_i), which is contiguous in
+// the rotated-frame volume B_a[i][j][z].  The plan stores, per (angle,
+// tile):
+//   a descriptor  {i0, ni, rows} and (jlo_i, len_i) for i = i0 .. i0+ni-1;
+//   per column of the tile, up to kMaxCand (row of the footprint in its
+//   shared-memory copy, weight) entries, in the order of gather_kernel's
+//   table (rotated row i, then j), with the weights recomputed by the
+//   forward's own arithmetic, so the sums are bitwise those of gather_kernel.
+// The gather CTA of (tile, z segment, batch entry) walks the subset's
+// angles through `stages` footprint buffers: while it sums angle g, the
+// bulk copies of the next angles fill the other buffers.  Every wait is
+// bounded.
+#include <cuda_runtime.h>
+
+#include "async_copy.cuh"
+#include "geometry.cuh"
+#include "internal.h"
+
+namespace spect {
+
+// ---------------------------------------------------------------- tables
+
+// One CTA per (tile, angle), one thread per column of the tile.
+__global__ void gather_tiled_table_kernel(const float2* __restrict__ cs_tab, int n, int nz, int T, int tiles_x,
+                                          int2* __restrict__ tab, int* __restrict__ desc, int* __restrict__ rows_max,
+                                          int* __restrict__ err)
+{
+    __shared__ int s_imin, s_imax;
+    __shared__ int s_jlo[kFpMaxRows], s_jhi[kFpMaxRows], s_off[kFpMaxRows];
+    const int tile = blockIdx.x, angle = blockIdx.y;
+    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const int cl = threadIdx.x;
+    const int x = tx * T + cl / T, y = ty * T + cl % T;
+    const bool live = cl < T * T && x < n && y < n;
+    if (threadIdx.x == 0) {
+        s_imin = 1 << 30;
+        s_imax = -1;
+    }
+    for (int r = threadIdx.x; r < kFpMaxRows; r += blockDim.x) {
+        s_jlo[r] = 1 << 30;
+        s_jhi[r] = -1;
+    }
+    __syncthreads();
+
+    // candidates of this column, enumerated exactly as gather_table_kernel
+    int ci[kMaxCand], cj[kMaxCand], cw[kMaxCand];
+    int count = 0;
+    if (live) {
+        const float c = 0.5f * (float)(n - 1);
+        const float2 cs = cs_tab[angle];
+        const float dx = (float)x - c, dy = (float)y - c;
+        const float pi = c + cs.x * dx + cs.y * dy;
+        const float pj = c - cs.y * dx + cs.x * dy;
+        const float ext = fabsf(cs.x) + fabsf(cs.y) + 1e-3f;
+        const int ia = max(0, (int)ceilf(pi - ext)), ib = min(n - 1, (int)floorf(pi + ext));
+        const int ja = max(0, (int)ceilf(pj - ext)), jb = min(n - 1, (int)floorf(pj + ext));
+        for (int i = ia; i <= ib; ++i)
+            for (int j = ja; j <= jb; ++j) {
+                float u, v;
+                sample_point(cs.x, cs.y, c, i, j, u, v);
+                const float fu = floorf(u), fv = floorf(v);
+                const int xa = (int)fu, ya = (int)fv;
+                const float ax = u - fu, by = v - fv;
+                const float wx = (x == xa) ? (1.f - ax) : (x == xa + 1 ? ax : 0.f);
+                const float wy = (y == ya) ? (1.f - by) : (y == ya + 1 ? by : 0.f);
+                if (wx != 0.f && wy != 0.f && count < kMaxCand) {
+                    ci[count] = i;
+                    cj[count] = j;
+                    cw[count] = __float_as_int(wx * wy);
+                    ++count;
+                }
+            }
+    }
+    for (int e = 0; e < count; ++e) {
+        atomicMin(&s_imin, ci[e]);
+        atomicMax(&s_imax, ci[e]);
+    }
+    __syncthreads();
+    const int i0 = s_imin <= s_imax ? s_imin : 0;
+    const int ni = s_imin <= s_imax ? s_imax - s_imin + 1 : 0;
+    const bool fits = ni <= kFpMaxRows;
+    for (int e = 0; e < count && fits; ++e) {
+        atomicMin(&s_jlo[ci[e] - i0], cj[e]);
+        atomicMax(&s_jhi[ci[e] - i0], cj[e]);
+    }
+    __syncthreads();
+    int* d = desc + ((size_t)angle * gridDim.x + tile) * kFpDescInts;
+    if (threadIdx.x == 0) {
+        int rows = 0;
+        for (int r = 0; r < (fits ? ni : 0); ++r) {
+            const int len = s_jhi[r] >= s_jlo[r] ? s_jhi[r] - s_jlo[r] + 1 : 0;
+            s_off[r] = rows;
+            d[4 + 2 * r] = len ? s_jlo[r] : 0;
+            d[5 + 2 * r] = len;
+            rows += len;
+        }
+        d[0] = i0;
+        d[1] = fits ? ni : 0;
+        d[2] = rows;
+        d[3] = 0;
+        atomicMax(rows_max, rows);
+        if (!fits) atomicExch(err, SPECT_EINVAL);
+    }
+    __syncthreads();
+    if (cl < T * T) {
+        int2* out = tab + (((size_t)angle * gridDim.x + tile) * (T * T) + cl) * kMaxCand;
+        for (int e = 0; e < kMaxCand; ++e) {
+            if (e < count && fits)
+                out[e] = make_int2(s_off[ci[e] - i0] + cj[e] - s_jlo[ci[e] - i0], cw[e]);
+            else
+                out[e] = make_int2(0, 0);
+        }
+    }
+}
+
+cudaError_t launch_gather_tiled_tables(const float2* cs, int n, int nz, int n_angles, int T, int2* tab, int* desc,
+                                       int* rows_max, int* err, cudaStream_t st)
+{
+    const int tiles_x = (n + T - 1) / T;
+    dim3 grid(tiles_x * tiles_x, n_angles);
+    gather_tiled_table_kernel<<<grid, ((T * T + 31) / 32) * 32, 0, st>>>(cs, n, nz, T, tiles_x, tab, desc, rows_max,
+                                                                          err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- gather
+
+namespace {
+
+// Warp 0 fills buffer `buf` for one angle: lane 0 announces the bytes on
+// `bar` and copies the tile's table slice (after the footprint rows, at row
+// rows_cap); lane l copies footprint row-run l (and l + 32, ...).  zs == nz:
+// one copy per run of rows (contiguous); else one copy per row of the z
+// segment [z0, z0 + zs).
+__device__ __forceinline__ void issue_footprint(const GatherTiledArgs& a, const int* __restrict__ d,
+                                                const int2* __restrict__ tab, const float* __restrict__ bslot,
+                                                uint32_t buf, uint32_t bar)
+{
+    const int lane = threadIdx.x & 31;
+    const int i0 = __ldg(d + 0), ni = __ldg(d + 1), rows = __ldg(d + 2);
+    const int z0 = blockIdx.z * a.zs;
+    const uint32_t row_bytes = (uint32_t)a.zs * 4u;
+    const uint32_t tab_bytes = (uint32_t)(a.T * a.T * kMaxCand) * 8u;
+    if (lane == 0) {
+        mbar_expect_tx(bar, (uint32_t)rows * row_bytes + tab_bytes);
+        bulk_load(buf + (uint32_t)a.rows_cap * row_bytes, tab, tab_bytes, bar);
+    }
+    __syncwarp();
+    // offsets of the runs: exclusive prefix of the lengths over the warp
+    int off = 0;
+    for (int r0 = 0; r0 < ni; r0 += 32) {
+        const int r = r0 + lane;
+        const int jlo = r < ni ? __ldg(d + 4 + 2 * r) : 0;
+        const int len = r < ni ? __ldg(d + 5 + 2 * r) : 0;
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int start = off + incl - len;
+        if (len > 0) {
+            const float* src = bslot + ((size_t)(i0 + r) * a.n + jlo) * a.nz + z0;
+            if (a.zs == a.nz) {
+                bulk_load(buf + (uint32_t)start * row_bytes, src, (uint32_t)len * row_bytes, bar);
+            } else {
+                for (int q = 0; q < len; ++q)
+                    bulk_load(buf + (uint32_t)(start + q) * row_bytes, src + (size_t)q * a.nz, row_bytes, bar);
+            }
+        }
+        off += __shfl_sync(0xffffffffu, incl, 31);
+    }
+}
+
+}  // namespace
+
+// 256 threads: warp w sums columns w, w + 8, ... of the T x T tile; lane l
+// holds float4 l of the z segment (lanes past zs/4 idle).
+template <int T>
+__global__ void __launch_bounds__(kGatherTiledThreads) gather_tiled_kernel(GatherTiledArgs a)
+{
+    extern __shared__ __align__(16) float4 gsm[];
+    const int tile = blockIdx.x, b = blockIdx.y;
+    const int tiles_x = (a.n + T - 1) / T;
+    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int zw = a.zs >> 2;  // float4 per row segment
+    const int z0 = blockIdx.z * a.zs;
+    const size_t vol = (size_t)a.n * a.n * a.nz;
+    constexpr int ncols = T * T;
+    constexpr int kCols = (ncols + 7) / 8;  // columns per warp
+    const size_t buf_f4 = (size_t)a.rows_cap * zw + (size_t)T * T * kMaxCand / 2;  // rows, then the table
+    const int S = a.stages;  // footprint buffers: angle g uses buffer g % S
+    float4* bufs = gsm;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gsm + S * buf_f4);
+    const float* bvol_b = a.bvol + (size_t)b * a.n_sel * vol;
+    const size_t tab_stride = (size_t)a.n_tiles * ncols * kMaxCand;  // per angle
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < S; ++q) mbar_init(smem_u32(bars + q), 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    auto issue = [&](int g) {
+        const int q = g % S;
+        issue_footprint(a, a.desc + ((size_t)a.sel[g] * a.n_tiles + tile) * kFpDescInts,
+                        a.tab + (size_t)a.sel[g] * tab_stride + (size_t)tile * ncols * kMaxCand,
+                        bvol_b + (size_t)g * vol, smem_u32(bufs + q * buf_f4), smem_u32(bars + q));
+    };
+    if (warp == 0)
+        for (int g = 0; g < S - 1 && g < a.n_sel; ++g) issue(g);
+
+    float4 acc[kCols];
+#pragma unroll
+    for (int k = 0; k < kCols; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool ok = true;
+    int g = 0;
+    for (; g < a.n_sel; ++g) {
+        // buffer (g + S - 1) % S was last read by angle g - 1, before the
+        // barrier that ended it
+        if (warp == 0 && g + S - 1 < a.n_sel) {
+            fence_async_smem();
+            issue(g + S - 1);
+        }
+        const int q = g % S;
+        const bool landed = mbar_wait(smem_u32(bars + q), (uint32_t)((g / S) & 1));
+        const float4* buf = bufs + q * buf_f4;
+        const int2* tab = reinterpret_cast<const int2*>(buf + (size_t)a.rows_cap * zw);
+#pragma unroll
+        for (int k = 0; k < kCols; ++k) {
+            const int cl = warp + 8 * k;
+            if (landed && cl < ncols) {
+                // the column's entries, one per lane, then broadcast in order
+                const int2 ent = lane < kMaxCand ? tab[cl * kMaxCand + lane] : make_int2(0, 0);
+#pragma unroll
+                for (int e = 0; e < kMaxCand; ++e) {
+                    const int row = __shfl_sync(0xffffffffu, ent.x, e);
+                    const int wb = __shfl_sync(0xffffffffu, ent.y, e);
+                    if (wb != 0 && lane < zw) {
+                        const float w = __int_as_float(wb);
+                        const float4 v = buf[(size_t)row * zw + lane];
+                        const float2 lo = __ffma2_rn(make_float2(w, w), make_float2(v.x, v.y),
+                                                     make_float2(acc[k].x, acc[k].y));
+                        const float2 hi = __ffma2_rn(make_float2(w, w), make_float2(v.z, v.w),
+                                                     make_float2(acc[k].z, acc[k].w));
+                        acc[k] = make_float4(lo.x, lo.y, hi.x, hi.y);
+                    }
+                }
+            }
+        }
+        ok = __syncthreads_and(landed);  // and buffer q is free for angle g + S
+        if (!ok) break;
+    }
+    if (!ok) {
+        // a timed-out wait: record it, and give the copies in flight (angles
+        // g .. g + S - 2) one more bounded wait before the CTA's shared memory
+        // goes away
+        if (threadIdx.x == 0) atomicExch(a.err, SPECT_ETIMEDOUT);
+        for (int h = g; h < g + S - 1 && h < a.n_sel; ++h) mbar_wait(smem_u32(bars + h % S), (uint32_t)((h / S) & 1));
+        return;
+    }
+
+    // epilogue: store, accumulate, or the fused OSEM update
+#pragma unroll
+    for (int k = 0; k < kCols; ++k) {
+        const int cl = warp + 8 * k;
+        const int x = tx * T + cl / T, y = ty * T + cl % T;
+        if (cl < ncols && x < a.n && y < a.n && lane < zw) {
+            const size_t col = (size_t)x * a.n + y;
+            float4* o = reinterpret_cast<float4*>(a.out + (size_t)b * vol + col * a.nz + z0) + lane;
+            const float4 s4 = acc[k];
+            if (a.sens) {
+                const float4 sv = __ldg(reinterpret_cast<const float4*>(a.sens + col * a.nz + z0) + lane);
+                float4 f = *o;
+                f.x = sv.x > 0.f ? f.x * s4.x / sv.x : f.x;
+                f.y = sv.y > 0.f ? f.y * s4.y / sv.y : f.y;
+                f.z = sv.z > 0.f ? f.z * s4.z / sv.z : f.z;
+                f.w = sv.w > 0.f ? f.w * s4.w / sv.w : f.w;
+                *o = f;
+            } else if (a.accumulate) {
+                float4 f = *o;
+                f.x += s4.x;
+                f.y += s4.y;
+                f.z += s4.z;
+                f.w += s4.w;
+                *o = f;
+            } else {
+                *o = s4;
+            }
+        }
+    }
+}
+
+size_t gather_tiled_smem(int rows_cap, int zs, int T, int stages)
+{
+    return stages * ((size_t)rows_cap * zs * sizeof(float) + (size_t)T * T * kMaxCand * sizeof(int2) + 8);
+}
+
+template <int T>
+cudaError_t launch_gather_tiled_t(const GatherTiledArgs& a, cudaStream_t st)
+{
+    static unsigned long long mask = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (!(mask & (1ull << (dev & 63)))) {
+        int optin = 0;
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(gather_tiled_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        if (e != cudaSuccess) return e;
+        mask |= 1ull << (dev & 63);
+    }
+    dim3 grid(a.n_tiles, a.batch, a.nz / a.zs);
+    gather_tiled_kernel<T><<<grid, kGatherTiledThreads, gather_tiled_smem(a.rows_cap, a.zs, T, a.stages), st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_tiled(const GatherTiledArgs& a, cudaStream_t st)
+{
+    return a.T == 8 ? launch_gather_tiled_t<8>(a, st) : launch_gather_tiled_t<4>(a, st);
+}
+
+}  // namespace spect

@@ -22,18 +22,25 @@ constexpr int kMaxIpt = 4;           // largest j-blur strips per thread
 
 
 // Shape of one plane-blur launch: which columns of z a CTA owns and the
-// shared-memory layout of its two plane buffers.
+// shared-memory layout of its buffers.
 struct PlaneTiling {
     int ktile;    // output columns per z tile (multiple of kStrip unless it is nz)
     int ntiles;   // z tiles
-    int rh;       // halo = largest PSF radius of the plan
+    int rh;       // halo = largest PSF radius of the plan, rounded up to even
     int ktpad;    // ktile rounded up to kStrip
     int npad;     // n rounded up to kStrip
-    int wp;       // P row stride (odd): ktpad + 2*rh (+1)
-    int qs;       // transposed Q row stride (odd): npad + 2*rh (+1); ktpad rows
+    int sp;       // P stride between row pairs, in 16-byte quads (odd): >= (ktpad + 2*rh) / 2
+    int sq;       // Q stride between column pairs, in quads (odd): >= (npad + 2*rh) / 2
     int threads;  // CTA size (multiple of 32, <= kFwdThreads)
     int ipt;      // j-blur strips per thread (1..kMaxIpt)
-    size_t smem;  // dynamic shared memory bytes
+    size_t smem;  // P, Q, the forward's tap-row table and the tap buffer, bytes
+    // Attenuation planes staged in shared memory by bulk copies, one plane
+    // ahead: row width in floats (0 when the buffer does not fit and A is
+    // read from global memory), and byte offsets of the tap buffer, the
+    // attenuation buffer and its mbarrier; per kernel (f: forward, b: back).
+    int a_cols_f, off_taps_f, off_a_f, off_bar_f;
+    int a_cols_b, off_taps_b, off_a_b, off_bar_b;
+    size_t smem_f, smem_b;  // dynamic shared memory of each kernel
 };
 
 struct ForwardArgs {
@@ -42,12 +49,14 @@ struct ForwardArgs {
     const float2* cs;      // [n_angles] (cos, sin)
     const float* taps;     // [n][kTapW] centred at kMaxR
     const int* rad;        // [n]
+    const int* work;       // [n+1] prefix sums of the per-plane work estimate
     const int* sel;        // [n_sel] angle ids
     int n, nz, n_sel, batch;
-    int chunks;            // depth chunks: chunk c takes planes c, c + chunks, ...
+    int chunks;            // depth chunks: contiguous plane ranges of equal work
     PlaneTiling t;
     float* out;            // [batch][n_sel][n][nz] raw depth sums when partials == nullptr
     float* partials;       // else [batch*n_sel*chunks][n][nz] per-chunk sums
+    int* err;              // SPECT_ETIMEDOUT when a bounded wait runs out
 };
 
 // Sum of the depth-chunk partials in chunk order, and optionally the OSEM
@@ -71,11 +80,13 @@ struct BlurBackArgs {
     const float* atten;    // [n_angles][n][n][nz] or nullptr
     const float* taps;
     const int* rad;
+    const int* work;       // [n+1] prefix sums of the per-plane work estimate
     const int* sel;        // [n_sel] angle ids
     int n, nz, n_sel, batch;
-    int chunks;            // depth chunks: chunk c takes planes c, c + chunks, ...
+    int chunks;            // depth chunks: contiguous plane ranges of equal work
     PlaneTiling t;
     float* bvol;           // [batch][n_sel][n][n][nz] rotated-frame volumes A . (K_i r)
+    int* err;              // SPECT_ETIMEDOUT when a bounded wait runs out
 };
 
 struct GatherArgs {
@@ -87,6 +98,28 @@ struct GatherArgs {
     float* out;            // [batch][n][n][nz]
     int accumulate;        // add into out instead of overwriting
     const float* sens;     // OSEM update: x <- sens>0 ? x*bp/sens : x (x is `out`)
+};
+
+// Tiled gather (gather_tiled.cu): T x T output columns per CTA, footprint
+// rows of each angle staged in shared memory by bulk copies.
+constexpr int kFpMaxRows = 32;                    // rotated rows i per footprint
+constexpr int kFpDescInts = 4 + 2 * kFpMaxRows;   // {i0, ni, rows, 0}, then (jlo, len) per i
+constexpr int kGatherTiledThreads = 256;
+
+struct GatherTiledArgs {
+    const float* bvol;     // [batch][n_sel][n][n][nz]
+    const int2* tab;       // [n_angles][n_tiles][T*T][kMaxCand] (footprint row, weight bits)
+    const int* desc;       // [n_angles][n_tiles][kFpDescInts]
+    const int* sel;        // [n_sel] angle ids
+    int n, nz, n_sel, batch;
+    int T, n_tiles;        // tile side (4 or 8), tiles
+    int zs;                // z segment per CTA (divides nz, multiple of 4, <= 128)
+    int rows_cap;          // largest footprint, rows
+    int stages;            // footprint buffers (angles in flight + 1)
+    float* out;            // [batch][n][n][nz]
+    int accumulate;
+    const float* sens;     // OSEM update, as GatherArgs
+    int* err;
 };
 
 // Tensor-core PSF path (SPECT_FLAG_PSF_BF16): n % 32 == 0, n <= 128,
@@ -123,11 +156,15 @@ size_t bf16_smem_bytes(int n);
 uint32_t bf16_tmem_cols(int n);
 int bf16_occupancy(int n);
 
-PlaneTiling plane_tiling(int n, int nz, int rh, size_t cap1, size_t cap2);
+PlaneTiling plane_tiling(int n, int nz, int rmax, size_t cap, size_t limit);
 cudaError_t launch_forward(const ForwardArgs& a, int grid_x, cudaStream_t st);
 cudaError_t launch_blur_back(const BlurBackArgs& a, int grid_x, cudaStream_t st);
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t st);
 cudaError_t launch_gather_tables(const float2* cs, int n, int nz, int n_angles, int2* tab, cudaStream_t st);
+cudaError_t launch_gather_tiled_tables(const float2* cs, int n, int nz, int n_angles, int T, int2* tab, int* desc,
+                                       int* rows_max, int* err, cudaStream_t st);
+cudaError_t launch_gather_tiled(const GatherTiledArgs& a, cudaStream_t st);
+size_t gather_tiled_smem(int rows_cap, int zs, int T, int stages);
 int forward_max_blocks_per_sm(const PlaneTiling& t);
 
 // Per-IPT instantiations (one translation unit each, compiled in parallel).
@@ -173,7 +210,12 @@ struct spect_plan {
     float* d_sens = nullptr;                  // [M][vol]
     float* d_partials = nullptr;              // forward depth-chunk partials
     size_t partial_planes = 0;
-    int2* d_gtab = nullptr;                   // [na][n*n][kMaxCand] adjoint-rotation gather tables
+    int2* d_gtab = nullptr;                   // adjoint-rotation gather tables: [na][n*n][kMaxCand], or
+                                              // tiled [na][gt_tiles][gt_T^2][kMaxCand]
+    int* d_gdesc = nullptr;                   // tiled gather footprints [na][gt_tiles][kFpDescInts]
+    int* d_gwork = nullptr;                   // tiled gather: largest footprint (rows)
+    bool gather_tiled = false;                // footprints staged in shared memory
+    int gt_T = 0, gt_tiles = 0, gt_zs = 0, gt_rows = 0, gt_stages = 2;
     bool bf16 = false;                        // tensor-core PSF path
     uint16_t* d_ttab = nullptr;               // [n][2][128*128] BF16 Toeplitz tiles (hi, lo)
     int* d_err = nullptr;                     // kernel status word (bounded waits)

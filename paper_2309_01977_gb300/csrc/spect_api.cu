@@ -263,6 +263,7 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
             a.cs = p->d_cs;
             a.taps = p->d_taps;
             a.rad = p->d_rad;
+            a.work = p->d_rad + p->n;  // forward work prefix
             a.sel = sel_dev;
             a.n = p->n;
             a.nz = p->nz;
@@ -272,6 +273,7 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
             a.t = t;
             a.out = out + (size_t)b0 * n_sel * plane;
             a.partials = use_partials ? p->d_partials : nullptr;
+            a.err = p->d_err;
             e = timed(p, "forward", st, 1, [&] { return launch_forward(a, chunks * t.ntiles, st); });
         }
         if (e != cudaSuccess) return cuda_fail(e, "forward kernel launch");
@@ -339,6 +341,7 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
                 bb.atten = p->d_atten;
                 bb.taps = p->d_taps;
                 bb.rad = p->d_rad;
+                bb.work = p->d_rad + 2 * p->n + 1;  // blur_back work prefix
                 bb.sel = sel_dev + g0;
                 bb.n = p->n;
                 bb.nz = p->nz;
@@ -348,9 +351,33 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
                 const int chunks = chunk_target(p, (long)nb * ng * p->tiling.ntiles);
                 bb.chunks = chunks;
                 bb.bvol = p->d_bvol;
+                bb.err = p->d_err;
                 e = timed(p, "blur_back", st, 1, [&] { return launch_blur_back(bb, chunks * p->tiling.ntiles, st); });
             }
             if (e != cudaSuccess) return cuda_fail(e, "blur_back kernel launch");
+            if (p->gather_tiled) {
+                GatherTiledArgs gt{};
+                gt.bvol = p->d_bvol;
+                gt.tab = p->d_gtab;
+                gt.desc = p->d_gdesc;
+                gt.sel = sel_dev + g0;
+                gt.n = p->n;
+                gt.nz = p->nz;
+                gt.n_sel = ng;
+                gt.batch = nb;
+                gt.T = p->gt_T;
+                gt.n_tiles = p->gt_tiles;
+                gt.zs = p->gt_zs;
+                gt.rows_cap = p->gt_rows;
+                gt.stages = p->gt_stages;
+                gt.out = out_b;
+                gt.accumulate = g0 > 0;
+                gt.sens = fused ? sens_update : nullptr;
+                gt.err = p->d_err;
+                e = timed(p, gt.sens ? "gather_update" : "gather", st, 1, [&] { return launch_gather_tiled(gt, st); });
+                if (e != cudaSuccess) return cuda_fail(e, "gather kernel launch");
+                continue;
+            }
             GatherArgs ga{};
             ga.bvol = p->d_bvol;
             ga.tab = p->d_gtab;
@@ -547,13 +574,11 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     for (int a = 0; a < p->na; ++a) p->subsets[a % p->M].push_back(a);
     for (auto& s : p->subsets) p->max_subset = std::max(p->max_subset, (int)s.size());
 
-    int smem_optin = 0, smem_sm = 0;
+    int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device);
     // leave room for the 1 KB the hardware reserves per CTA and static shared memory
     const size_t cap1 = (size_t)std::min(smem_optin, 227 * 1024) - 2048;
-    const size_t cap2 = (size_t)smem_sm / 2 - 2048;
-    p->tiling = plane_tiling(p->n, p->nz, p->rmax, cap1, cap2);
+    p->tiling = plane_tiling(p->n, p->nz, p->rmax, cap1, (size_t)smem_optin);
     if (p->tiling.smem == 0) { free_plan(p); return fail(SPECT_EINVAL, "plane %dx%d too large for shared memory", p->n, p->nz); }
     p->bf16 = (g.flags & SPECT_FLAG_PSF_BF16) != 0;
     p->fwd_occ = p->bf16 ? bf16_occupancy(p->n) : std::max(1, forward_max_blocks_per_sm(p->tiling));
@@ -564,11 +589,11 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     p->bvol_cap = (size_t)std::max(p->max_subset, 16);
     if ((rc = dev_alloc(p, &p->d_cs, p->na)) ||
         (rc = dev_alloc(p, &p->d_taps, taps.size())) ||
-        (rc = dev_alloc(p, &p->d_rad, (size_t)p->n)) ||
+        (rc = dev_alloc(p, &p->d_rad, (size_t)3 * p->n + 2)) ||
         (rc = dev_alloc(p, &p->d_sel_all, (size_t)p->na)) ||
         (rc = dev_alloc(p, &p->d_sens, (size_t)p->M * vol)) ||
         (rc = dev_alloc(p, &p->d_partials, p->partial_planes * plane)) ||
-        (rc = dev_alloc(p, &p->d_gtab, (size_t)p->na * p->n * p->n * kMaxCand)) ||
+        (rc = dev_alloc(p, &p->d_gwork, 1)) ||
         (rc = dev_alloc(p, &p->d_bvol, p->bvol_cap * vol)) ||
         (rc = dev_alloc(p, &p->d_ratio, (size_t)p->max_subset * plane)) ||
         (rc = dev_alloc(p, &p->d_bp, vol)) ||
@@ -608,10 +633,64 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
         SPECT_CK(cudaMemcpyAsync(p->d_ttab, ttab.data(), ttab.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st),
                  "copy Toeplitz tiles");
     SPECT_CK(cudaMemcpyAsync(p->d_taps, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice, st), "copy taps");
-    SPECT_CK(cudaMemcpyAsync(p->d_rad, rad.data(), rad.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy radii");
+    // radii, then per kernel the prefix sums of a per-plane work estimate
+    // for the depth chunks: a fixed cost per plane (staging, barriers,
+    // attenuation loads) plus a cost per tap, in the ratios measured on
+    // GB300 with per-CTA timers: about 43 taps' worth per plane for the
+    // forward and 27 for the back blur
+    std::vector<int> radw(3 * (size_t)p->n + 2, 0);
+    int* wf = radw.data() + p->n;
+    int* wb = wf + p->n + 1;
+    for (int i = 0; i < p->n; ++i) {
+        radw[i] = rad[i];
+        wf[i + 1] = wf[i] + 43 + (2 * rad[i] + 1);
+        wb[i + 1] = wb[i] + 27 + (2 * rad[i] + 1);
+    }
+    SPECT_CK(cudaMemcpyAsync(p->d_rad, radw.data(), radw.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy radii");
     SPECT_CK(cudaMemcpyAsync(p->d_sel_all, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy angles");
-    SPECT_CK(timed(p, "gather_tables", st, 1, [&] { return launch_gather_tables(p->d_cs, p->n, p->nz, p->na, p->d_gtab, st); }),
-             "gather table kernel");
+    // Gather tables.  Tiled (footprints staged in shared memory) for planes
+    // of at least 128 x 128 with nz <= 128 (smaller planes are faster with
+    // the per-column gather): 8 x 8 tiles, whole columns (each run of
+    // footprint rows is one contiguous copy) and two footprint buffers (one
+    // angle in flight; a third buffer measured slower on GB300).
+    p->gather_tiled = p->n >= 128 && p->nz <= 128;
+    if (p->gather_tiled) {
+        p->gt_T = 8;
+        const int tx = (p->n + p->gt_T - 1) / p->gt_T;
+        p->gt_tiles = tx * tx;
+        if ((rc = dev_alloc(p, &p->d_gtab, (size_t)p->na * p->gt_tiles * p->gt_T * p->gt_T * kMaxCand)) ||
+            (rc = dev_alloc(p, &p->d_gdesc, (size_t)p->na * p->gt_tiles * kFpDescInts))) {
+            free_plan(p);
+            return rc;
+        }
+        SPECT_CK(cudaMemsetAsync(p->d_gwork, 0, sizeof(int), st), "clear footprint size");
+        SPECT_CK(timed(p, "gather_tables", st, 1, [&] {
+                     return launch_gather_tiled_tables(p->d_cs, p->n, p->nz, p->na, p->gt_T, p->d_gtab, p->d_gdesc,
+                                                       p->d_gwork, p->d_err, st);
+                 }),
+                 "gather table kernel");
+        int rows = 0, err = 0;
+        SPECT_CK(cudaMemcpyAsync(&rows, p->d_gwork, sizeof(int), cudaMemcpyDeviceToHost, st), "read footprint size");
+        SPECT_CK(cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "read status");
+        SPECT_CK(cudaStreamSynchronize(st), "gather tables");
+        p->gt_rows = std::max(rows, 1);
+        p->gt_zs = p->nz;
+        p->gt_stages = 2;
+        if (err != 0 || gather_tiled_smem(p->gt_rows, p->gt_zs, p->gt_T, 2) > (size_t)smem_optin) {
+            // footprints too large for shared memory: the per-column gather
+            p->gather_tiled = false;
+            SPECT_CK(cudaMemsetAsync(p->d_err, 0, sizeof(int), st), "clear status");
+        }
+    }
+    if (!p->gather_tiled) {
+        if ((rc = dev_alloc(p, &p->d_gtab, (size_t)p->na * p->n * p->n * kMaxCand))) {
+            free_plan(p);
+            return rc;
+        }
+        SPECT_CK(timed(p, "gather_tables", st, 1,
+                       [&] { return launch_gather_tables(p->d_cs, p->n, p->nz, p->na, p->d_gtab, st); }),
+                 "gather table kernel");
+    }
     for (int m = 0; m < p->M; ++m)
         SPECT_CK(cudaMemcpyAsync(p->d_sel[m], p->subsets[m].data(), p->subsets[m].size() * sizeof(int),
                                  cudaMemcpyHostToDevice, st), "copy subsets");
