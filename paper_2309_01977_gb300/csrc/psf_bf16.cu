@@ -27,6 +27,7 @@
 
 #include <cstdint>
 
+#include "async_copy.cuh"
 #include "geometry.cuh"
 #include "internal.h"
 
@@ -37,12 +38,6 @@ namespace {
 constexpr int kTcThreads = 512;                 // 16 warps: 4 TMEM lane quadrants x 4 column parts
 constexpr int kTcM = 128;                       // MMA M = axial size padded to 128
 constexpr int kTile = kTcM * kTcM * 2;          // one 128x128 BF16 tile, bytes
-constexpr long long kWaitCycles = 4000000000LL; // bounded mbarrier waits (~2 s)
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
 
 // K-major operand tiles with the 128-byte swizzle: rows of 64 BF16 (128 B);
 // 8 rows form a 1 KB atom in which 16-byte chunk c of row r is stored at
@@ -80,35 +75,6 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
-{
-    const long long t0 = clock64();
-    for (;;) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
-    }
-}
-
-__device__ __forceinline__ void tma_load_1d(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -248,7 +214,7 @@ __device__ __forceinline__ bool tc_setup(TcState& st, unsigned char* smem, int n
         mbar_init(st.s.bar_t, 1);
         mbar_init(st.s.bar_1, 1);
         mbar_init(st.s.bar_2, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_init_fence();
     }
     if ((threadIdx.x >> 5) == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(st.tmem_slot)),
@@ -337,44 +303,58 @@ __device__ __forceinline__ void put4(uint32_t b1, uint32_t b1_lo, int j, int k, 
 
 // B1[j][k] = A[j][k] * bilinear(f)[j][k] for k < nz, 0 for nz <= k < 128, as
 // BF16 hi and lo parts.  A warp stages whole rows, lane l covering k = 4l..4l+3
-// with 128-bit loads (one 512-byte row per load instruction), two rows at a
-// time.
+// with 128-bit loads (one 512-byte row per load instruction), four rows at a
+// time so that twenty loads per lane are in flight together.
 __device__ __forceinline__ void tc_stage_plane(uint32_t b1, uint32_t b1_lo, const TcTapRow* rows,
                                                const float* __restrict__ xb, const float* __restrict__ arow, int n,
                                                int nz)
 {
+    constexpr int kRows = 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int k = 4 * lane;
     const bool in = k < nz;
-    for (int j0 = warp; j0 < n; j0 += 2 * nw) {
-        const int j1 = j0 + nw;
-        const bool has1 = j1 < n;
-        const TcTapRow t0 = rows[j0];
-        const TcTapRow t1 = rows[has1 ? j1 : j0];
-        float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-        if (in) {
-            float4 f0[4], f1[4];
+    for (int jb = warp; jb < n; jb += kRows * nw) {
+        float4 v[kRows];
+        int jr[kRows];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                f0[q] = __ldg(reinterpret_cast<const float4*>(xb + t0.off[q] + k));
-                f1[q] = __ldg(reinterpret_cast<const float4*>(xb + t1.off[q] + k));
-            }
-            float4 a0 = make_float4(1.f, 1.f, 1.f, 1.f), a1 = a0;
-            if (arow) {
-                a0 = __ldg(reinterpret_cast<const float4*>(arow + (size_t)j0 * nz + k));
-                a1 = __ldg(reinterpret_cast<const float4*>(arow + (size_t)(has1 ? j1 : j0) * nz + k));
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                fma4(v0, t0.w[q], f0[q]);
-                fma4(v1, t1.w[q], f1[q]);
-            }
-            v0.x *= a0.x; v0.y *= a0.y; v0.z *= a0.z; v0.w *= a0.w;
-            v1.x *= a1.x; v1.y *= a1.y; v1.z *= a1.z; v1.w *= a1.w;
+        for (int r = 0; r < kRows; ++r) {
+            jr[r] = jb + r * nw;
+            v[r] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        put4(b1, b1_lo, j0, k, n, v0);
-        if (has1) put4(b1, b1_lo, j1, k, n, v1);
+        if (in) {
+            float4 f[kRows][4], av[kRows];
+            TcTapRow t[kRows];
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                const int j = jr[r] < n ? jr[r] : jb;  // rows past n repeat a valid row; not stored
+                t[r] = rows[j];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) f[r][q] = __ldg(reinterpret_cast<const float4*>(xb + t[r].off[q] + k));
+                av[r] = arow ? __ldg(reinterpret_cast<const float4*>(arow + (size_t)j * nz + k))
+                             : make_float4(1.f, 1.f, 1.f, 1.f);
+            }
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) fma4(v[r], t[r].w[q], f[r][q]);
+                v[r].x *= av[r].x;
+                v[r].y *= av[r].y;
+                v[r].z *= av[r].z;
+                v[r].w *= av[r].w;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kRows; ++r)
+            if (jr[r] < n) put4(b1, b1_lo, jr[r], k, n, v[r]);
     }
+}
+
+// Ask L2 to fetch one attenuation plane (n rows of nz floats; rows start on
+// 16-byte boundaries as nz % 8 == 0) ahead of its use; a hint that nothing
+// waits on.
+__device__ __forceinline__ void tc_prefetch_plane(const float* plane, int n, int nz)
+{
+    for (int j = threadIdx.x; j < n; j += blockDim.x) prefetch_l2(plane + (size_t)j * nz, (uint32_t)nz * 4u);
 }
 
 // B1[j][k] = proj[j][k] (all ones when proj is NULL) for k < nz, as BF16 hi
@@ -424,6 +404,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
     int i = chunk;
     if (i < n) {
         const float* arow = a.atten ? a.atten + ((size_t)angle * n + i) * n * nz : nullptr;
+        if (a.atten && i + a.chunks < n) tc_prefetch_plane(arow + (size_t)a.chunks * n * nz, n, nz);
         if (threadIdx.x == 0) tma_load_1d(st.s.tap, a.ttab + (size_t)i * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
         tc_tap_rows(rows, n, nz, i, cs, c);
         __syncthreads();
@@ -444,20 +425,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
-        if (threadIdx.x == 0) issue_gemm2(st.s, d2, idesc, n, !first);
+        bool ok2 = true;
+        if (threadIdx.x == 0) {
+            issue_gemm2(st.s, d2, idesc, n, !first);
+            // GEMM 2(i) is short: as soon as it has read the Toeplitz tiles,
+            // fetch those of the next plane behind the staging below
+            if (inext < n) {
+                ok2 = mbar_wait(st.s.bar_2, ph_2);
+                if (ok2) tma_load_1d(st.s.tap, a.ttab + (size_t)inext * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
+            }
+        }
         first = false;
         if (inext < n) {
             // GEMM 1(i) has finished with B1; stage the next plane meanwhile
             const float* arow = a.atten ? a.atten + ((size_t)angle * n + inext) * n * nz : nullptr;
+            if (a.atten && inext + a.chunks < n) tc_prefetch_plane(arow + (size_t)a.chunks * n * nz, n, nz);
             tc_tap_rows(rows, n, nz, inext, cs, c);
             __syncthreads();
             tc_stage_plane(st.s.b1, st.s.b1_lo, rows, xb, arow, n, nz);
             fence_async_smem();
         }
-        ok = all_ok(mbar_wait(st.s.bar_2, ph_2), a.err);
+        ok = all_ok(ok2 && mbar_wait(st.s.bar_2, ph_2), a.err);
         ph_2 ^= 1u;
         if (!ok || inext >= n) break;
-        if (threadIdx.x == 0) tma_load_1d(st.s.tap, a.ttab + (size_t)inext * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
         ok = all_ok(mbar_wait(st.s.bar_t, ph_t), a.err);
         ph_t ^= 1u;
         if (ok && threadIdx.x == 0) issue_gemm1(st.s, d1, idesc, n);
@@ -504,6 +494,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
 
     // the projection of this angle is the B operand of every plane's GEMM 1
     int i = chunk;
+    if (i < n && a.atten) tc_prefetch_plane(a.atten + ((size_t)angle * n + i) * n * nz, n, nz);
     if (i < n && threadIdx.x == 0)
         tma_load_1d(st.s.tap, a.ttab + (size_t)i * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
     tc_stage_proj(st.s.b1, st.s.b1_lo, pr, n, nz);
@@ -535,6 +526,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
         tc_fence_after();
         // B[i][j][k] = A[i][j][k] * (K_i r)[j][k]; D2 holds (K_i r)^T (lanes k)
         const float* arow = a.atten ? a.atten + ((size_t)angle * n + i) * n * nz : nullptr;
+        if (a.atten && inext < n) tc_prefetch_plane(arow + (size_t)a.chunks * n * nz, n, nz);
         float* brow = bvol + (size_t)i * n * nz;
         for (int cc = 16 * (warp >> 2); cc < n; cc += 64) {
             float aw[16];
