@@ -6,51 +6,93 @@
 
 namespace spect {
 
-// T_att of Eq. (1) in the rotated frame of angle a: one thread per detector
-// ray (j, k) walks depth from the detector side (i = n-1) inward,
+// T_att of Eq. (1) in the rotated frame of angle a: one thread per four
+// detector rays (j, k..k+3) walks depth from the detector side (i = n-1)
+// inward,
 //   A[i] = exp(-(sum_{i'>i} tau[i'] + tau[i]/2)),  tau = voxel_cm * bilinear(mu)(u, v, k).
-// The running sum is FP64 (f64 != 0) or Kahan-compensated FP32; the
-// exponential is FP32 in both (its argument carries the sum's precision).
-// The mu loads do not depend on the sum, so the unrolled walk keeps several
-// in flight.
-__global__ void attenuation_kernel(const float* __restrict__ mu, const float2* __restrict__ cs_tab, int n, int nz,
-                                   float voxel_cm, int f64, float* __restrict__ atten)
+// The running sum is compensated (Kahan) FP32, and with f64 != 0 it is
+// folded into an FP64 total every kFold steps (the last <= kFold terms are
+// held as the compensated FP32 pair), so the ray's prefix sum is carried in
+// FP64 at the cost of a few FP64 operations per kFold steps.  The
+// exponential is FP32 in both modes.  A block covers 256 / (nz/4) rows j of
+// one angle, whose bilinear taps overlap in L1.
+namespace {
+constexpr int kFold = 8;
+
+struct RaySum {
+    float s = 0.f, c = 0.f;  // compensated partial sum: value s - c
+    double base = 0.0;       // FP64 total of the folded terms
+    float base_f = 0.f;      // base rounded to FP32
+    __device__ __forceinline__ float prefix() const { return base_f + (s - c); }
+    __device__ __forceinline__ void add(float tau)
+    {
+        const float y = tau - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ void fold()
+    {
+        base += (double)s;
+        base -= (double)c;
+        base_f = (float)base;
+        s = c = 0.f;
+    }
+};
+}  // namespace
+
+__global__ void __launch_bounds__(256) attenuation_kernel(const float* __restrict__ mu, const float2* __restrict__ cs_tab,
+                                                          int n, int nz, float voxel_cm, int f64,
+                                                          float* __restrict__ atten)
 {
     const int angle = blockIdx.y;
+    const int zq = nz >> 2;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * nz) return;
-    const int j = idx / nz, k = idx - j * nz;
+    if (idx >= n * zq) return;
+    const int j = idx / zq, k = 4 * (idx - j * zq);
     const float2 cs = cs_tab[angle];
     const float c = 0.5f * (float)(n - 1);
-    double sum_d = 0.0;
-    float sum = 0.f, comp = 0.f;
-    float* out = atten + ((size_t)angle * n * n + j) * nz + k;
-#pragma unroll 8
-    for (int i = n - 1; i >= 0; --i) {
-        float u, v;
-        sample_point(cs.x, cs.y, c, i, j, u, v);
-        const float fu = floorf(u), fv = floorf(v);
-        const int x0 = (int)fu, y0 = (int)fv;
-        const float ax = u - fu, by = v - fv;
-        float m = 0.f;
-        if (x0 >= 0 && x0 < n && y0 >= 0 && y0 < n) m = fmaf((1.f - ax) * (1.f - by), __ldg(mu + ((size_t)x0 * n + y0) * nz + k), m);
-        if (x0 + 1 >= 0 && x0 + 1 < n && y0 >= 0 && y0 < n) m = fmaf(ax * (1.f - by), __ldg(mu + ((size_t)(x0 + 1) * n + y0) * nz + k), m);
-        if (x0 >= 0 && x0 < n && y0 + 1 >= 0 && y0 + 1 < n) m = fmaf((1.f - ax) * by, __ldg(mu + ((size_t)x0 * n + y0 + 1) * nz + k), m);
-        if (x0 + 1 >= 0 && x0 + 1 < n && y0 + 1 >= 0 && y0 + 1 < n) m = fmaf(ax * by, __ldg(mu + ((size_t)(x0 + 1) * n + y0 + 1) * nz + k), m);
-        const float tau = voxel_cm * m;
-        float a;
-        if (f64) {
-            a = expf(-(float)(sum_d + 0.5 * (double)tau));
-            sum_d += (double)tau;
-        } else {
-            a = expf(-((sum + comp) + 0.5f * tau));
-            // Kahan summation of the optical depth beyond the plane
-            const float yv = tau - comp;
-            const float tv = sum + yv;
-            comp = (tv - sum) - yv;
-            sum = tv;
+    RaySum r[4];
+    float4* out = reinterpret_cast<float4*>(atten + ((size_t)angle * n * n + j) * nz + k);
+    const size_t plane4 = (size_t)n * nz / 4;
+    for (int i0 = n - 1; i0 >= 0; i0 -= kFold) {
+#pragma unroll
+        for (int s = 0; s < kFold; ++s) {
+            const int i = i0 - s;
+            if (i < 0) break;
+            float u, v;
+            sample_point(cs.x, cs.y, c, i, j, u, v);
+            const float fu = floorf(u), fv = floorf(v);
+            const int x0 = (int)fu, y0 = (int)fv;
+            const float ax = u - fu, by = v - fv;
+            const bool vx0 = x0 >= 0 && x0 < n, vx1 = x0 + 1 >= 0 && x0 + 1 < n;
+            const bool vy0 = y0 >= 0 && y0 < n, vy1 = y0 + 1 >= 0 && y0 + 1 < n;
+            float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+            auto tap = [&](bool ok, int x, int y, float w) {
+                if (!ok) return;
+                const float4 q = __ldg(reinterpret_cast<const float4*>(mu + ((size_t)x * n + y) * nz + k));
+                m.x = fmaf(w, q.x, m.x);
+                m.y = fmaf(w, q.y, m.y);
+                m.z = fmaf(w, q.z, m.z);
+                m.w = fmaf(w, q.w, m.w);
+            };
+            tap(vx0 && vy0, x0, y0, (1.f - ax) * (1.f - by));
+            tap(vx1 && vy0, x0 + 1, y0, ax * (1.f - by));
+            tap(vx0 && vy1, x0, y0 + 1, (1.f - ax) * by);
+            tap(vx1 && vy1, x0 + 1, y0 + 1, ax * by);
+            const float tau[4] = {voxel_cm * m.x, voxel_cm * m.y, voxel_cm * m.z, voxel_cm * m.w};
+            float a[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a[q] = expf(-(r[q].prefix() + 0.5f * tau[q]));
+                r[q].add(tau[q]);
+            }
+            out[(size_t)i * plane4] = make_float4(a[0], a[1], a[2], a[3]);
         }
-        out[(size_t)i * n * nz] = a;
+        if (f64) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) r[q].fold();
+        }
     }
 }
 
@@ -58,7 +100,7 @@ cudaError_t launch_attenuation(const float* mu, const float2* cs, int n, int nz,
                                float* atten, cudaStream_t st)
 {
     const int threads = 256;
-    dim3 grid((n * nz + threads - 1) / threads, n_angles);
+    dim3 grid((n * (nz / 4) + threads - 1) / threads, n_angles);
     attenuation_kernel<<<grid, threads, 0, st>>>(mu, cs, n, nz, voxel_cm, f64, atten);
     return cudaGetLastError();
 }
