@@ -124,7 +124,10 @@ cudaError_t launch_diag_finalize(const double* part, int n_part, double* out3, c
 // Sum of the depth-chunk partial projections (chunk order, deterministic)
 // and, with y, the OSEM ratio r = y / (p + s) (0 where p + s == 0) and the
 // FP64 count sums of (p + s), y and y * p / (p + s) per block.
-__global__ void forward_reduce_kernel(ReduceArgs a)
+// The FP64 count sums run only when requested (kDiag): FP64 throughput on
+// GB300 is a small fraction of FP32.
+template <bool kDiag>
+__global__ void __launch_bounds__(256) forward_reduce_kernel(ReduceArgs a)
 {
     __shared__ double red[32];
     const int plane4 = a.plane >> 2;
@@ -154,15 +157,17 @@ __global__ void forward_reduce_kernel(ReduceArgs a)
             for (int q = 0; q < 4; ++q) {
                 const float den = pv[q] + s;
                 rv[q] = den > 0.f ? yy[q] / den : 0.f;
-                d0 += (double)den;
-                d1 += (double)yy[q];
-                d2 += (double)(rv[q] * pv[q]);
+                if (kDiag) {
+                    d0 += (double)den;
+                    d1 += (double)yy[q];
+                    d2 += (double)(rv[q] * pv[q]);
+                }
             }
             o = make_float4(rv[0], rv[1], rv[2], rv[3]);
         }
         reinterpret_cast<float4*>(a.out)[e] = o;
     }
-    if (a.diag_blocks) {
+    if (kDiag) {
         const double s0 = block_sum_f64(d0, red);
         const double s1 = block_sum_f64(d1, red);
         const double s2 = block_sum_f64(d2, red);
@@ -176,7 +181,10 @@ __global__ void forward_reduce_kernel(ReduceArgs a)
 
 cudaError_t launch_forward_reduce(const ReduceArgs& a, int blocks, cudaStream_t st)
 {
-    forward_reduce_kernel<<<blocks, 256, 0, st>>>(a);
+    if (a.diag_blocks)
+        forward_reduce_kernel<true><<<blocks, 256, 0, st>>>(a);
+    else
+        forward_reduce_kernel<false><<<blocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
