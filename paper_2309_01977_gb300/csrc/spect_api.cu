@@ -229,7 +229,9 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
                 float s, double* diag_blocks, int* n_diag, cudaStream_t st, const float* s_ptr = nullptr)
 {
     const PlaneTiling& t = p->tiling;
-    const int chunks = chunk_target(p, (long)n_sel * (p->bf16 ? 1 : t.ntiles));
+    // never more chunks than the partial buffer holds for one batch entry
+    const int chunks = (int)std::min<size_t>(chunk_target(p, (long)n_sel * (p->bf16 ? 1 : t.ntiles)),
+                                             std::max<size_t>(1, p->partial_planes / (size_t)n_sel));
     const bool use_partials = chunks > 1 || y != nullptr;
     const size_t vol = vol_elems(p), plane = plane_elems(p);
     int bper = batch;

@@ -8,8 +8,9 @@ Tolerances:
     measured error is an order of magnitude below this);
   - FP64 count sums: conservation holds to FP32 rounding of H x (1e-6).
 Sizes span several blur strips and plane tiles with ragged tails (n and nz
-not multiples of 16), the 64^3 and 128^3 workloads in full, and a 192^3
-geometry whose planes are split into z tiles.
+not multiples of 16), a 132^2 x 44 geometry whose back projection takes the
+tiled gather with partial tiles, the 64^3 and 128^3 workloads in full, and a
+192^3 geometry whose planes are split into z tiles.
 """
 import math
 
@@ -37,6 +38,9 @@ CASES = {
     "psf_only": (dict(n=32, nz=44, n_angles=5, n_subsets=1, attenuation=False, psf_slope=0.15), 13),
     "explicit_angles": (dict(n=24, nz=8, n_angles=6, n_subsets=2, det_offset=3.0, psf_sigma0=0.8,
                              angles_rad=[0.0, 0.4, 1.9, math.pi, 4.0, 6.0]), 14),
+    # planes of 128^2 and up take the tiled gather; 132 leaves partial 8x8
+    # tiles at the edge and nz = 44 short z rows
+    "tiled132x44": (dict(n=132, nz=44, n_angles=9, n_subsets=3), 15),
 }
 
 
@@ -147,8 +151,9 @@ def test_osem_resume_is_bitwise(spect_lib, oracle_mod, cuda):
     assert torch.equal(a, b)
 
 
-def test_forward_is_deterministic_and_batched(spect_lib, oracle_mod, cuda):
-    g, f, mu, plan, og = _setup(spect_lib, oracle_mod, cuda, "ragged40x36")
+@pytest.mark.parametrize("name", ["ragged40x36", "tiled132x44"])
+def test_forward_is_deterministic_and_batched(spect_lib, oracle_mod, cuda, name):
+    g, f, mu, plan, og = _setup(spect_lib, oracle_mod, cuda, name)
     rng = np.random.Generator(np.random.PCG64(8))
     xs = _t(rng.uniform(size=(3, g.n, g.n, g.nz)), cuda)
     pb = plan.forward(xs)
