@@ -6,14 +6,19 @@ shares no code with it.  See ``spect_oracle.c`` for the definitions and the
 readings taken where the paper is silent.
 """
 from .oracle import (  # noqa: F401
+    ALGORITHMS,
+    PRIORS,
     Geom,
     attenuation,
     back,
     build,
     forward,
+    map_recon,
     n_threads,
     osem,
     poisson_ll,
+    prior_grad,
+    prior_value,
     psf_rmax,
     psf_taps,
     rotate,

@@ -71,6 +71,13 @@ def _load():
                                                                          _dp, _dp]
             lib.or_poisson_ll.restype = ctypes.c_double
             lib.or_poisson_ll.argtypes = [_dp, _dp, ctypes.c_double, ctypes.c_size_t]
+            lib.or_prior_value.restype = ctypes.c_double
+            lib.or_prior_value.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+            lib.or_prior_grad.restype = None
+            lib.or_prior_grad.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
+            lib.or_map.restype = None
+            lib.or_map.argtypes = ([_dp, ctypes.c_double] + geom_args + [ctypes.c_int] * 5 +
+                                   [ctypes.c_double] * 4 + [_dp])
             lib.or_n_threads.restype = ctypes.c_int
             lib.or_set_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -218,3 +225,36 @@ def poisson_ll(y, p, s: float) -> float:
     p = _f64(p).ravel()
     assert y.size == p.size
     return _load().or_poisson_ll(_ptr(y), _ptr(p), float(s), y.size)
+
+
+PRIORS = {"none": 0, "quadratic": 1, "rdp": 2}
+ALGORITHMS = {"osmaposl": 1, "bsrem": 2}
+
+
+def prior_value(f, prior: str, delta: float = 1.0, gamma: float = 2.0) -> float:
+    """V(f) = sum_r sum_s w_rs phi(f_r, f_s) over 26-neighbourhoods, w = 1/distance (Table 1)."""
+    f = _f64(f)
+    n, n2, nz = f.shape
+    assert n == n2
+    return _load().or_prior_value(_ptr(f), n, nz, PRIORS[prior], float(delta), float(gamma))
+
+
+def prior_grad(f, prior: str, delta: float = 1.0, gamma: float = 2.0):
+    """dV/df for the prior of prior_value."""
+    f = _f64(f)
+    n, n2, nz = f.shape
+    assert n == n2
+    g = np.zeros_like(f)
+    _load().or_prior_grad(_ptr(f), n, nz, PRIORS[prior], float(delta), float(gamma), _ptr(g))
+    return g
+
+
+def map_recon(y, s: float, g: Geom, n_subsets: int, first: int, count: int, algorithm: str, prior: str,
+              beta: float, delta: float = 1.0, gamma: float = 2.0, alpha0: float = 1.0, f0=None):
+    """OSMAPOSL or BSREM subiterations first..first+count-1 (Eq. PGA, Table 1) from f0 (default ones)."""
+    y = _f64(y).reshape(g.n_angles, g.n, g.nz)
+    f = np.ones((g.n, g.n, g.nz)) if f0 is None else _f64(f0).reshape(g.n, g.n, g.nz).copy()
+    _load().or_map(_ptr(y), float(s), *g._args(), int(n_subsets), int(first), int(count), ALGORITHMS[algorithm],
+                   PRIORS[prior], float(beta), float(delta), float(gamma), float(alpha0), _ptr(f))
+    return f
+

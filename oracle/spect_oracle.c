@@ -33,6 +33,18 @@
  *   - subsets S_m = { n : n mod M == m }, visited m = 0..M-1.
  *   - OSEM: where H_m^T 1 == 0 the voxel is unchanged; where H_m f + s == 0
  *     the ratio is 0.  No epsilon anywhere.
+ *   - priors (Sec. 2.1.3, Table 1, prior classes): V(f) = sum_r sum_s w_rs
+ *     phi(f_r, f_s) over the 26 neighbours s of r inside the volume, with
+ *     w_rs = 1 / |r - s| (inverse Euclidean distance in voxels); a term whose
+ *     RDP denominator f_r + f_s + gamma |f_r - f_s| is 0 contributes 0.
+ *   - MAP algorithms (Eq. PGA with the Table 1 preconditioners), beta_n =
+ *     beta / M (c_n = 1/M, the subset's share of the data):
+ *       OSMAPOSL  f <- f H_m^T r / (H_m^T 1 + beta_n grad V(f)); a voxel whose
+ *                 denominator is <= 0 is unchanged;
+ *       BSREM     f <- max(0, f + alpha_t f / (c_n H^T 1) (H_m^T r - H_m^T 1
+ *                 - beta_n grad V(f))), H^T 1 over all angles, alpha_t =
+ *                 alpha0 / (1 + floor(t / M)) (one relaxation step per
+ *                 iteration); a voxel with H^T 1 == 0 is unchanged.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -411,3 +423,138 @@ double or_poisson_ll(const double* y, const double* p, double s, size_t count)
     }
     return L;
 }
+
+/* ---------------------------------------------------------------- priors */
+
+/* Nearest-neighbour priors of Table 1: the pair function phi(a, b) and its
+ * partial derivative in its first argument.
+ *   kind 1, QuadraticPrior:          phi = ((a - b) / delta)^2 / 4
+ *   kind 2, RelativeDifferencePrior: phi = (a - b)^2 / (a + b + gamma |a - b|)
+ */
+static double prior_phi(int kind, double a, double b, double delta, double gamma)
+{
+    double d = a - b;
+    if (kind == 1) return (d / delta) * (d / delta) / 4.0;
+    double den = a + b + gamma * fabs(d);
+    return den != 0.0 ? d * d / den : 0.0;
+}
+
+/* d phi(a, b) / d a.  Quadratic: (a - b) / (2 delta^2).  RDP, with
+ * S = a + b + gamma |a - b|: (2 (a - b) S - (a - b)^2 (1 + gamma sign(a - b)))
+ * / S^2, written out without simplification. */
+static double prior_dphi_a(int kind, double a, double b, double delta, double gamma)
+{
+    double d = a - b;
+    if (kind == 1) return d / (2.0 * delta * delta);
+    double S = a + b + gamma * fabs(d);
+    if (S == 0.0) return 0.0;
+    double sg = d > 0.0 ? 1.0 : (d < 0.0 ? -1.0 : 0.0);
+    return (2.0 * d * S - d * d * (1.0 + gamma * sg)) / (S * S);
+}
+
+/* V(f) = sum_r sum_s w_rs phi(f_r, f_s), s over the 26 neighbours of r that
+ * lie inside the volume, w_rs = 1 / |r - s|. */
+double or_prior_value(const double* f, int n, int nz, int kind, double delta, double gamma)
+{
+    double V = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            for (int k = 0; k < nz; ++k)
+                for (int di = -1; di <= 1; ++di)
+                    for (int dj = -1; dj <= 1; ++dj)
+                        for (int dk = -1; dk <= 1; ++dk) {
+                            if (!di && !dj && !dk) continue;
+                            int i2 = i + di, j2 = j + dj, k2 = k + dk;
+                            if (i2 < 0 || i2 >= n || j2 < 0 || j2 >= n || k2 < 0 || k2 >= nz) continue;
+                            double w = 1.0 / sqrt((double)(di * di + dj * dj + dk * dk));
+                            V += w * prior_phi(kind, f[IDX3(i, j, k, n, nz)], f[IDX3(i2, j2, k2, n, nz)], delta, gamma);
+                        }
+    return V;
+}
+
+/* dV/df_r.  f_r appears in the terms (r, s) as the first argument and in
+ * the terms (s, r) as the second; phi is symmetric for both priors, so the
+ * second partial of (s, r) equals the first partial of (r, s):
+ *   dV/df_r = sum_s w_rs 2 dphi(f_r, f_s)/da. */
+void or_prior_grad(const double* f, int n, int nz, int kind, double delta, double gamma, double* grad)
+{
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            for (int k = 0; k < nz; ++k) {
+                double g = 0.0, fr = f[IDX3(i, j, k, n, nz)];
+                for (int di = -1; di <= 1; ++di)
+                    for (int dj = -1; dj <= 1; ++dj)
+                        for (int dk = -1; dk <= 1; ++dk) {
+                            if (!di && !dj && !dk) continue;
+                            int i2 = i + di, j2 = j + dj, k2 = k + dk;
+                            if (i2 < 0 || i2 >= n || j2 < 0 || j2 >= n || k2 < 0 || k2 >= nz) continue;
+                            double w = 1.0 / sqrt((double)(di * di + dj * dj + dk * dk));
+                            g += w * 2.0 * prior_dphi_a(kind, fr, f[IDX3(i2, j2, k2, n, nz)], delta, gamma);
+                        }
+                grad[IDX3(i, j, k, n, nz)] = g;
+            }
+}
+
+/* ---------------------------------------------------------------- MAP */
+
+/* OSMAPOSL (algo 1) and BSREM (algo 2) subiterations first .. first+count-1
+ * with prior `kind` (0: none), as stated in the header (Eq. PGA, Table 1). */
+void or_map(const double* y, double s, int n, int nz, int n_angles, const double* angles,
+            double voxel_cm, const double* mu, int use_psf, double sigma0, double slope,
+            double nsigma, double det_offset, int n_subsets, int first, int count,
+            int algo, int kind, double beta, double delta, double gamma, double alpha0, double* f)
+{
+    size_t vol = (size_t)n * n * nz, plane = (size_t)n * nz;
+    int* sel = (int*)malloc(sizeof(int) * (size_t)n_angles);
+    double* p = (double*)malloc(sizeof(double) * plane * (size_t)n_angles);
+    double* ones = (double*)malloc(sizeof(double) * plane * (size_t)n_angles);
+    double* bp = (double*)malloc(sizeof(double) * vol);
+    double* sens = (double*)malloc(sizeof(double) * vol);
+    double* sens_all = (double*)malloc(sizeof(double) * vol);
+    double* gv = (double*)calloc(vol, sizeof(double));
+    double c = 1.0 / (double)n_subsets, beta_n = beta * c;
+    for (size_t q = 0; q < plane * (size_t)n_angles; ++q) ones[q] = 1.0;
+    if (algo == 2) {
+        for (int a = 0; a < n_angles; ++a) sel[a] = a;
+        or_back(ones, n, nz, n_angles, angles, voxel_cm, mu, use_psf, sigma0, slope, nsigma, det_offset,
+                sel, n_angles, sens_all);
+    }
+    for (int t = first; t < first + count; ++t) {
+        int m = t % n_subsets, ns = 0;
+        for (int a = 0; a < n_angles; ++a)
+            if (a % n_subsets == m) sel[ns++] = a;
+        or_forward(f, n, nz, n_angles, angles, voxel_cm, mu, use_psf, sigma0, slope, nsigma,
+                   det_offset, sel, ns, p);
+        for (int a = 0; a < ns; ++a)
+            for (size_t q = 0; q < plane; ++q) {
+                double den = p[(size_t)a * plane + q] + s;
+                p[(size_t)a * plane + q] = den > 0.0 ? y[(size_t)sel[a] * plane + q] / den : 0.0;
+            }
+        or_back(p, n, nz, n_angles, angles, voxel_cm, mu, use_psf, sigma0, slope, nsigma,
+                det_offset, sel, ns, bp);
+        or_back(ones, n, nz, n_angles, angles, voxel_cm, mu, use_psf, sigma0, slope, nsigma,
+                det_offset, sel, ns, sens);
+        if (kind) or_prior_grad(f, n, nz, kind, delta, gamma, gv);
+        double alpha = alpha0 / (1.0 + (double)(t / n_subsets));
+        for (size_t q = 0; q < vol; ++q) {
+            if (algo == 1) {
+                double den = sens[q] + beta_n * gv[q];
+                if (den > 0.0) f[q] = f[q] * bp[q] / den;
+            } else {
+                if (sens_all[q] > 0.0) {
+                    double v = f[q] + alpha * f[q] / (c * sens_all[q]) * (bp[q] - sens[q] - beta_n * gv[q]);
+                    f[q] = v > 0.0 ? v : 0.0;
+                }
+            }
+        }
+    }
+    free(sel);
+    free(p);
+    free(ones);
+    free(bp);
+    free(sens);
+    free(sens_all);
+    free(gv);
+}
+

@@ -231,3 +231,78 @@ def test_poisson_gradient_matches_finite_differences(oracle_mod):
         lm = oracle_mod.poisson_ll(y, oracle_mod.forward(fm, g), s)
         fd = (lp - lm) / (2 * h)
         assert fd == pytest.approx(grad[q], rel=1e-5, abs=1e-6 * np.abs(grad).max())
+
+
+# ---------------------------------------------------------------- priors and MAP (Sec. 2.1.3, Table 1)
+
+def test_prior_value_two_voxels_closed_form(oracle_mod):
+    """Two voxels along z (w = 1): V = phi(a, b) + phi(b, a), by hand."""
+    f = np.array([[[3.0, 1.0]]])
+    # RDP, gamma = 2: (3-1)^2 / (3+1+2*2) = 0.5 per ordered pair
+    assert oracle_mod.prior_value(f, "rdp", gamma=2.0) == pytest.approx(1.0, rel=1e-15)
+    # quadratic, delta = 2: ((3-1)/2)^2 / 4 = 0.25 per ordered pair
+    assert oracle_mod.prior_value(f, "quadratic", delta=2.0) == pytest.approx(0.5, rel=1e-15)
+
+
+def test_prior_gradient_two_voxels_closed_form(oracle_mod):
+    """V(a, b) = 2 (a-b)^2 / (a+b+2|a-b|) at (3, 1): dV/da = 0.625, dV/db = -0.875 (by hand)."""
+    g = oracle_mod.prior_grad(np.array([[[3.0, 1.0]]]), "rdp", gamma=2.0)
+    assert g[0, 0, 0] == pytest.approx(0.625, rel=1e-14)
+    assert g[0, 0, 1] == pytest.approx(-0.875, rel=1e-14)
+
+
+def test_prior_neighbour_weights_inverse_distance(oracle_mod):
+    """2x2x2 block, one corner a, the rest c: the corner has 3 neighbours at
+    distance 1, 3 at sqrt 2 and 1 at sqrt 3, each pair counted twice."""
+    a, c = 2.0, 0.5
+    f = np.full((2, 2, 2), c)
+    f[0, 0, 0] = a
+    phi = (a - c) ** 2 / (a + c + 2.0 * abs(a - c))
+    expect = 2 * phi * (3 + 3 / math.sqrt(2) + 1 / math.sqrt(3))
+    assert oracle_mod.prior_value(f, "rdp", gamma=2.0) == pytest.approx(expect, rel=1e-14)
+
+
+@pytest.mark.parametrize("prior", ["quadratic", "rdp"])
+def test_prior_gradient_matches_finite_differences(oracle_mod, prior):
+    rng = _rng(21)
+    f = rng.uniform(0.2, 3.0, size=(5, 5, 6))
+    g = oracle_mod.prior_grad(f, prior, delta=1.5, gamma=2.0)
+    for _ in range(12):
+        q = tuple(int(v) for v in rng.integers(0, [5, 5, 6]))
+        h = 1e-5
+        fp = f.copy(); fp[q] += h
+        fm = f.copy(); fm[q] -= h
+        fd = (oracle_mod.prior_value(fp, prior, 1.5, 2.0) - oracle_mod.prior_value(fm, prior, 1.5, 2.0)) / (2 * h)
+        assert fd == pytest.approx(g[q], rel=1e-6, abs=1e-9)
+
+
+@pytest.mark.parametrize("prior", ["quadratic", "rdp"])
+def test_prior_gradient_vanishes_on_constant_image(oracle_mod, prior):
+    g = oracle_mod.prior_grad(np.full((4, 4, 5), 1.7), prior)
+    assert np.abs(g).max() == 0.0
+
+
+def test_osmaposl_without_prior_weight_is_osem(oracle_mod):
+    """Table 1: OSMAPOSL with beta = 0 has the OSEM preconditioner."""
+    g, y, s = _small_problem(oracle_mod, 0.05)
+    f_osem, _ = oracle_mod.osem(y, s, g, 4, 0, 5)
+    f_map = oracle_mod.map_recon(y, s, g, 4, 0, 5, "osmaposl", "rdp", beta=0.0)
+    np.testing.assert_allclose(f_map, f_osem, rtol=1e-13, atol=0)
+
+
+def test_bsrem_one_subset_first_step_is_mlem(oracle_mod):
+    """BSREM with one subset, beta = 0 and alpha = 1: f + f/H^T1 (H^T r - H^T 1) = f H^T r / H^T 1."""
+    g, y, s = _small_problem(oracle_mod, 0.05)
+    f_mlem, _ = oracle_mod.osem(y, s, g, 1, 0, 1)
+    f_map = oracle_mod.map_recon(y, s, g, 1, 0, 1, "bsrem", "rdp", beta=0.0, alpha0=1.0)
+    np.testing.assert_allclose(f_map, f_mlem, rtol=1e-12, atol=1e-14 * np.abs(f_mlem).max())
+
+
+@pytest.mark.parametrize("algorithm", ["osmaposl", "bsrem"])
+def test_map_prior_smooths(oracle_mod, algorithm):
+    """With the RDP weighted in, the image's own RDP value drops below the unregularised one."""
+    g, y, s = _small_problem(oracle_mod, 0.05)
+    f0 = oracle_mod.map_recon(y, s, g, 4, 0, 8, algorithm, "rdp", beta=0.0)
+    f1 = oracle_mod.map_recon(y, s, g, 4, 0, 8, algorithm, "rdp", beta=0.3)
+    assert oracle_mod.prior_value(f1, "rdp") < oracle_mod.prior_value(f0, "rdp")
+    assert np.isfinite(f1).all() and f1.min() >= 0.0
