@@ -59,6 +59,7 @@ def parse_args():
     ap.add_argument("--serve-requests", type=int, default=256,
                     help="requests of the serving leg (0 skips it)")
     ap.add_argument("--serve-budget-gib", type=float, default=8.0)
+    ap.add_argument("--no-map", action="store_true", help="skip the BSREM-RDP leg")
     return ap.parse_args()
 
 
@@ -484,6 +485,21 @@ def run_libspect(args):
         "kernel_avg_us": {k: round(1e3 * v[1] / v[0], 2) for k, v in prof.items()},
         "plane_tiling": {k: plan.info()[k] for k in ("ztile", "n_ztiles", "threads", "smem_bytes")}})
 
+    # MAP leg: BSREM with the relative difference prior (beta 0.3, gamma 2,
+    # the paper's hyperparameters) on the same workload and data, 4 x 8
+    map_leg = None
+    if not args.no_map:
+        def step_map():
+            x.fill_(1.0)
+            plan.map(y_dev, s, x, 0, n_sub, "bsrem", "rdp", beta=0.3, gamma=2.0, alpha0=1.0)
+        step_map()
+        torch.cuda.synchronize()
+        ms_map = max_over_ranks(timed(step_map, max(2, args.steps // 2)))
+        k_map = max(2, args.steps // 2)
+        map_leg = {"algorithm": "BSREM, relative difference prior (beta 0.3, gamma 2)",
+                   "subset_iters_per_s": replica_throughput(world, k_map, n_sub, ms_map),
+                   "ms_per_recon": ms_map / k_map}
+
     serving = None
     if args.serve_requests > 0 and world == 1:
         serving = run_serving(spect, dev, args)
@@ -503,7 +519,7 @@ def run_libspect(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16 PSF, f32" if bf16 else "f32", "data": "synthetic",
             "config": cfg,
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": int(launches),
-            "clocks": clk, "serving": serving,
+            "clocks": clk, "map": map_leg, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     plan.close()

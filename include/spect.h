@@ -158,6 +158,52 @@ int spect_osem_run(spect_plan* plan, const float* y, float s, float* x_inout, in
 int spect_osem_run_dev(spect_plan* plan, const float* y, const float* s_dev, float* x_inout, int first_subiter,
                        int n_subiters, double* diag_dev, void* stream);
 
+/* ---------------------------------------------------------------- MAP */
+
+/* Nearest-neighbour priors (Sec. 2.1.3 and Table 1, prior classes):
+ *   V(x) = sum_r sum_s w_rs phi(x_r, x_s), s over the 26 neighbours of voxel
+ *   r inside the volume, w_rs = 1 / |r - s| (voxel units);
+ *   SPECT_PRIOR_QUADRATIC  phi = ((a - b) / delta)^2 / 4
+ *   SPECT_PRIOR_RDP        phi = (a - b)^2 / (a + b + gamma |a - b|)
+ *                          (relative difference prior; a pair whose
+ *                          denominator is 0 contributes 0). */
+#define SPECT_PRIOR_NONE 0
+#define SPECT_PRIOR_QUADRATIC 1
+#define SPECT_PRIOR_RDP 2
+
+/* Algorithms of Table 1 beyond OSEM, as preconditioned gradient ascent
+ * (Eq. PGA) with beta_n = beta / M:
+ *   SPECT_ALG_OSMAPOSL  x <- x H_m^T r / (H_m^T 1 + beta_n grad V(x)), r = y/(H_m x + s);
+ *                       a voxel whose denominator is <= 0 is unchanged;
+ *   SPECT_ALG_BSREM     x <- max(0, x + alpha_t M x / H^T 1 (H_m^T r - H_m^T 1 - beta_n grad V(x))),
+ *                       H^T 1 over all angles, alpha_t = alpha0 / (1 + floor(t / M))
+ *                       for subiteration t; a voxel with H^T 1 == 0 is unchanged. */
+#define SPECT_ALG_OSMAPOSL 1
+#define SPECT_ALG_BSREM 2
+
+typedef struct spect_map_params {
+    int algorithm;   /* SPECT_ALG_* */
+    int prior;       /* SPECT_PRIOR_* */
+    float beta;      /* prior weight (before the 1/M subset scaling) */
+    float delta;     /* quadratic prior scale (> 0) */
+    float gamma;     /* RDP edge-preservation parameter (>= 0) */
+    float alpha0;    /* BSREM relaxation at the first iteration (> 0) */
+} spect_map_params;
+
+/* OSMAPOSL or BSREM subiterations first_subiter .. first_subiter+n_subiters-1
+ * (subset m = t mod M) on x_inout (device float[nx][ny][nz], updated in
+ * place), with the same y, s and plan as spect_osem_run.  The first call on
+ * a plan allocates two volumes (the prior gradient and, for BSREM, H^T 1
+ * over all angles, recomputed after spect_plan_set_mu).  Resume by calling
+ * again with the next first_subiter.  Asynchronous on `stream`. */
+int spect_map_run(spect_plan* plan, const float* y, float s, float* x_inout, int first_subiter, int n_subiters,
+                  const spect_map_params* params, void* stream);
+
+/* grad_out = dV/dx for prior `prior` (SPECT_PRIOR_QUADRATIC or _RDP) on a
+ * device volume x[n][n][nz]; no plan, nothing allocated.  Asynchronous. */
+int spect_prior_grad(const float* x, int n, int nz, int prior, float delta, float gamma, float* grad_out,
+                     void* stream);
+
 /* Reuse a plan for a new attenuation map: recompute the attenuation cache
  * and the subset sensitivities from mu_dev [nx][ny][nz] (1/cm), queued on
  * `stream` (no synchronisation).  The geometry tables are kept. */

@@ -12,6 +12,7 @@
 
 #include "geometry.cuh"
 #include "internal.h"
+#include "update.cuh"
 
 namespace spect {
 
@@ -121,14 +122,8 @@ __global__ void __launch_bounds__(256) gather_kernel(GatherArgs a)
         }
     }
     float4* o = reinterpret_cast<float4*>(a.out + (size_t)b * vol + (size_t)col * nz) + z4;
-    if (a.sens) {
-        const float4 sv = __ldg(reinterpret_cast<const float4*>(a.sens + (size_t)col * nz) + z4);
-        float4 f = *o;
-        f.x = sv.x > 0.f ? f.x * acc.x / sv.x : f.x;
-        f.y = sv.y > 0.f ? f.y * acc.y / sv.y : f.y;
-        f.z = sv.z > 0.f ? f.z * acc.z / sv.z : f.z;
-        f.w = sv.w > 0.f ? f.w * acc.w / sv.w : f.w;
-        *o = f;
+    if (a.upd.mode != kUpdNone) {
+        *o = update4(a.upd, *o, acc, ((size_t)col * nz >> 2) + z4);
     } else if (a.accumulate) {
         float4 f = *o;
         f.x += acc.x;

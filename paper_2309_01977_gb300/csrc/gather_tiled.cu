@@ -22,6 +22,7 @@
 #include "async_copy.cuh"
 #include "geometry.cuh"
 #include "internal.h"
+#include "update.cuh"
 
 namespace spect {
 
@@ -276,14 +277,8 @@ __global__ void __launch_bounds__(kGatherTiledThreads) gather_tiled_kernel(Gathe
             const size_t col = (size_t)x * a.n + y;
             float4* o = reinterpret_cast<float4*>(a.out + (size_t)b * vol + col * a.nz + z0) + lane;
             const float4 s4 = acc[k];
-            if (a.sens) {
-                const float4 sv = __ldg(reinterpret_cast<const float4*>(a.sens + col * a.nz + z0) + lane);
-                float4 f = *o;
-                f.x = sv.x > 0.f ? f.x * s4.x / sv.x : f.x;
-                f.y = sv.y > 0.f ? f.y * s4.y / sv.y : f.y;
-                f.z = sv.z > 0.f ? f.z * s4.z / sv.z : f.z;
-                f.w = sv.w > 0.f ? f.w * s4.w / sv.w : f.w;
-                *o = f;
+            if (a.upd.mode != kUpdNone) {
+                *o = update4(a.upd, *o, s4, ((col * a.nz + z0) >> 2) + lane);
             } else if (a.accumulate) {
                 float4 f = *o;
                 f.x += s4.x;

@@ -89,6 +89,17 @@ struct BlurBackArgs {
     int* err;              // SPECT_ETIMEDOUT when a bounded wait runs out
 };
 
+// Image update at the end of a subiteration (update.cuh).
+constexpr int kUpdNone = 0, kUpdOsem = 1, kUpdOsl = 2, kUpdBsrem = 3;
+struct UpdateSpec {
+    int mode;              // kUpd*
+    const float* sens;     // H_m^T 1 of the subset
+    const float* grad;     // prior gradient grad V(x), or nullptr (zero)
+    const float* sens_all; // BSREM: H^T 1 over all angles
+    float beta_n;          // prior weight of the subiteration, beta / M
+    float step;            // BSREM: alpha_t * M
+};
+
 struct GatherArgs {
     const float* bvol;     // [batch][n_sel][n][n][nz]
     const int2* tab;       // [n_angles][n*n][kMaxCand] (row offset, weight bits)
@@ -97,7 +108,7 @@ struct GatherArgs {
     int lanes_per_col;     // 32, or the power of two >= nz/4 when nz/4 < 32
     float* out;            // [batch][n][n][nz]
     int accumulate;        // add into out instead of overwriting
-    const float* sens;     // OSEM update: x <- sens>0 ? x*bp/sens : x (x is `out`)
+    UpdateSpec upd;        // mode != kUpdNone: update x (`out`) with the finished back projection
 };
 
 // Tiled gather (gather_tiled.cu): T x T output columns per CTA, footprint
@@ -118,7 +129,7 @@ struct GatherTiledArgs {
     int stages;            // footprint buffers (angles in flight + 1)
     float* out;            // [batch][n][n][nz]
     int accumulate;
-    const float* sens;     // OSEM update, as GatherArgs
+    UpdateSpec upd;        // as GatherArgs
     int* err;
 };
 
@@ -181,7 +192,9 @@ constexpr int kReduceBlocks = 1024;  // largest grid of the reduction kernel
 cudaError_t launch_poisson_ll(const float* y, const float* p, float s, size_t count, double* block_part,
                               int n_blocks, double* ll, float* grad, cudaStream_t st);
 cudaError_t launch_fill(float* dst, size_t count, float value, cudaStream_t st);
-cudaError_t launch_update(float* x, const float* bp, const float* sens, size_t count, cudaStream_t st);
+cudaError_t launch_update(float* x, const float* bp, const UpdateSpec& u, size_t count, cudaStream_t st);
+cudaError_t launch_prior_grad(const float* x, float* grad, int n, int nz, int prior, float delta, float gamma,
+                              cudaStream_t st);
 
 }  // namespace spect
 
@@ -213,6 +226,9 @@ struct spect_plan {
     int2* d_gtab = nullptr;                   // adjoint-rotation gather tables: [na][n*n][kMaxCand], or
                                               // tiled [na][gt_tiles][gt_T^2][kMaxCand]
     int* d_gdesc = nullptr;                   // tiled gather footprints [na][gt_tiles][kFpDescInts]
+    float* d_grad = nullptr;                  // MAP: prior gradient (allocated by the first MAP call)
+    float* d_sens_all = nullptr;              // BSREM: H^T 1 over all angles (first BSREM call)
+    bool sens_all_ok = false;                 // d_sens_all matches the current attenuation map
     int* d_gwork = nullptr;                   // tiled gather: largest footprint (rows)
     bool gather_tiled = false;                // footprints staged in shared memory
     int gt_T = 0, gt_tiles = 0, gt_zs = 0, gt_rows = 0, gt_stages = 2;

@@ -3,6 +3,7 @@
 
 #include "geometry.cuh"
 #include "internal.h"
+#include "update.cuh"
 
 namespace spect {
 
@@ -245,22 +246,79 @@ cudaError_t launch_fill(float* dst, size_t count, float value, cudaStream_t st)
 
 namespace spect {
 
-// OSEM update (Table 1, OSEM row): x <- x * bp / sens where sens > 0.
-__global__ void update_kernel(float* __restrict__ x, const float* __restrict__ bp, const float* __restrict__ sens,
-                              size_t count)
+// The subiteration's image update (update.cuh) where the back projection
+// was gathered into a separate buffer.
+__global__ void update_kernel(float* __restrict__ x, const float* __restrict__ bp, UpdateSpec u, size_t count)
 {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-        const float sv = sens[i];
-        if (sv > 0.f) x[i] = x[i] * bp[i] / sv;
+        const float gv = u.grad ? u.grad[i] : 0.f;
+        const float sa = u.sens_all ? u.sens_all[i] : 0.f;
+        x[i] = update1(u, x[i], bp[i], u.sens[i], gv, sa);
     }
 }
 
-cudaError_t launch_update(float* x, const float* bp, const float* sens, size_t count, cudaStream_t st)
+cudaError_t launch_update(float* x, const float* bp, const UpdateSpec& u, size_t count, cudaStream_t st)
 {
     size_t blocks = (count + 255) / 256;
     if (blocks > 8192) blocks = 8192;
     if (blocks == 0) return cudaSuccess;
-    update_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, bp, sens, count);
+    update_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, bp, u, count);
+    return cudaGetLastError();
+}
+
+// Gradient of a nearest-neighbour prior (Sec. 2.1.3, Table 1):
+//   V(x) = sum_r sum_s w_rs phi(x_r, x_s),  s over the 26 neighbours of r
+//   inside the volume, w_rs = 1 / |r - s|;
+//   dV/dx_r = 2 sum_s w_rs dphi(x_r, x_s)/dx_r  (phi symmetric), with
+//   quadratic  phi = ((a - b)/delta)^2 / 4:  dphi/da = (a - b) / (2 delta^2);
+//   RDP  phi = (a - b)^2 / (a + b + gamma|a - b|):
+//        dphi/da = (a - b)(a + 3b + gamma|a - b|) / (a + b + gamma|a - b|)^2,
+//   a pair whose RDP denominator is 0 contributing 0.  One thread per voxel,
+//   z fastest, neighbours through L1.
+__global__ void __launch_bounds__(256) prior_grad_kernel(const float* __restrict__ x, float* __restrict__ grad, int n,
+                                                         int nz, int prior, float delta, float gamma)
+{
+    const size_t vol = (size_t)n * n * nz;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= vol) return;
+    const int k = (int)(idx % nz);
+    const int j = (int)((idx / nz) % n);
+    const int i = (int)(idx / ((size_t)nz * n));
+    const float a = x[idx];
+    const float inv2d2 = 1.f / (2.f * delta * delta);
+    const float wt[4] = {0.f, 1.f, 1.f / sqrtf(2.f), 1.f / sqrtf(3.f)};
+    float g = 0.f;
+#pragma unroll
+    for (int di = -1; di <= 1; ++di)
+#pragma unroll
+        for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+            for (int dk = -1; dk <= 1; ++dk) {
+                if (!di && !dj && !dk) continue;
+                const int i2 = i + di, j2 = j + dj, k2 = k + dk;
+                if (i2 < 0 || i2 >= n || j2 < 0 || j2 >= n || k2 < 0 || k2 >= nz) continue;
+                const float b = __ldg(x + ((size_t)i2 * n + j2) * nz + k2);
+                const float w = wt[di * di + dj * dj + dk * dk];
+                const float d = a - b;
+                float t;
+                if (prior == SPECT_PRIOR_QUADRATIC) {
+                    t = d * inv2d2;
+                } else {
+                    const float ad = fabsf(d);
+                    const float S = a + b + gamma * ad;
+                    t = S != 0.f ? d * (a + 3.f * b + gamma * ad) / (S * S) : 0.f;
+                }
+                g = fmaf(2.f * w, t, g);
+            }
+    grad[idx] = g;
+}
+
+cudaError_t launch_prior_grad(const float* x, float* grad, int n, int nz, int prior, float delta, float gamma,
+                              cudaStream_t st)
+{
+    const size_t vol = (size_t)n * n * nz;
+    if (vol == 0) return cudaSuccess;
+    prior_grad_kernel<<<(unsigned)((vol + 255) / 256), 256, 0, st>>>(x, grad, n, nz, prior, delta, gamma);
     return cudaGetLastError();
 }
 

@@ -304,18 +304,18 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
 // x_out (per batch entry) = sum over sel of H_a^T proj_a, optionally fused with
 // the OSEM update x_out <- x_out * bp / sens (then batch must be 1).
 int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev, int n_sel, int batch,
-             const float* sens_update, cudaStream_t st)
+             const UpdateSpec* upd, cudaStream_t st)
 {
     const size_t vol = vol_elems(p), plane = plane_elems(p);
     const int gmax = (int)std::min<size_t>(16, p->bvol_cap);
-    const bool fused = sens_update && n_sel <= gmax;
+    const bool fused = upd && n_sel <= gmax;
     // Angle groups of a fixed size (independent of the batch, so that each
     // volume is summed in the same order alone or in a batch), and as many
     // batch entries per launch as the rotated-frame buffer holds.
     const int G = std::min(gmax, n_sel);
     const int bper = std::max(1, std::min(batch, (int)(p->bvol_cap / G)));
     for (int b0 = 0; b0 < batch; b0 += bper) {
-        float* out_b = (sens_update && !fused) ? p->d_bp : x_out + (size_t)b0 * vol;
+        float* out_b = (upd && !fused) ? p->d_bp : x_out + (size_t)b0 * vol;
         const int nb = std::min(bper, batch - b0);
         for (int g0 = 0; g0 < n_sel; g0 += G) {
             const int ng = std::min(G, n_sel - g0);
@@ -374,9 +374,9 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
                 gt.stages = p->gt_stages;
                 gt.out = out_b;
                 gt.accumulate = g0 > 0;
-                gt.sens = fused ? sens_update : nullptr;
+                if (fused) gt.upd = *upd;
                 gt.err = p->d_err;
-                e = timed(p, gt.sens ? "gather_update" : "gather", st, 1, [&] { return launch_gather_tiled(gt, st); });
+                e = timed(p, fused ? "gather_update" : "gather", st, 1, [&] { return launch_gather_tiled(gt, st); });
                 if (e != cudaSuccess) return cuda_fail(e, "gather kernel launch");
                 continue;
             }
@@ -395,12 +395,12 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
             }
             ga.out = out_b;
             ga.accumulate = g0 > 0;
-            ga.sens = fused ? sens_update : nullptr;
-            e = timed(p, ga.sens ? "gather_update" : "gather", st, 1, [&] { return launch_gather(ga, st); });
+            if (fused) ga.upd = *upd;
+            e = timed(p, fused ? "gather_update" : "gather", st, 1, [&] { return launch_gather(ga, st); });
             if (e != cudaSuccess) return cuda_fail(e, "gather kernel launch");
         }
-        if (sens_update && !fused) {
-            cudaError_t e = timed(p, "update", st, 1, [&] { return launch_update(x_out + (size_t)b0 * vol, p->d_bp, sens_update, vol, st); });
+        if (upd && !fused) {
+            cudaError_t e = timed(p, "update", st, 1, [&] { return launch_update(x_out + (size_t)b0 * vol, p->d_bp, *upd, vol, st); });
             if (e != cudaSuccess) return cuda_fail(e, "update kernel launch");
         }
     }
@@ -450,7 +450,67 @@ int osem_core(spect_plan* plan, const float* y, float s, const float* s_dev, flo
             });
             if (e != cudaSuccess) return cuda_fail(e, "diag kernel launch");
         }
-        rc = run_back(plan, plan->d_ratio, x_inout, plan->d_sel[m], ns, 1, plan->d_sens + (size_t)m * vol, st);
+        UpdateSpec u{};
+        u.mode = kUpdOsem;
+        u.sens = plan->d_sens + (size_t)m * vol;
+        rc = run_back(plan, plan->d_ratio, x_inout, plan->d_sel[m], ns, 1, &u, st);
+        if (rc) return rc;
+    }
+    return SPECT_OK;
+}
+
+// OSMAPOSL / BSREM subiterations (Eq. PGA, Table 1): per subiteration the
+// ratio y / (H_m x + s), the prior gradient of the current image, then the
+// back projection with the MAP update fused into the gather.
+int map_core(spect_plan* plan, const float* y, float s, float* x_inout, int first_subiter, int n_subiters,
+             const spect_map_params* mp, void* stream)
+{
+    if (int rc = check_plan(plan)) return rc;
+    if (!mp) return fail(SPECT_EINVAL, "params is NULL");
+    if (mp->algorithm != SPECT_ALG_OSMAPOSL && mp->algorithm != SPECT_ALG_BSREM)
+        return fail(SPECT_EINVAL, "unknown algorithm %d", mp->algorithm);
+    if (mp->prior < SPECT_PRIOR_NONE || mp->prior > SPECT_PRIOR_RDP) return fail(SPECT_EINVAL, "unknown prior %d", mp->prior);
+    if (mp->prior == SPECT_PRIOR_QUADRATIC && !(mp->delta > 0.f)) return fail(SPECT_EINVAL, "delta must be > 0");
+    if (mp->prior == SPECT_PRIOR_RDP && !(mp->gamma >= 0.f)) return fail(SPECT_EINVAL, "gamma must be >= 0");
+    if (!(mp->beta >= 0.f)) return fail(SPECT_EINVAL, "beta must be >= 0");
+    if (mp->algorithm == SPECT_ALG_BSREM && !(mp->alpha0 > 0.f)) return fail(SPECT_EINVAL, "alpha0 must be > 0");
+    if (!y || !x_inout) return fail(SPECT_EINVAL, "y and x_inout must be device pointers");
+    if (!aligned16(y) || !aligned16(x_inout)) return fail(SPECT_EINVAL, "y and x_inout must be 16-byte aligned");
+    if (first_subiter < 0 || n_subiters < 0) return fail(SPECT_EINVAL, "negative subiteration range");
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t vol = vol_elems(plan);
+    int rc;
+    if (!plan->d_grad && ((rc = dev_alloc(plan, &plan->d_grad, vol)))) return rc;
+    if (mp->algorithm == SPECT_ALG_BSREM && !plan->sens_all_ok) {
+        if (!plan->d_sens_all && ((rc = dev_alloc(plan, &plan->d_sens_all, vol)))) return rc;
+        rc = run_back(plan, nullptr, plan->d_sens_all, plan->d_sel_all, plan->na, 1, nullptr, st);
+        if (rc) return rc;
+        plan->sens_all_ok = true;
+    }
+    const float c = 1.f / (float)plan->M;
+    for (int t = first_subiter; t < first_subiter + n_subiters; ++t) {
+        const int m = t % plan->M;
+        const int ns = (int)plan->subsets[m].size();
+        rc = run_forward(plan, x_inout, plan->d_ratio, plan->d_sel[m], ns, 1, y, s, nullptr, nullptr, st);
+        if (rc) return rc;
+        UpdateSpec u{};
+        u.mode = mp->algorithm == SPECT_ALG_OSMAPOSL ? kUpdOsl : kUpdBsrem;
+        u.sens = plan->d_sens + (size_t)m * vol;
+        u.beta_n = mp->beta * c;
+        if (mp->prior != SPECT_PRIOR_NONE) {
+            cudaError_t e = timed(plan, "prior_grad", st, 1, [&] {
+                return launch_prior_grad(x_inout, plan->d_grad, plan->n, plan->nz, mp->prior, mp->delta, mp->gamma, st);
+            });
+            if (e != cudaSuccess) return cuda_fail(e, "prior gradient kernel");
+            u.grad = plan->d_grad;
+        }
+        if (u.mode == kUpdBsrem) {
+            u.sens_all = plan->d_sens_all;
+            u.step = mp->alpha0 / (1.f + (float)(t / plan->M)) / c;
+        }
+        rc = run_back(plan, plan->d_ratio, x_inout, plan->d_sel[m], ns, 1, &u, st);
         if (rc) return rc;
     }
     return SPECT_OK;
@@ -822,7 +882,27 @@ int spect_plan_set_mu(spect_plan* plan, const float* mu_dev, void* stream)
         return fail(SPECT_EINVAL, "the plan models attenuation: mu must be a 16-byte aligned device pointer");
     DeviceGuard guard(plan->device);
     if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
+    plan->sens_all_ok = false;  // BSREM's H^T 1 follows the attenuation map
     return refresh_mu(plan, mu_dev, static_cast<cudaStream_t>(stream));
+}
+
+int spect_map_run(spect_plan* plan, const float* y, float s, float* x_inout, int first_subiter, int n_subiters,
+                  const spect_map_params* params, void* stream)
+{
+    return map_core(plan, y, s, x_inout, first_subiter, n_subiters, params, stream);
+}
+
+int spect_prior_grad(const float* x, int n, int nz, int prior, float delta, float gamma, float* grad_out,
+                     void* stream)
+{
+    if (!x || !grad_out) return fail(SPECT_EINVAL, "x and grad_out must be device pointers");
+    if (n <= 0 || nz <= 0) return fail(SPECT_EINVAL, "bad volume size %d x %d x %d", n, n, nz);
+    if (prior != SPECT_PRIOR_QUADRATIC && prior != SPECT_PRIOR_RDP) return fail(SPECT_EINVAL, "unknown prior %d", prior);
+    if (prior == SPECT_PRIOR_QUADRATIC && !(delta > 0.f)) return fail(SPECT_EINVAL, "delta must be > 0");
+    if (prior == SPECT_PRIOR_RDP && !(gamma >= 0.f)) return fail(SPECT_EINVAL, "gamma must be >= 0");
+    cudaError_t e = launch_prior_grad(x, grad_out, n, nz, prior, delta, gamma, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "prior gradient kernel");
+    return SPECT_OK;
 }
 
 int spect_poisson_ll(spect_plan* plan, const float* y, const float* p, float s, size_t count, double* ll_dev,

@@ -35,6 +35,11 @@ SPECT_FLAG_PSF = 2
 SPECT_FLAG_PSF_BF16 = 4
 SPECT_FLAG_ATTEN_F64 = 8
 
+SPECT_PRIOR_NONE, SPECT_PRIOR_QUADRATIC, SPECT_PRIOR_RDP = 0, 1, 2
+SPECT_ALG_OSMAPOSL, SPECT_ALG_BSREM = 1, 2
+PRIORS = {"none": SPECT_PRIOR_NONE, "quadratic": SPECT_PRIOR_QUADRATIC, "rdp": SPECT_PRIOR_RDP}
+ALGORITHMS = {"osmaposl": SPECT_ALG_OSMAPOSL, "bsrem": SPECT_ALG_BSREM}
+
 # Every symbol include/spect.h declares (checked by the CPU test suite).
 EXPORTED = [
     "spect_plan_create", "spect_plan_destroy", "spect_plan_query", "spect_subset_size", "spect_subset_angles",
@@ -42,6 +47,7 @@ EXPORTED = [
     "spect_status_str", "spect_last_error", "spect_version",
     "spect_profile_enable", "spect_profile_read", "spect_kernel_launches",
     "spect_poisson_ll_noalloc", "spect_plan_check", "spect_plan_set_mu", "spect_osem_run_dev",
+    "spect_map_run", "spect_prior_grad",
     "spect_serve_create", "spect_serve_submit", "spect_serve_poll", "spect_serve_wait",
     "spect_serve_cancel", "spect_serve_stats_get", "spect_serve_destroy",
 ]
@@ -51,6 +57,11 @@ class SpectError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(message)
         self.status = status
+
+
+class _MapParams(ctypes.Structure):
+    _fields_ = [("algorithm", ctypes.c_int), ("prior", ctypes.c_int), ("beta", ctypes.c_float),
+                ("delta", ctypes.c_float), ("gamma", ctypes.c_float), ("alpha0", ctypes.c_float)]
 
 
 class _Geom(ctypes.Structure):
@@ -104,6 +115,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.spect_back.argtypes = [vp, vp, vp, i, i, vp]
         lib.spect_sensitivity.argtypes = [vp, i, vp, vp]
         lib.spect_osem_run.argtypes = [vp, vp, f, vp, i, i, vp, vp]
+        lib.spect_map_run.argtypes = [vp, vp, f, vp, i, i, ctypes.POINTER(_MapParams), vp]
+        lib.spect_prior_grad.argtypes = [vp, i, i, i, f, f, vp, vp]
         lib.spect_osem_run_dev.argtypes = [vp, vp, vp, vp, i, i, vp, vp]
         lib.spect_plan_set_mu.argtypes = [vp, vp, vp]
         lib.spect_poisson_ll.argtypes = [vp, vp, vp, f, ctypes.c_size_t, vp, vp, vp]
@@ -251,6 +264,22 @@ def spect_osem_run_dev(plan: int, y: torch.Tensor, s_dev: torch.Tensor, x: torch
                                      _dptr(diag, torch.float64), _stream(stream)))
 
 
+def spect_map_run(plan: int, y: torch.Tensor, s: float, x: torch.Tensor, first_subiter: int, n_subiters: int,
+                  algorithm: str, prior: str, beta: float, delta: float = 1.0, gamma: float = 2.0,
+                  alpha0: float = 1.0, stream=None):
+    mp = _MapParams(ALGORITHMS[algorithm], PRIORS[prior], beta, delta, gamma, alpha0)
+    _check(load().spect_map_run(plan, _dptr(y), float(s), _dptr(x), first_subiter, n_subiters, ctypes.byref(mp),
+                                _stream(stream)))
+
+
+def spect_prior_grad(x: torch.Tensor, prior: str, grad: torch.Tensor, delta: float = 1.0, gamma: float = 2.0,
+                     stream=None):
+    if x.dim() != 3 or x.shape[0] != x.shape[1] or grad.shape != x.shape:
+        raise SpectError(SPECT_EINVAL, "x must be [n][n][nz] and grad the same shape")
+    _check(load().spect_prior_grad(_dptr(x), x.shape[0], x.shape[2], PRIORS[prior], float(delta), float(gamma),
+                                   _dptr(grad), _stream(stream)))
+
+
 def spect_plan_set_mu(plan: int, mu: Optional[torch.Tensor], stream=None):
     _check(load().spect_plan_set_mu(plan, _dptr(mu), _stream(stream)))
 
@@ -356,6 +385,12 @@ class Plan:
         d = torch.zeros((max(count, 1), 3), device=x.device, dtype=torch.float64) if diag else None
         spect_osem_run(self.handle, y, s, x, first, count, d, stream)
         return d
+
+    def map(self, y: torch.Tensor, s: float, x: torch.Tensor, first: int, count: int, algorithm: str = "bsrem",
+            prior: str = "rdp", beta: float = 0.3, delta: float = 1.0, gamma: float = 2.0, alpha0: float = 1.0,
+            stream=None):
+        """OSMAPOSL / BSREM subiterations with a nearest-neighbour prior (include/spect.h)."""
+        spect_map_run(self.handle, y, s, x, first, count, algorithm, prior, beta, delta, gamma, alpha0, stream)
 
     def poisson_ll(self, y: torch.Tensor, p: torch.Tensor, s: float, grad: bool = False, stream=None):
         ll = torch.zeros(1, device=p.device, dtype=torch.float64)
