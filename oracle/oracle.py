@@ -75,6 +75,8 @@ def _load():
             lib.or_prior_value.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
             lib.or_prior_grad.restype = None
             lib.or_prior_grad.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
+            lib.or_set_orbit.restype = None
+            lib.or_set_orbit.argtypes = [_dp, ctypes.c_int]
             lib.or_map.restype = None
             lib.or_map.argtypes = ([_dp, ctypes.c_double] + geom_args + [ctypes.c_int] * 5 +
                                    [ctypes.c_double] * 4 + [_dp])
@@ -104,7 +106,9 @@ class Geom:
     mu: optional attenuation map [n][n][nz] in 1/cm;
     use_psf: depth-dependent Gaussian blur on/off;
     sigma0, slope: sigma_i = sigma0 + slope * d_i with d_i = n - i - 0.5 + det_offset;
-    nsigma: truncation radius R_i = ceil(nsigma * sigma_i).
+    nsigma: truncation radius R_i = ceil(nsigma * sigma_i);
+    det_offsets: optional per-angle detector offsets (a non-circular orbit):
+    d_i(a) = n - i - 0.5 + det_offsets[a] replaces det_offset for angle a.
     """
 
     n: int
@@ -118,8 +122,14 @@ class Geom:
     slope: float = 0.03
     nsigma: float = 3.0
     det_offset: float = 0.0
+    det_offsets: Optional[Sequence[float]] = None
 
     def _args(self):
+        # the orbit travels through the oracle's module state, set for every call
+        orb = None if self.det_offsets is None else _f64(self.det_offsets)
+        if orb is not None:
+            assert orb.size == self.n_angles
+        _load().or_set_orbit(_ptr(orb), int(self.n_angles))
         ang = None if self.angles is None else _f64(self.angles)
         mu = None if self.mu is None else _f64(self.mu).reshape(self.n, self.n, self.nz)
         self._keep = (ang, mu)  # keep the buffers alive for the call

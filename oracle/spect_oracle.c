@@ -26,7 +26,9 @@
  *   - default angles theta_n = 2*pi*n / n_angles.
  *   - attenuation: detector on the +x side; with tau = voxel_cm * (R_n mu),
  *       A[i] = exp( -( sum_{i'>i} tau[i'] + tau[i]/2 ) )   (mid-voxel rule).
- *   - PSF: d_i = n - i - 0.5 + det_offset (voxels),
+ *   - PSF: d_i = n - i - 0.5 + det_offset (voxels), or with a non-circular
+ *     orbit (or_set_orbit) d_i(a) = n - i - 0.5 + det_offsets[a] for angle a
+ *     (the detector's distance varies with the angle),
  *       sigma_i = sigma0 + slope * d_i,  R_i = ceil(nsigma * sigma_i),
  *       w_i(t) = exp(-t^2 / (2 sigma_i^2)) for |t| <= R_i, normalised to sum 1,
  *     2-D kernel w_i(t) w_i(u) over (j,k), zero padding at the edges.
@@ -231,6 +233,24 @@ void or_attenuation(const double* mu, int n, int nz, double theta, double voxel_
 
 /* ---------------------------------------------------------------- H, H^T */
 
+/* Non-circular orbit (Sec. 2.1.1, the per-angle detector geometry of T_cdr):
+ * per-angle detector offsets in voxels, or none (every angle uses the
+ * geometry's det_offset).  Test infrastructure state, set by or_set_orbit. */
+static double* g_orbit = NULL;
+static int g_orbit_n = 0;
+
+void or_set_orbit(const double* det_offsets, int n_angles)
+{
+    free(g_orbit);
+    g_orbit = NULL;
+    g_orbit_n = 0;
+    if (det_offsets && n_angles > 0) {
+        g_orbit = (double*)malloc(sizeof(double) * (size_t)n_angles);
+        memcpy(g_orbit, det_offsets, sizeof(double) * (size_t)n_angles);
+        g_orbit_n = n_angles;
+    }
+}
+
 typedef struct {
     int n, nz, n_angles;
     const double* angles;  /* NULL: uniform */
@@ -250,6 +270,16 @@ static void forward_one(const or_geom* g, const double* f, int angle, double* pr
     double theta = angle_of(angle, g->n_angles, g->angles);
     double* rot = (double*)malloc(sizeof(double) * vol);
     double* blurred = (double*)malloc(sizeof(double) * vol);
+    double* own_taps = NULL;
+    int* own_rad = NULL;
+    if (g->use_psf && g_orbit && angle < g_orbit_n) {      /* this angle's own PSF table */
+        rmax = or_psf_rmax(n, g->sigma0, g->slope, g->nsigma, g_orbit[angle]);
+        own_taps = (double*)malloc(sizeof(double) * (size_t)n * (2 * rmax + 1));
+        own_rad = (int*)malloc(sizeof(int) * (size_t)n);
+        or_psf_taps(n, g->sigma0, g->slope, g->nsigma, g_orbit[angle], rmax, NULL, own_rad, own_taps);
+        taps = own_taps;
+        radius = own_rad;
+    }
     or_rotate(f, n, nz, theta, rot);                       /* T_rot */
     if (g->mu) {                                           /* T_att */
         double* A = (double*)malloc(sizeof(double) * vol);
@@ -273,6 +303,8 @@ static void forward_one(const or_geom* g, const double* f, int angle, double* pr
         for (size_t q = 0; q < plane; ++q) proj[q] += blurred[(size_t)i * plane + q];
     free(rot);
     free(blurred);
+    free(own_taps);
+    free(own_rad);
 }
 
 /* Per-angle back projection H_n^T q, ADDED into out: the transpose of each
@@ -286,6 +318,16 @@ static void back_one(const or_geom* g, const double* q, int angle, double* out,
     double theta = angle_of(angle, g->n_angles, g->angles);
     double* b = (double*)malloc(sizeof(double) * vol);
     double* r = (double*)malloc(sizeof(double) * vol);
+    double* own_taps = NULL;
+    int* own_rad = NULL;
+    if (g->use_psf && g_orbit && angle < g_orbit_n) {      /* this angle's own PSF table */
+        rmax = or_psf_rmax(n, g->sigma0, g->slope, g->nsigma, g_orbit[angle]);
+        own_taps = (double*)malloc(sizeof(double) * (size_t)n * (2 * rmax + 1));
+        own_rad = (int*)malloc(sizeof(int) * (size_t)n);
+        or_psf_taps(n, g->sigma0, g->slope, g->nsigma, g_orbit[angle], rmax, NULL, own_rad, own_taps);
+        taps = own_taps;
+        radius = own_rad;
+    }
     if (g->use_psf) {
 #pragma omp parallel for schedule(dynamic)
         for (int i = 0; i < n; ++i) {
@@ -307,6 +349,8 @@ static void back_one(const or_geom* g, const double* q, int angle, double* out,
     for (size_t p = 0; p < vol; ++p) out[p] += r[p];
     free(b);
     free(r);
+    free(own_taps);
+    free(own_rad);
 }
 
 static or_geom make_geom(int n, int nz, int n_angles, const double* angles, double voxel_cm,

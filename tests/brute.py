@@ -59,15 +59,18 @@ def forward_lib(f, theta, mu, voxel_cm, use_psf, sigma0, slope, nsigma, det_offs
     return p.sum(axis=0)
 
 
-def dense_h(n, nz, angles, mu, voxel_cm, use_psf, sigma0, slope, nsigma, det_offset=0.0) -> np.ndarray:
-    """Dense H of shape [len(angles)*n*nz, n*n*nz] (rows: angle, bin y, bin z)."""
+def dense_h(n, nz, angles, mu, voxel_cm, use_psf, sigma0, slope, nsigma, det_offset=0.0,
+            det_offsets=None) -> np.ndarray:
+    """Dense H of shape [len(angles)*n*nz, n*n*nz] (rows: angle, bin y, bin z).
+    det_offsets (optional): a detector offset per angle (non-circular orbit)."""
     nvox = n * n * nz
     cols = []
     for q in range(nvox):
         e = np.zeros(nvox)
         e[q] = 1.0
         e = e.reshape(n, n, nz)
-        col = [forward_lib(e, th, mu, voxel_cm, use_psf, sigma0, slope, nsigma, det_offset).ravel()
-               for th in angles]
+        col = [forward_lib(e, th, mu, voxel_cm, use_psf, sigma0, slope, nsigma,
+                           det_offset if det_offsets is None else det_offsets[a]).ravel()
+               for a, th in enumerate(angles)]
         cols.append(np.concatenate(col))
     return np.stack(cols, axis=1)
