@@ -84,6 +84,10 @@ typedef struct spect_geom {
     float det_offset;         /* extra detector distance, voxels */
     int n_subsets;            /* M >= 1 (ordered subsets) */
     unsigned flags;           /* SPECT_FLAG_* */
+    const float* det_offsets; /* host array [n_angles] or NULL: a non-circular orbit, the
+                                 detector offset of each angle in voxels (replaces
+                                 det_offset; each angle gets its own PSF table, T_cdr of
+                                 Eq. 1 with d_i = n - i - 0.5 + det_offsets[a]) */
 } spect_geom;
 
 typedef struct spect_plan spect_plan;

@@ -19,6 +19,7 @@ constexpr int kStrip = 16;           // outputs per thread along one blur strip
 constexpr int kFwdThreads = 512;     // most threads of the forward / blur kernels
 constexpr int kMaxCand = 9;          // rotated-grid samples that can touch one voxel
 constexpr int kMaxIpt = 4;           // largest j-blur strips per thread
+constexpr int kTcTile = 128 * 128;   // BF16 Toeplitz tile, elements
 
 
 // Shape of one plane-blur launch: which columns of z a CTA owns and the
@@ -50,6 +51,8 @@ struct ForwardArgs {
     const float* taps;     // [n][kTapW] centred at kMaxR
     const int* rad;        // [n]
     const int* work;       // [n+1] prefix sums of the per-plane work estimate
+    size_t taps_stride;    // floats between the angles' tap tables (0: one table)
+    int rad_stride;        // ints between the angles' radius / work tables (0: one table)
     const int* sel;        // [n_sel] angle ids
     int n, nz, n_sel, batch;
     int chunks;            // depth chunks: contiguous plane ranges of equal work
@@ -81,6 +84,8 @@ struct BlurBackArgs {
     const float* taps;
     const int* rad;
     const int* work;       // [n+1] prefix sums of the per-plane work estimate
+    size_t taps_stride;    // as ForwardArgs
+    int rad_stride;
     const int* sel;        // [n_sel] angle ids
     int n, nz, n_sel, batch;
     int chunks;            // depth chunks: contiguous plane ranges of equal work
@@ -141,6 +146,7 @@ struct ForwardBf16Args {
     const float* atten;
     const float2* cs;
     const uint16_t* ttab;
+    size_t ttab_stride;    // elements between the angles' Toeplitz tile sets (0: one set)
     const int* sel;
     int n, nz, n_sel, batch, chunks;
     uint32_t tmem_cols;
@@ -154,6 +160,7 @@ struct BlurBackBf16Args {
     size_t proj_bstride;
     const float* atten;
     const uint16_t* ttab;
+    size_t ttab_stride;    // elements between the angles' Toeplitz tile sets (0: one set)
     const int* sel;
     int n, nz, n_sel, batch, chunks;
     uint32_t tmem_cols;
@@ -208,7 +215,8 @@ struct spect_plan {
     int device = 0, num_sms = 0;
     std::vector<double> angles;
     std::vector<std::vector<int>> subsets;  // host angle lists
-    std::vector<int> rad;                   // host PSF radius per depth plane
+    std::vector<int> rad;                   // host PSF radius per depth plane (per table)
+    int psf_tables = 1;                     // PSF tables: n_angles for a non-circular orbit, else 1
     int max_subset = 0;
     spect::PlaneTiling tiling{};
     int fwd_occ = 1;         // resident forward CTAs per SM

@@ -395,6 +395,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1) forward_kernel(ForwardArgs a)
     const int chunk = blockIdx.x % a.chunks, tile = blockIdx.x / a.chunks;
     const int sidx = blockIdx.y, b = blockIdx.z;
     const int angle = a.sel[sidx];
+    // this angle's PSF tables (a non-circular orbit has one per angle)
+    const float* taps_g = a.taps + (size_t)angle * a.taps_stride;
+    const int* rad_g = a.rad + (size_t)angle * a.rad_stride;
+    const int* work_g = a.work + (size_t)angle * a.rad_stride;
     const float2 cs = a.cs[angle];
     const float c = 0.5f * (float)(n - 1);
     const int kt0 = tile * t.ktile;
@@ -429,10 +433,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1) forward_kernel(ForwardArgs a)
 
     const float* xb = a.x + (size_t)b * n * n * nz;
     int i_lo, i_hi;
-    chunk_range(a.work, n, a.chunks, chunk, i_lo, i_hi);
+    chunk_range(work_g, n, a.chunks, chunk, i_lo, i_hi);
     TapPrefetch tp;
     if (i_lo < i_hi) {
-        tp.load(a.taps, i_lo);
+        tp.load(taps_g, i_lo);
         tp.store(taps_s, i_lo);  // visible after the first barrier below
     }
     __syncthreads();  // barrier initialised
@@ -442,7 +446,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) forward_kernel(ForwardArgs a)
     bool timed_out = false;
     for (int i = i_lo; i < i_hi; ++i) {
         if (i + 1 < i_hi) {
-            tp.load(a.taps, i + 1);
+            tp.load(taps_g, i + 1);
             if (aplane && !abuf) prefetch_plane_l2(aplane + (size_t)(i + 1) * n * nz, n, nz, klo, khi);
         }
         // ---- stage the rotated, attenuated plane (T_rot, T_att)
@@ -469,7 +473,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) forward_kernel(ForwardArgs a)
         }
         // ---- blur along z and y, accumulate over depth (T_cdr, P_x)
         const float* trow = taps_s + (i & 1) * (kMaxR + 1);
-        switch (__ldg(a.rad + i)) {
+        switch (__ldg(rad_g + i)) {
 #define SPECT_FWD_CASE(RR) \
     case RR: fwd_blur_plane<RR, IPT>(P, Q, t, z0, jq, trow, acc); break;
             SPECT_R_CASES(SPECT_FWD_CASE)
@@ -584,6 +588,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1) blur_back_kernel(BlurBackArgs 
     const int chunk = blockIdx.x % a.chunks, tile = blockIdx.x / a.chunks;
     const int sidx = blockIdx.y, b = blockIdx.z;
     const int angle = a.sel[sidx];
+    // this angle's PSF tables (a non-circular orbit has one per angle)
+    const float* taps_g = a.taps + (size_t)angle * a.taps_stride;
+    const int* rad_g = a.rad + (size_t)angle * a.rad_stride;
+    const int* work_g = a.work + (size_t)angle * a.rad_stride;
     const int kt0 = tile * t.ktile;
     const int KT = min(t.ktile, nz - kt0);
     const int kw0 = kt0 - t.rh;
@@ -631,10 +639,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1) blur_back_kernel(BlurBackArgs 
         }
     }
     int i_lo, i_hi;
-    chunk_range(a.work, n, a.chunks, chunk, i_lo, i_hi);
+    chunk_range(work_g, n, a.chunks, chunk, i_lo, i_hi);
     TapPrefetch tp;
     if (i_lo < i_hi) {
-        tp.load(a.taps, i_lo);
+        tp.load(taps_g, i_lo);
         tp.store(taps_s, i_lo);
     }
     if (abuf && tid == 0) {
@@ -651,13 +659,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1) blur_back_kernel(BlurBackArgs 
     bool timed_out = false;
     for (int i = i_lo; i < i_hi; ++i) {
         if (i + 1 < i_hi) {
-            tp.load(a.taps, i + 1);
+            tp.load(taps_g, i + 1);
             if (aplane && !abuf) prefetch_plane_l2(aplane + (size_t)(i + 1) * n * nz, n, nz, kt0, kt0 + KT);
         }
         const float* trow = taps_s + (i & 1) * (kMaxR + 1);
         const float* aglob = aplane ? aplane + (size_t)i * n * nz : nullptr;
         bool ok = true;
-        switch (__ldg(a.rad + i)) {
+        switch (__ldg(rad_g + i)) {
 #define SPECT_BACK_CASE(RR) \
     case RR: ok = back_blur_plane<RR, IPT, kSmemA>(P, Q, t, a, z0, trow, i, aglob, As, bar, parity, kt0, KT, bvol); break;
             SPECT_R_CASES(SPECT_BACK_CASE)

@@ -382,6 +382,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
     const int n = a.n, nz = a.nz;
     const int chunk = blockIdx.x, sidx = blockIdx.y, b = blockIdx.z;
     const int angle = a.sel[sidx];
+    const uint16_t* ttab = a.ttab + (size_t)angle * a.ttab_stride;  // this angle's tiles
     const float2 cs = a.cs[angle];
     const float c = 0.5f * (float)(n - 1);
     const uint32_t ncols = a.tmem_cols;
@@ -405,7 +406,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
     if (i < n) {
         const float* arow = a.atten ? a.atten + ((size_t)angle * n + i) * n * nz : nullptr;
         if (a.atten && i + a.chunks < n) tc_prefetch_plane(arow + (size_t)a.chunks * n * nz, n, nz);
-        if (threadIdx.x == 0) tma_load_1d(st.s.tap, a.ttab + (size_t)i * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
+        if (threadIdx.x == 0) tma_load_1d(st.s.tap, ttab + (size_t)i * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
         tc_tap_rows(rows, n, nz, i, cs, c);
         __syncthreads();
         tc_stage_plane(st.s.b1, st.s.b1_lo, rows, xb, arow, n, nz);
@@ -432,7 +433,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
             // fetch those of the next plane behind the staging below
             if (inext < n) {
                 ok2 = mbar_wait(st.s.bar_2, ph_2);
-                if (ok2) tma_load_1d(st.s.tap, a.ttab + (size_t)inext * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
+                if (ok2) tma_load_1d(st.s.tap, ttab + (size_t)inext * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
             }
         }
         first = false;
@@ -479,6 +480,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
     const int n = a.n, nz = a.nz;
     const int chunk = blockIdx.x, sidx = blockIdx.y, b = blockIdx.z;
     const int angle = a.sel[sidx];
+    const uint16_t* ttab = a.ttab + (size_t)angle * a.ttab_stride;  // this angle's tiles
     const uint32_t ncols = a.tmem_cols;
     TcState st;
     tc_setup(st, tsm, n, ncols);
@@ -496,7 +498,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
     int i = chunk;
     if (i < n && a.atten) tc_prefetch_plane(a.atten + ((size_t)angle * n + i) * n * nz, n, nz);
     if (i < n && threadIdx.x == 0)
-        tma_load_1d(st.s.tap, a.ttab + (size_t)i * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
+        tma_load_1d(st.s.tap, ttab + (size_t)i * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
     tc_stage_proj(st.s.b1, st.s.b1_lo, pr, n, nz);
     fence_async_smem();
     if (i < n) {
@@ -522,7 +524,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
         ph_2 ^= 1u;
         if (!ok) break;
         if (inext < n && threadIdx.x == 0)
-            tma_load_1d(st.s.tap, a.ttab + (size_t)inext * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
+            tma_load_1d(st.s.tap, ttab + (size_t)inext * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
         tc_fence_after();
         // B[i][j][k] = A[i][j][k] * (K_i r)[j][k]; D2 holds (K_i r)^T (lanes k)
         const float* arow = a.atten ? a.atten + ((size_t)angle * n + i) * n * nz : nullptr;

@@ -86,6 +86,7 @@ struct Request {
     uint64_t id = 0;
     spect_geom geom{};
     std::vector<double> angles;
+    std::vector<float> offsets;  // non-circular orbit, or empty
     float s = 0.f;
     int n_iters = 0;
     uint64_t tag = 0;
@@ -104,6 +105,7 @@ struct Request {
 struct Slot {
     spect_geom geom{};
     std::vector<double> angles;
+    std::vector<float> offsets;
     spect_plan* plan = nullptr;
     float* d_mu = nullptr;
     float* d_y = nullptr;
@@ -118,12 +120,12 @@ struct Slot {
     Request* req = nullptr;
 };
 
-bool same_geometry(const spect_geom& a, const std::vector<double>& aa, const spect_geom& b,
-                   const std::vector<double>& ba)
+bool same_geometry(const spect_geom& a, const std::vector<double>& aa, const std::vector<float>& ao,
+                   const spect_geom& b, const std::vector<double>& ba, const std::vector<float>& bo)
 {
     return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.voxel_cm == b.voxel_cm && a.n_angles == b.n_angles &&
            a.psf_sigma0 == b.psf_sigma0 && a.psf_slope == b.psf_slope && a.psf_nsigma == b.psf_nsigma &&
-           a.det_offset == b.det_offset && a.n_subsets == b.n_subsets && a.flags == b.flags && aa == ba;
+           a.det_offset == b.det_offset && a.n_subsets == b.n_subsets && a.flags == b.flags && aa == ba && ao == bo;
 }
 
 }  // namespace
@@ -166,7 +168,9 @@ size_t request_bytes(const spect_geom& g, int num_sms)
     b += std::max<size_t>(max_subset, 16) * vol * 4;                     // rotated-frame volumes
     b += max_subset * plane * 4 + vol * 4;                               // ratio, back projection
     if (g.flags & SPECT_FLAG_ATTEN) b += na * vol * 4;                   // attenuation cache
-    if (g.flags & SPECT_FLAG_PSF_BF16) b += n * 2 * 128 * 128 * 2;       // Toeplitz tiles
+    const size_t tables = g.det_offsets ? na : 1;                        // PSF tables (orbit)
+    if (g.flags & SPECT_FLAG_PSF_BF16) b += tables * n * 2 * 128 * 128 * 2;  // Toeplitz tiles
+    b += tables * n * (41 * 4 + 3 * 4);                                   // taps, radii, work
     b += 3 * vol * 4 + na * plane * 4;                                   // mu, x, y
     b += 1 << 20;                                                        // tables, small scratch
     return b;
@@ -193,6 +197,7 @@ int create_slot(spect_server* sv, Request* r, cudaStream_t st, Slot** out)
     if (!sl) return SPECT_ENOMEM;
     sl->geom = r->geom;
     sl->angles = r->angles;
+    sl->offsets = r->offsets;
     sl->vol = r->vol;
     sl->proj = r->proj;
     sl->bytes = r->bytes;
@@ -211,6 +216,7 @@ int create_slot(spect_server* sv, Request* r, cudaStream_t st, Slot** out)
     }
     spect_geom g = sl->geom;
     g.angles_rad = sl->angles.empty() ? nullptr : sl->angles.data();
+    g.det_offsets = sl->offsets.empty() ? nullptr : sl->offsets.data();
     int rc = spect_plan_create(&g, (g.flags & SPECT_FLAG_ATTEN) ? sl->d_mu : nullptr, st, &sl->plan);
     if (rc) {
         destroy_slot(sl);
@@ -305,7 +311,7 @@ void scheduler(spect_server* sv)
             }
             Slot* sl = nullptr;
             for (Slot* c : sv->slots)
-                if (!c->busy && same_geometry(c->geom, c->angles, r->geom, r->angles)) {
+                if (!c->busy && same_geometry(c->geom, c->angles, c->offsets, r->geom, r->angles, r->offsets)) {
                     sl = c;
                     break;
                 }
@@ -450,7 +456,9 @@ int spect_serve_submit(spect_server* sv, const spect_request* req, uint64_t* id)
     if (!r) return sfail(SPECT_ENOMEM, "host allocation failed");
     r->geom = g;
     r->geom.angles_rad = nullptr;
+    r->geom.det_offsets = nullptr;
     if (g.angles_rad) r->angles.assign(g.angles_rad, g.angles_rad + g.n_angles);
+    if (g.det_offsets) r->offsets.assign(g.det_offsets, g.det_offsets + g.n_angles);
     r->s = req->s;
     r->n_iters = req->n_iters;
     r->tag = req->tag;

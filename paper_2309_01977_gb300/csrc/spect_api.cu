@@ -154,19 +154,21 @@ float bf16_value(uint16_t h)
 // in the K-major 128-byte-swizzled layout of a 128 x 128 tile: K blocks of
 // 64 columns (16 KB apart), rows of 128 B, 8-row atoms of 1 KB in which the
 // 16-byte chunk c of row r sits at chunk c ^ (r % 8).
-void build_toeplitz_bf16(const spect_geom& g, int n, std::vector<uint16_t>& out)
+void build_toeplitz_bf16(const spect_geom& g, int n, double offset, std::vector<uint16_t>& all)
 {
     const int T = 128;
-    out.assign((size_t)n * 2 * T * T, 0);
+    const size_t base = all.size();
+    all.resize(base + (size_t)n * 2 * T * T, 0);
+    uint16_t* out = all.data() + base;
     for (int i = 0; i < n; ++i) {
-        const double d = (double)n - i - 0.5 + (double)g.det_offset;
+        const double d = (double)n - i - 0.5 + offset;
         const double s = (double)g.psf_sigma0 + (double)g.psf_slope * d;
         const int r = (int)std::ceil((double)g.psf_nsigma * s);
         std::vector<double> w(2 * r + 1);
         double sum = 0.0;
         for (int t = -r; t <= r; ++t) sum += (w[t + r] = std::exp(-(double)t * t / (2.0 * s * s)));
         for (double& v : w) v /= sum;
-        uint16_t* hi = out.data() + (size_t)i * 2 * T * T;
+        uint16_t* hi = out + (size_t)i * 2 * T * T;
         uint16_t* lo = hi + (size_t)T * T;
         for (int row = 0; row < T; ++row)
             for (int col = std::max(0, row - r); col <= std::min(T - 1, row + r); ++col) {
@@ -186,17 +188,21 @@ size_t plane_elems(const spect_plan* p) { return (size_t)p->n * p->nz; }
 
 // Host PSF table (Eq. 1, T_cdr): sigma_i = sigma0 + slope * (n - i - 0.5 + offset),
 // R_i = ceil(nsigma * sigma_i), taps exp(-t^2 / (2 sigma_i^2)) normalised in FP64.
-void build_psf(const spect_geom& g, int n, bool psf, std::vector<float>& taps, std::vector<int>& rad, int& rmax)
+// One angle's table (detector offset `offset`), appended to taps / rad.
+void build_psf(const spect_geom& g, int n, bool psf, double offset, std::vector<float>& all_taps,
+               std::vector<int>& all_rad, int& rmax)
 {
-    taps.assign((size_t)n * kTapW, 0.f);
-    rad.assign(n, 0);
-    rmax = 0;
+    const size_t tb = all_taps.size(), rb = all_rad.size();
+    all_taps.resize(tb + (size_t)n * kTapW, 0.f);
+    all_rad.resize(rb + (size_t)n, 0);
+    float* taps = all_taps.data() + tb;
+    int* rad = all_rad.data() + rb;
     for (int i = 0; i < n; ++i) {
         if (!psf) {
             taps[(size_t)i * kTapW + kMaxR] = 1.f;
             continue;
         }
-        const double d = (double)n - i - 0.5 + (double)g.det_offset;
+        const double d = (double)n - i - 0.5 + offset;
         const double s = (double)g.psf_sigma0 + (double)g.psf_slope * d;
         const int r = (int)std::ceil((double)g.psf_nsigma * s);
         rad[i] = r;
@@ -247,6 +253,7 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
             a.atten = p->d_atten;
             a.cs = p->d_cs;
             a.ttab = p->d_ttab;
+            a.ttab_stride = p->psf_tables > 1 ? (size_t)p->n * 2 * kTcTile : 0;
             a.sel = sel_dev;
             a.n = p->n;
             a.nz = p->nz;
@@ -266,6 +273,8 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
             a.taps = p->d_taps;
             a.rad = p->d_rad;
             a.work = p->d_rad + p->n;  // forward work prefix
+            a.taps_stride = p->psf_tables > 1 ? (size_t)p->n * kTapW : 0;
+            a.rad_stride = p->psf_tables > 1 ? 3 * p->n + 2 : 0;
             a.sel = sel_dev;
             a.n = p->n;
             a.nz = p->nz;
@@ -326,6 +335,7 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
                 bb.proj_bstride = (size_t)n_sel * plane;
                 bb.atten = p->d_atten;
                 bb.ttab = p->d_ttab;
+                bb.ttab_stride = p->psf_tables > 1 ? (size_t)p->n * 2 * kTcTile : 0;
                 bb.sel = sel_dev + g0;
                 bb.n = p->n;
                 bb.nz = p->nz;
@@ -344,6 +354,8 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
                 bb.taps = p->d_taps;
                 bb.rad = p->d_rad;
                 bb.work = p->d_rad + 2 * p->n + 1;  // blur_back work prefix
+                bb.taps_stride = p->psf_tables > 1 ? (size_t)p->n * kTapW : 0;
+                bb.rad_stride = p->psf_tables > 1 ? 3 * p->n + 2 : 0;
                 bb.sel = sel_dev + g0;
                 bb.n = p->n;
                 bb.nz = p->nz;
@@ -602,6 +614,7 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     if (!p) return fail(SPECT_ENOMEM, "host allocation failed");
     p->geom = g;
     p->geom.angles_rad = nullptr;
+    p->geom.det_offsets = nullptr;
     p->n = g.nx;
     p->nz = g.nz;
     p->na = g.n_angles;
@@ -624,9 +637,16 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
         p->angles[a] = th;
         cs[a] = make_float2((float)std::cos(th), (float)std::sin(th));
     }
+    // PSF tables: one per angle for a non-circular orbit, else one
     std::vector<float> taps;
     std::vector<int> rad;
-    build_psf(g, p->n, psf, taps, rad, p->rmax);
+    p->psf_tables = g.det_offsets ? p->na : 1;
+    p->rmax = 0;
+    for (int a = 0; a < p->psf_tables; ++a) {
+        const double off = g.det_offsets ? (double)g.det_offsets[a] : (double)g.det_offset;
+        if (!std::isfinite(off)) { free_plan(p); return fail(SPECT_EINVAL, "detector offset %d is not finite", a); }
+        build_psf(g, p->n, psf, off, taps, rad, p->rmax);
+    }
     p->rad = rad;
     if (p->rmax > kMaxR) {
         free_plan(p);
@@ -651,7 +671,7 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     p->bvol_cap = (size_t)std::max(p->max_subset, 16);
     if ((rc = dev_alloc(p, &p->d_cs, p->na)) ||
         (rc = dev_alloc(p, &p->d_taps, taps.size())) ||
-        (rc = dev_alloc(p, &p->d_rad, (size_t)3 * p->n + 2)) ||
+        (rc = dev_alloc(p, &p->d_rad, (size_t)p->psf_tables * (3 * p->n + 2))) ||
         (rc = dev_alloc(p, &p->d_sel_all, (size_t)p->na)) ||
         (rc = dev_alloc(p, &p->d_sens, (size_t)p->M * vol)) ||
         (rc = dev_alloc(p, &p->d_partials, p->partial_planes * plane)) ||
@@ -686,7 +706,8 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     } while (0)
     std::vector<uint16_t> ttab;
     if (p->bf16) {
-        build_toeplitz_bf16(g, p->n, ttab);
+        for (int a = 0; a < p->psf_tables; ++a)
+            build_toeplitz_bf16(g, p->n, g.det_offsets ? (double)g.det_offsets[a] : (double)g.det_offset, ttab);
         if ((rc = dev_alloc(p, &p->d_ttab, ttab.size()))) { free_plan(p); return rc; }
     }
     SPECT_CK(cudaMemcpyAsync(p->d_cs, cs.data(), cs.size() * sizeof(float2), cudaMemcpyHostToDevice, st), "copy angles");
@@ -700,13 +721,17 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     // attenuation loads) plus a cost per tap, in the ratios measured on
     // GB300 with per-CTA timers: about 43 taps' worth per plane for the
     // forward and 27 for the back blur
-    std::vector<int> radw(3 * (size_t)p->n + 2, 0);
-    int* wf = radw.data() + p->n;
-    int* wb = wf + p->n + 1;
-    for (int i = 0; i < p->n; ++i) {
-        radw[i] = rad[i];
-        wf[i + 1] = wf[i] + 43 + (2 * rad[i] + 1);
-        wb[i + 1] = wb[i] + 27 + (2 * rad[i] + 1);
+    const size_t rstride = 3 * (size_t)p->n + 2;  // per table: radii, forward and back work prefixes
+    std::vector<int> radw(p->psf_tables * rstride, 0);
+    for (int a = 0; a < p->psf_tables; ++a) {
+        int* rw = radw.data() + a * rstride;
+        int* wf = rw + p->n;
+        int* wb = wf + p->n + 1;
+        for (int i = 0; i < p->n; ++i) {
+            rw[i] = rad[(size_t)a * p->n + i];
+            wf[i + 1] = wf[i] + 43 + (2 * rw[i] + 1);
+            wb[i + 1] = wb[i] + 27 + (2 * rw[i] + 1);
+        }
     }
     SPECT_CK(cudaMemcpyAsync(p->d_rad, radw.data(), radw.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy radii");
     SPECT_CK(cudaMemcpyAsync(p->d_sel_all, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy angles");

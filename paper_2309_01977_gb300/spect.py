@@ -74,6 +74,7 @@ class _Geom(ctypes.Structure):
         ("psf_nsigma", ctypes.c_float), ("det_offset", ctypes.c_float),
         ("n_subsets", ctypes.c_int),
         ("flags", ctypes.c_uint),
+        ("det_offsets", ctypes.POINTER(ctypes.c_float)),
     ]
 
 
@@ -182,6 +183,7 @@ class Geometry:
     atten_f64: bool = False
     psf_bf16: bool = False
     angles_rad: Optional[Sequence[float]] = None
+    det_offsets: Optional[Sequence[float]] = None  # per-angle detector offsets (non-circular orbit)
 
     def to_c(self):
         g = _Geom()
@@ -189,10 +191,17 @@ class Geometry:
         g.nz = int(self.nz)
         g.voxel_cm = float(self.voxel_cm)
         g.n_angles = int(self.n_angles)
-        keep = None
+        keep = []
         if self.angles_rad is not None:
-            keep = (ctypes.c_double * len(self.angles_rad))(*[float(a) for a in self.angles_rad])
-            g.angles_rad = ctypes.cast(keep, ctypes.POINTER(ctypes.c_double))
+            arr = (ctypes.c_double * len(self.angles_rad))(*[float(a) for a in self.angles_rad])
+            keep.append(arr)
+            g.angles_rad = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
+        if self.det_offsets is not None:
+            if len(self.det_offsets) != self.n_angles:
+                raise SpectError(SPECT_EINVAL, "det_offsets needs one value per angle")
+            arr = (ctypes.c_float * len(self.det_offsets))(*[float(v) for v in self.det_offsets])
+            keep.append(arr)
+            g.det_offsets = ctypes.cast(arr, ctypes.POINTER(ctypes.c_float))
         g.psf_sigma0 = float(self.psf_sigma0)
         g.psf_slope = float(self.psf_slope)
         g.psf_nsigma = float(self.psf_nsigma)

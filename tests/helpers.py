@@ -21,7 +21,8 @@ def oracle_geom(oracle, g, mu64):
                        voxel_cm=float(np.float32(g.voxel_cm)), mu=mu64 if g.attenuation else None,
                        use_psf=g.psf, sigma0=float(np.float32(g.psf_sigma0)),
                        slope=float(np.float32(g.psf_slope)), nsigma=float(np.float32(g.psf_nsigma)),
-                       det_offset=float(np.float32(g.det_offset)))
+                       det_offset=float(np.float32(g.det_offset)),
+                       det_offsets=None if g.det_offsets is None else [float(np.float32(v)) for v in g.det_offsets])
 
 
 def phantom_inputs(n, nz, seed):

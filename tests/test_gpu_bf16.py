@@ -29,9 +29,11 @@ def _t(a, dev):
     (96, 96, 96, 8, 3, 1000),
     (128, 128, 120, 8, 0, 2),
     (64, 40, 12, 3, -1, 7),   # axial size below 128 and not a multiple of 16
+    (64, 64, 16, 4, -1, 8),   # non-circular orbit (per-angle Toeplitz tiles)
 ])
 def test_bf16_projection_parity(spect_lib, oracle_mod, cuda, n, nz, na, M, subset, seed):
-    g = spect_lib.Geometry(n=n, nz=nz, n_angles=na, n_subsets=M, psf_bf16=True, atten_f64=True)
+    offs = [3.0 + 2.0 * math.cos(2 * 2 * math.pi * a / na) for a in range(na)] if seed == 8 else None
+    g = spect_lib.Geometry(n=n, nz=nz, n_angles=na, n_subsets=M, psf_bf16=True, atten_f64=True, det_offsets=offs)
     f, mu = phantom_inputs(n, nz, seed)
     plan = spect_lib.Plan(g, _t(mu, cuda))
     og = oracle_geom(oracle_mod, g, mu)

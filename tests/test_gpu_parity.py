@@ -9,7 +9,7 @@ Tolerances:
   - FP64 count sums: conservation holds to FP32 rounding of H x (1e-6).
 Sizes span several blur strips and plane tiles with ragged tails (n and nz
 not multiples of 16), a 132^2 x 44 geometry whose back projection takes the
-tiled gather with partial tiles, the 64^3 and 128^3 workloads in full, and a
+tiled gather with partial tiles, a non-circular orbit (per-angle PSF tables), the 64^3 and 128^3 workloads in full, and a
 192^3 geometry whose planes are split into z tiles.
 """
 import math
@@ -41,6 +41,9 @@ CASES = {
     # planes of 128^2 and up take the tiled gather; 132 leaves partial 8x8
     # tiles at the edge and nz = 44 short z rows
     "tiled132x44": (dict(n=132, nz=44, n_angles=9, n_subsets=3), 15),
+    # non-circular (elliptical) orbit: every angle has its own PSF table
+    "orbit48x40": (dict(n=48, nz=40, n_angles=12, n_subsets=3,
+                        det_offsets=[2.0 + 1.5 * math.cos(2 * 2 * math.pi * a / 12) for a in range(12)]), 16),
 }
 
 
