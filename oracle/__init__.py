@@ -16,6 +16,7 @@ from .oracle import (  # noqa: F401
     map_recon,
     n_threads,
     osem,
+    osem_multi,
     poisson_ll,
     prior_grad,
     prior_value,

@@ -268,3 +268,29 @@ def map_recon(y, s: float, g: Geom, n_subsets: int, first: int, count: int, algo
                    PRIORS[prior], float(beta), float(delta), float(gamma), float(alpha0), _ptr(f))
     return f
 
+
+
+def osem_multi(ys, ss, geoms, scales, n_subsets: int, first: int, count: int, f0=None):
+    """OSEM for a multi-photopeak extended system matrix (Sec. 2.1.1, Eq.
+    extended_sm): H' = sum_n v_n (x) a_n H_n, one system matrix H_n per peak
+    (its own attenuation map and PSF) scaled by a_n (detector sensitivity and
+    branching ratio), B_n the identity.  With the Poisson gradient of Table 1
+    for the stacked data, each subiteration is
+        r_n = y_n / (a_n H_n,m f + s_n),
+        f <- f * (sum_n a_n H_n,m^T r_n) / (sum_n a_n H_n,m^T 1)   (unchanged where the sum is 0).
+    Built from the FP64 forward and back projections of each peak."""
+    f = np.ones((geoms[0].n, geoms[0].n, geoms[0].nz)) if f0 is None else _f64(f0).copy()
+    for t in range(first, first + count):
+        sel = subset_angles(geoms[0].n_angles, n_subsets, t % n_subsets)
+        bp = np.zeros_like(f)
+        sens = np.zeros_like(f)
+        for y, s, g, a in zip(ys, ss, geoms, scales):
+            p = a * forward(f, g, sel)
+            den = p + s
+            yv = _f64(y).reshape(g.n_angles, g.n, g.nz)[sel]
+            r = np.where(den > 0, yv / np.where(den > 0, den, 1.0), 0.0)
+            bp += a * back(r, g, sel)
+            sens += a * back(np.ones_like(r), g, sel)
+        pos = sens > 0
+        f = np.where(pos, f * bp / np.where(pos, sens, 1.0), f)
+    return f

@@ -331,3 +331,46 @@ def test_brute_force_dense_h_noncircular_orbit(oracle_mod):
     g1 = oracle_mod.Geom(n=n, nz=nz, n_angles=8, angles=angles, mu=mu, det_offset=1.5, **kw)
     g2 = oracle_mod.Geom(n=n, nz=nz, n_angles=8, angles=angles, mu=mu, det_offsets=[1.5] * 8, **kw)
     np.testing.assert_array_equal(oracle_mod.forward(x, g1), oracle_mod.forward(x, g2))
+
+
+# ---------------------------------------------------------------- multi-photopeak extended system matrix
+
+def _two_peaks(oracle_mod, seed=71):
+    n = nz = 12
+    f_raw, mu = phantom.make_phantom(n, nz, seed)
+    g1 = oracle_mod.Geom(n=n, nz=nz, n_angles=8, mu=mu, use_psf=True, sigma0=0.5, slope=0.05)
+    g2 = oracle_mod.Geom(n=n, nz=nz, n_angles=8, mu=0.8 * mu, use_psf=True, sigma0=0.7, slope=0.08)
+    rng = _rng(seed)
+    y1 = rng.poisson(oracle_mod.forward(f_raw, g1) * 50.0 + 1.0).astype(float)
+    y2 = rng.poisson(0.6 * oracle_mod.forward(f_raw, g2) * 50.0 + 1.0).astype(float)
+    return g1, g2, y1, y2
+
+
+def test_multi_peak_with_one_peak_is_osem(oracle_mod):
+    g1, g2, y1, y2 = _two_peaks(oracle_mod)
+    f_ref, _ = oracle_mod.osem(y1, 1.0, g1, 4, 0, 6)
+    f = oracle_mod.osem_multi([y1], [1.0], [g1], [1.0], 4, 0, 6)
+    np.testing.assert_allclose(f, f_ref, rtol=1e-12, atol=0)
+
+
+def test_multi_peak_two_copies_of_one_peak_is_osem(oracle_mod):
+    """Two identical peaks observing the same counts: numerator and
+    denominator both double, so the update is OSEM's."""
+    g1, g2, y1, y2 = _two_peaks(oracle_mod)
+    f_ref, _ = oracle_mod.osem(y1, 1.0, g1, 4, 0, 6)
+    f = oracle_mod.osem_multi([y1, y1], [1.0, 1.0], [g1, g1], [1.0, 1.0], 4, 0, 6)
+    np.testing.assert_allclose(f, f_ref, rtol=1e-12, atol=0)
+
+
+def test_multi_peak_count_conservation(oracle_mod):
+    """s = 0: the subset's predicted counts over all peaks equal its measured counts after the update."""
+    g1, g2, y1, y2 = _two_peaks(oracle_mod)
+    scales = [1.0, 0.6]
+    f = np.ones((12, 12, 12))
+    for t in range(4):
+        f_new = oracle_mod.osem_multi([y1, y2], [0.0, 0.0], [g1, g2], scales, 4, t, 1, f)
+        sel = oracle_mod.subset_angles(8, 4, t % 4)
+        pred = sum(a * oracle_mod.forward(f_new, g, sel).sum() for a, g in zip(scales, [g1, g2]))
+        meas = y1[sel].sum() + y2[sel].sum()
+        assert pred == pytest.approx(meas, rel=1e-11)
+        f = f_new
