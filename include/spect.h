@@ -203,6 +203,19 @@ typedef struct spect_map_params {
 int spect_map_run(spect_plan* plan, const float* y, float s, float* x_inout, int first_subiter, int n_subiters,
                   const spect_map_params* params, void* stream);
 
+/* OSEM for several photopeaks (Sec. 2.1.1, Eq. extended_sm: H' = sum_n v_n (x)
+ * a_n H_n, B_n = identity, A_n = the scalar a_n per peak): plans[n] is the
+ * system matrix of peak n (its own attenuation map and PSF model; all peaks
+ * share the volume, angles, subsets and device), scales[n] = a_n > 0 (detector
+ * sensitivity times branching ratio), y[n] its projections (device,
+ * [n_angles][ny][nz]) and s[n] >= 0 its additive term.  Subiteration t:
+ *   x <- x (sum_n a_n H_n,m^T (y_n / (a_n H_n,m x + s_n))) / (sum_n a_n H_n,m^T 1)
+ * (unchanged where the denominator is 0).  1 <= n_peaks <= 8; plans[0] may not
+ * appear again in the list (its buffers hold partial sums); its first call
+ * allocates one volume.  Asynchronous on `stream`. */
+int spect_multi_osem_run(spect_plan* const* plans, const float* scales, int n_peaks, const float* const* y,
+                         const float* s, float* x_inout, int first_subiter, int n_subiters, void* stream);
+
 /* grad_out = dV/dx for prior `prior` (SPECT_PRIOR_QUADRATIC or _RDP) on a
  * device volume x[n][n][nz]; no plan, nothing allocated.  Asynchronous. */
 int spect_prior_grad(const float* x, int n, int nz, int prior, float delta, float gamma, float* grad_out,

@@ -73,6 +73,7 @@ struct ReduceArgs {
     const float* y;        // [n_angles][plane] or nullptr
     const int* sel;        // angle ids (ratio mode)
     float s;
+    float scale;           // forward-model scale a (multi-photopeak): r = a y / (a p + s); 1 otherwise
     const float* s_ptr;    // when not NULL, s is read from this device word
     double* diag_blocks;   // [gridDim.x][3] or nullptr: sums of (p+s), y, y*p/(p+s)
 };
@@ -103,6 +104,7 @@ struct UpdateSpec {
     const float* sens_all; // BSREM: H^T 1 over all angles
     float beta_n;          // prior weight of the subiteration, beta / M
     float step;            // BSREM: alpha_t * M
+    const float* bp_add;   // added to the back projection before the update (other photopeaks), or nullptr
 };
 
 struct GatherArgs {
@@ -200,6 +202,8 @@ cudaError_t launch_poisson_ll(const float* y, const float* p, float s, size_t co
                               int n_blocks, double* ll, float* grad, cudaStream_t st);
 cudaError_t launch_fill(float* dst, size_t count, float value, cudaStream_t st);
 cudaError_t launch_update(float* x, const float* bp, const UpdateSpec& u, size_t count, cudaStream_t st);
+constexpr int kMaxPeaks = 8;
+cudaError_t launch_wsum(float* out, const float* const* in, const float* w, int terms, size_t count, cudaStream_t st);
 cudaError_t launch_prior_grad(const float* x, float* grad, int n, int nz, int prior, float delta, float gamma,
                               cudaStream_t st);
 
@@ -235,6 +239,7 @@ struct spect_plan {
                                               // tiled [na][gt_tiles][gt_T^2][kMaxCand]
     int* d_gdesc = nullptr;                   // tiled gather footprints [na][gt_tiles][kFpDescInts]
     float* d_grad = nullptr;                  // MAP: prior gradient (allocated by the first MAP call)
+    float* d_msens = nullptr;                 // multi-photopeak: weighted subset sensitivity (first call)
     float* d_sens_all = nullptr;              // BSREM: H^T 1 over all angles (first BSREM call)
     bool sens_all_ok = false;                 // d_sens_all matches the current attenuation map
     int* d_gwork = nullptr;                   // tiled gather: largest footprint (rows)

@@ -156,8 +156,8 @@ __global__ void __launch_bounds__(256) forward_reduce_kernel(ReduceArgs a)
             float rv[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float den = pv[q] + s;
-                rv[q] = den > 0.f ? yy[q] / den : 0.f;
+                const float den = a.scale * pv[q] + s;
+                rv[q] = den > 0.f ? a.scale * yy[q] / den : 0.f;
                 if (kDiag) {
                     d0 += (double)den;
                     d1 += (double)yy[q];
@@ -253,7 +253,8 @@ __global__ void update_kernel(float* __restrict__ x, const float* __restrict__ b
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
         const float gv = u.grad ? u.grad[i] : 0.f;
         const float sa = u.sens_all ? u.sens_all[i] : 0.f;
-        x[i] = update1(u, x[i], bp[i], u.sens[i], gv, sa);
+        const float b = u.bp_add ? bp[i] + u.bp_add[i] : bp[i];
+        x[i] = update1(u, x[i], b, u.sens[i], gv, sa);
     }
 }
 
@@ -263,6 +264,36 @@ cudaError_t launch_update(float* x, const float* bp, const UpdateSpec& u, size_t
     if (blocks > 8192) blocks = 8192;
     if (blocks == 0) return cudaSuccess;
     update_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, bp, u, count);
+    return cudaGetLastError();
+}
+
+// out = sum_t w[t] in[t] (the weighted subset sensitivity of several photopeaks).
+struct WsumArgs {
+    const float* in[kMaxPeaks];
+    float w[kMaxPeaks];
+};
+
+__global__ void wsum_kernel(float* __restrict__ out, WsumArgs a, int terms, size_t count)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        float v = a.w[0] * a.in[0][i];
+        for (int t = 1; t < terms; ++t) v = fmaf(a.w[t], a.in[t][i], v);
+        out[i] = v;
+    }
+}
+
+cudaError_t launch_wsum(float* out, const float* const* in, const float* w, int terms, size_t count, cudaStream_t st)
+{
+    if (terms < 1 || terms > kMaxPeaks) return cudaErrorInvalidValue;
+    WsumArgs a{};
+    for (int t = 0; t < terms; ++t) {
+        a.in[t] = in[t];
+        a.w[t] = w[t];
+    }
+    size_t blocks = (count + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    if (blocks == 0) return cudaSuccess;
+    wsum_kernel<<<(unsigned)blocks, 256, 0, st>>>(out, a, terms, count);
     return cudaGetLastError();
 }
 

@@ -232,7 +232,8 @@ int chunk_target(const spect_plan* p, long items)
 // projects to bitwise the same values alone or in a batch.  diag_blocks
 // (ratio mode only) receives per-block FP64 sums; *n_diag their count.
 int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, int n_sel, int batch, const float* y,
-                float s, double* diag_blocks, int* n_diag, cudaStream_t st, const float* s_ptr = nullptr)
+                float s, double* diag_blocks, int* n_diag, cudaStream_t st, const float* s_ptr = nullptr,
+                float scale = 1.f)
 {
     const PlaneTiling& t = p->tiling;
     // never more chunks than the partial buffer holds for one batch entry
@@ -299,6 +300,7 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
         r.y = y;
         r.sel = sel_dev;
         r.s = s;
+        r.scale = scale;
         r.s_ptr = s_ptr;
         r.diag_blocks = (y && diag_blocks) ? diag_blocks : nullptr;
         const size_t total4 = (size_t)r.items * plane / 4;
@@ -313,7 +315,7 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
 // x_out (per batch entry) = sum over sel of H_a^T proj_a, optionally fused with
 // the OSEM update x_out <- x_out * bp / sens (then batch must be 1).
 int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev, int n_sel, int batch,
-             const UpdateSpec* upd, cudaStream_t st)
+             const UpdateSpec* upd, cudaStream_t st, bool accumulate = false)
 {
     const size_t vol = vol_elems(p), plane = plane_elems(p);
     const int gmax = (int)std::min<size_t>(16, p->bvol_cap);
@@ -385,7 +387,7 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
                 gt.rows_cap = p->gt_rows;
                 gt.stages = p->gt_stages;
                 gt.out = out_b;
-                gt.accumulate = g0 > 0;
+                gt.accumulate = g0 > 0 || accumulate;
                 if (fused) gt.upd = *upd;
                 gt.err = p->d_err;
                 e = timed(p, fused ? "gather_update" : "gather", st, 1, [&] { return launch_gather_tiled(gt, st); });
@@ -406,7 +408,7 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
                 ga.lanes_per_col = l;
             }
             ga.out = out_b;
-            ga.accumulate = g0 > 0;
+            ga.accumulate = g0 > 0 || accumulate;
             if (fused) ga.upd = *upd;
             e = timed(p, fused ? "gather_update" : "gather", st, 1, [&] { return launch_gather(ga, st); });
             if (e != cudaSuccess) return cuda_fail(e, "gather kernel launch");
@@ -523,6 +525,62 @@ int map_core(spect_plan* plan, const float* y, float s, float* x_inout, int firs
             u.step = mp->alpha0 / (1.f + (float)(t / plan->M)) / c;
         }
         rc = run_back(plan, plan->d_ratio, x_inout, plan->d_sel[m], ns, 1, &u, st);
+        if (rc) return rc;
+    }
+    return SPECT_OK;
+}
+
+// OSEM for a multi-photopeak extended system matrix (Eq. extended_sm):
+// per subiteration each peak's ratio r'_n = a_n y_n / (a_n H_n,m x + s_n),
+// the weighted sensitivity sum_n a_n H_n,m^T 1, the back projections of the
+// first peaks accumulated into a scratch volume, and the last peak's back
+// projection fused with the update x <- x (sum_n H_n,m^T r'_n) / (sum_n a_n H_n,m^T 1).
+// plans[0]'s back-projection buffer holds the partial sum (so plans[0] must
+// differ from the last plan).
+int multi_core(spect_plan* const* plans, const float* scales, int P, const float* const* y, const float* s,
+               float* x, int first, int count, void* stream)
+{
+    if (!plans || !scales || !y || !s) return fail(SPECT_EINVAL, "plans, scales, y and s must not be NULL");
+    if (P < 1 || P > kMaxPeaks) return fail(SPECT_EINVAL, "n_peaks must be in [1, %d]", kMaxPeaks);
+    if (!x || !aligned16(x)) return fail(SPECT_EINVAL, "x_inout must be a 16-byte aligned device pointer");
+    if (first < 0 || count < 0) return fail(SPECT_EINVAL, "negative subiteration range");
+    spect_plan* p0 = plans[0];
+    for (int n = 0; n < P; ++n) {
+        spect_plan* q = plans[n];
+        if (!q) return fail(SPECT_EINVAL, "plan %d is NULL", n);
+        if (q->n != p0->n || q->nz != p0->nz || q->na != p0->na || q->M != p0->M || q->device != p0->device)
+            return fail(SPECT_EINVAL, "plan %d: peaks must share volume, angles, subsets and device", n);
+        if (n > 0 && q == p0) return fail(SPECT_EINVAL, "plan %d repeats plans[0]", n);
+        if (!y[n] || !aligned16(y[n])) return fail(SPECT_EINVAL, "y[%d] must be a 16-byte aligned device pointer", n);
+        if (!(scales[n] > 0.f) || !(s[n] >= 0.f)) return fail(SPECT_EINVAL, "peak %d: scale must be > 0, s >= 0", n);
+    }
+    DeviceGuard guard(p0->device);
+    if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plans' device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t vol = vol_elems(p0);
+    int rc;
+    if (!p0->d_msens && ((rc = dev_alloc(p0, &p0->d_msens, vol)))) return rc;
+    for (int t = first; t < first + count; ++t) {
+        const int m = t % p0->M;
+        const int ns = (int)p0->subsets[m].size();
+        const float* sens[kMaxPeaks];
+        for (int n = 0; n < P; ++n) {
+            rc = run_forward(plans[n], x, plans[n]->d_ratio, plans[n]->d_sel[m], ns, 1, y[n], s[n], nullptr, nullptr,
+                             st, nullptr, scales[n]);
+            if (rc) return rc;
+            sens[n] = plans[n]->d_sens + (size_t)m * vol;
+        }
+        cudaError_t e = timed(p0, "sens_sum", st, 1, [&] { return launch_wsum(p0->d_msens, sens, scales, P, vol, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "weighted sum kernel");
+        for (int n = 0; n + 1 < P; ++n) {
+            rc = run_back(plans[n], plans[n]->d_ratio, p0->d_bp, plans[n]->d_sel[m], ns, 1, nullptr, st, n > 0);
+            if (rc) return rc;
+        }
+        UpdateSpec u{};
+        u.mode = kUpdOsem;
+        u.sens = p0->d_msens;
+        u.bp_add = P > 1 ? p0->d_bp : nullptr;
+        rc = run_back(plans[P - 1], plans[P - 1]->d_ratio, x, plans[P - 1]->d_sel[m], ns, 1, &u, st);
         if (rc) return rc;
     }
     return SPECT_OK;
@@ -915,6 +973,12 @@ int spect_map_run(spect_plan* plan, const float* y, float s, float* x_inout, int
                   const spect_map_params* params, void* stream)
 {
     return map_core(plan, y, s, x_inout, first_subiter, n_subiters, params, stream);
+}
+
+int spect_multi_osem_run(spect_plan* const* plans, const float* scales, int n_peaks, const float* const* y,
+                         const float* s, float* x_inout, int first_subiter, int n_subiters, void* stream)
+{
+    return multi_core(plans, scales, n_peaks, y, s, x_inout, first_subiter, n_subiters, stream);
 }
 
 int spect_prior_grad(const float* x, int n, int nz, int prior, float delta, float gamma, float* grad_out,

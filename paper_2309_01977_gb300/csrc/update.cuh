@@ -33,6 +33,10 @@ __device__ __forceinline__ float update1(const UpdateSpec& u, float f, float bp,
 // Float4 i4 of a volume: x holds the current image, bp the back projection.
 __device__ __forceinline__ float4 update4(const UpdateSpec& u, float4 x, float4 bp, size_t i4)
 {
+    if (u.bp_add) {
+        const float4 b2 = __ldg(reinterpret_cast<const float4*>(u.bp_add) + i4);
+        bp = make_float4(bp.x + b2.x, bp.y + b2.y, bp.z + b2.z, bp.w + b2.w);
+    }
     const float4 sv = __ldg(reinterpret_cast<const float4*>(u.sens) + i4);
     float4 gv = make_float4(0.f, 0.f, 0.f, 0.f), sa = gv;
     if (u.grad) gv = __ldg(reinterpret_cast<const float4*>(u.grad) + i4);

@@ -47,7 +47,7 @@ EXPORTED = [
     "spect_status_str", "spect_last_error", "spect_version",
     "spect_profile_enable", "spect_profile_read", "spect_kernel_launches",
     "spect_poisson_ll_noalloc", "spect_plan_check", "spect_plan_set_mu", "spect_osem_run_dev",
-    "spect_map_run", "spect_prior_grad",
+    "spect_map_run", "spect_prior_grad", "spect_multi_osem_run",
     "spect_serve_create", "spect_serve_submit", "spect_serve_poll", "spect_serve_wait",
     "spect_serve_cancel", "spect_serve_stats_get", "spect_serve_destroy",
 ]
@@ -118,6 +118,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.spect_osem_run.argtypes = [vp, vp, f, vp, i, i, vp, vp]
         lib.spect_map_run.argtypes = [vp, vp, f, vp, i, i, ctypes.POINTER(_MapParams), vp]
         lib.spect_prior_grad.argtypes = [vp, i, i, i, f, f, vp, vp]
+        lib.spect_multi_osem_run.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(f), i, ctypes.POINTER(vp),
+                                             ctypes.POINTER(f), vp, i, i, vp]
         lib.spect_osem_run_dev.argtypes = [vp, vp, vp, vp, i, i, vp, vp]
         lib.spect_plan_set_mu.argtypes = [vp, vp, vp]
         lib.spect_poisson_ll.argtypes = [vp, vp, vp, f, ctypes.c_size_t, vp, vp, vp]
@@ -279,6 +281,18 @@ def spect_map_run(plan: int, y: torch.Tensor, s: float, x: torch.Tensor, first_s
     mp = _MapParams(ALGORITHMS[algorithm], PRIORS[prior], beta, delta, gamma, alpha0)
     _check(load().spect_map_run(plan, _dptr(y), float(s), _dptr(x), first_subiter, n_subiters, ctypes.byref(mp),
                                 _stream(stream)))
+
+
+def spect_multi_osem_run(plans, scales, ys, ss, x: torch.Tensor, first_subiter: int, n_subiters: int, stream=None):
+    """OSEM over several photopeaks (include/spect.h): plans, scales, ys, ss per peak."""
+    P = len(plans)
+    if not (len(scales) == len(ys) == len(ss) == P):
+        raise SpectError(SPECT_EINVAL, "plans, scales, ys and ss must have one entry per peak")
+    ph = (ctypes.c_void_p * P)(*[p.handle if isinstance(p, Plan) else p for p in plans])
+    sc = (ctypes.c_float * P)(*[float(v) for v in scales])
+    yp = (ctypes.c_void_p * P)(*[_dptr(y) for y in ys])
+    sp = (ctypes.c_float * P)(*[float(v) for v in ss])
+    _check(load().spect_multi_osem_run(ph, sc, P, yp, sp, _dptr(x), first_subiter, n_subiters, _stream(stream)))
 
 
 def spect_prior_grad(x: torch.Tensor, prior: str, grad: torch.Tensor, delta: float = 1.0, gamma: float = 2.0,
