@@ -20,7 +20,7 @@ LIB = os.path.join(PKG, "libspect.so")
 SOURCES = ["spect_api.cu", "plane_host.cu", "gather_kernel.cu", "gather_tiled.cu", "misc_kernels.cu",
            "forward_ipt1.cu", "forward_ipt2.cu", "forward_ipt3.cu", "forward_ipt4.cu",
            "blur_back_ipt1.cu", "blur_back_ipt2.cu", "blur_back_ipt3.cu", "blur_back_ipt4.cu",
-           "noalloc.cu", "psf_bf16.cu", "serve.cu"]
+           "noalloc.cu", "psf_bf16.cu", "serve.cu", "pet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

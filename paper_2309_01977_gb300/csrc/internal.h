@@ -211,6 +211,8 @@ cudaError_t launch_prior_grad(const float* x, float* grad, int n, int nz, int pr
 
 // Sets the thread-local message returned by spect_last_error().
 void spect_internal_set_error(const char* msg);
+// Adds kernels launched outside spect_api.cu to spect_kernel_launches().
+void spect_internal_count_launches(unsigned long long kernels);
 
 struct spect_plan {
     spect_geom geom{};

@@ -24,8 +24,12 @@ thread_local std::string g_last_error;
 void spect_internal_set_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
 namespace {
-
 std::atomic<unsigned long long> g_launches{0};
+}  // namespace
+
+void spect_internal_count_launches(unsigned long long kernels) { g_launches += kernels; }
+
+namespace {
 
 cudaEvent_t take_event(spect_plan* p)
 {

@@ -1,6 +1,6 @@
 """CPU checks of the C ABI: the library builds, loads and exports every
-function include/spect.h declares; host-side validation rejects bad
-geometry before touching the GPU.  No kernel runs here."""
+function include/spect.h and include/pet.h declare; host-side validation
+rejects bad geometry before touching the GPU.  No kernel runs here."""
 import ctypes
 import os
 import re
@@ -17,7 +17,7 @@ def declared_functions():
             continue
         text = open(os.path.join(ROOT, "include", fname)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^[A-Za-z_][A-Za-z0-9_ ]*[\s*]+(spect_[a-z0-9_]+)\s*\(", text, re.M):
+        for m in re.finditer(r"^[A-Za-z_][A-Za-z0-9_ ]*[\s*]+((?:spect|pet)_[a-z0-9_]+)\s*\(", text, re.M):
             names.add(m.group(1))
     return sorted(names)
 
@@ -33,6 +33,8 @@ def test_library_exports_every_declared_symbol(spect_lib):
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
     assert not missing, missing
     assert set(spect_lib.EXPORTED) <= set(declared_functions())
+    from paper_2309_01977_gb300 import pet
+    assert set(pet.PET_EXPORTED) == {n for n in declared_functions() if n.startswith("pet_")}
 
 
 def test_status_strings(spect_lib):
@@ -93,3 +95,29 @@ def test_serve_config_validation(spect_lib):
     st = ctypes.c_int()
     assert lib.spect_serve_poll(None, 1, ctypes.byref(st)) == spect_lib.SPECT_EINVAL
     assert lib.spect_serve_destroy(None) == 0
+
+
+@pytest.mark.parametrize("bad, msg", [
+    (dict(shape=(0, 4, 4)), "image size"),
+    (dict(voxel=(1.0, 0.0, 1.0)), "voxel"),
+    (dict(n_subsets=0), "n_subsets"),
+    (dict(rr_sigma_mm=2.0, rr_nsigma=0.0), "rr_nsigma"),
+    (dict(rr_sigma_mm=40.0), "radius"),
+])
+def test_pet_geometry_validation(spect_lib, bad, msg):
+    from paper_2309_01977_gb300 import pet
+    kw = dict(shape=(8, 8, 8), voxel=(2.0, 2.0, 2.0))
+    kw.update(bad)
+    g = pet.PetGeometry(**kw).to_c()
+    out = ctypes.c_void_p()
+    lib = pet.load()
+    assert lib.pet_plan_create(ctypes.byref(g), None, None, ctypes.byref(out)) == spect_lib.SPECT_EINVAL
+    assert msg.encode() in lib.spect_last_error()
+    assert out.value is None
+
+
+def test_pet_null_plan_rejected(spect_lib):
+    from paper_2309_01977_gb300 import pet
+    lib = pet.load()
+    assert lib.pet_forward(None, None, None, None, 0, None, None) == spect_lib.SPECT_EINVAL
+    assert lib.pet_lm_osem_run(None, None, None, None, 0, None, None, 0, 1, None, None) == spect_lib.SPECT_EINVAL
