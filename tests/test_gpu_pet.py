@@ -115,7 +115,9 @@ def test_mult_matches_oracle(pet_mods, small, cuda):
     plan = _plan(pet, wl, mu, cuda)
     got = plan.mult(_t(L, cuda), _t(e, cuda)).cpu().numpy()
     ref = opet.mult(L, og, mu=mu, eta=e)
-    assert np.max(np.abs(got - ref) / ref) <= 2e-6
+    # exp(-L) carries the absolute FP32 error of the line integral L of mu
+    # (a few hundred samples, L up to ~2): the FP32 bound of 1e-5
+    assert np.max(np.abs(got - ref) / ref) <= 1e-5
     plan.close()
     plan = _plan(pet, wl, None, cuda)
     assert np.array_equal(plan.mult(_t(L, cuda)).cpu().numpy(), np.ones(len(L), dtype=np.float32))
@@ -217,7 +219,7 @@ def test_full_grid_sampled_lines_and_count_identity(pet_mods, cuda):
     og = opet.PetGeom(wl.shape, wl.voxel, rr_sigma_mm=np.float32(wl.rr_sigma_mm), rr_nsigma=3.0)
     L = lors.cpu().numpy()[pick]
     m_ref = opet.mult(L, og, mu=mu.cpu().numpy(), eta=eta.cpu().numpy()[pick])
-    assert np.max(np.abs(mult.cpu().numpy()[pick] - m_ref) / m_ref) <= 2e-6
+    assert np.max(np.abs(mult.cpu().numpy()[pick] - m_ref) / m_ref) <= 1e-5
     ref = opet.forward(act.cpu().numpy(), L, og, mult.cpu().numpy()[pick])
     got = p.cpu().numpy()[pick]
     err = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-3 * np.max(np.abs(ref)))
