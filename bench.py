@@ -62,6 +62,10 @@ def parse_args():
     ap.add_argument("--no-map", action="store_true", help="skip the BSREM-RDP leg")
     ap.add_argument("--no-multipeak", action="store_true", help="skip the two-photopeak OSEM leg")
     ap.add_argument("--no-orbit", action="store_true", help="skip the non-circular orbit OSEM leg")
+    ap.add_argument("--no-pet", action="store_true", help="skip the listmode PET leg")
+    ap.add_argument("--pet-only", action="store_true",
+                    help="run only the listmode PET leg (one GPU) and print it as one JSON line")
+    ap.add_argument("--pet-prompts", type=int, default=None, help="prompts of the PET leg (default 30 M)")
     return ap.parse_args()
 
 
@@ -437,6 +441,108 @@ def run_orbit_leg(spect, torch, dev, wl, g, f_raw, mu, x, timed, max_over_ranks,
             "subset_iters_per_s": replica_throughput(world, k, n_sub, ms), "ms_per_recon": ms / k}
 
 
+def run_pet_leg(torch, dev, timed, max_over_ranks, world, k, cpu_seconds: float, with_cpu: bool, prompts=None):
+    """Listmode PET (Eq. PET_SM, Joseph projector, listmode OSEM) on the
+    paper's PET grid: 204 x 204 x 154 voxels of 1.25 mm, a 338 mm scanner of
+    64 rings x 448 crystals, 3 mm FWHM resolution model, 30 M prompts (10 %
+    randoms) in 3 subsets.  The sensitivity image comes from the pairs of
+    every 4th crystal of every 2nd ring, each weighted 64 (plan-time input,
+    not timed).  Timed: one listmode OSEM iteration (3 subiterations over all
+    30 M events) per step."""
+    from paper_2309_01977_gb300 import pet, pet_phantom as pp
+    import dataclasses
+    wl = pp.PET_WORKLOADS["petlm204"]
+    if prompts:
+        wl = dataclasses.replace(wl, prompts=int(prompts))
+    act, mu, semi = pp.head_phantom(wl.shape, wl.voxel, wl.seed, device=dev)
+    lors, eta, s, n_true = pp.draw_events(wl, act, semi, device=dev)
+    torch.cuda.empty_cache()
+    g = pet.PetGeometry(wl.shape, wl.voxel, rr_sigma_mm=wl.rr_sigma_mm, n_subsets=wl.n_subsets)
+    plan = pet.PetPlan(g, mu)
+    mult = plan.mult(lors, eta)
+    L_all, eta_all, w = pp.scanner_lors(wl.scanner, angle_step=4, ring_step=2, device=dev, eff_seed=wl.seed)
+    sens = plan.back(plan.mult(L_all, eta_all) * w, L_all)
+    del L_all, eta_all
+    torch.cuda.empty_cache()
+    x = torch.ones(wl.shape, device=dev)
+    M = wl.n_subsets
+    n_ev = lors.shape[0]
+
+    def step():
+        x.fill_(1.0)
+        plan.lm_osem(lors, mult, s, sens, x, 0, M)
+    step()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(timed(step, k))
+    plan.profile_enable(True)
+    plan.profile_read(reset=True)
+    timed(step, k)
+    prof = plan.profile_read(reset=True)
+    plan.profile_enable(False)
+    em = prof.get("joseph_em", (1, float("nan")))
+    samples = float(sum(pet_sample_count(lors, wl)))  # bilinear samples per pass over all events
+    leg = {"workload": "petlm204: 204x204x154 (1.25 mm), 64x448-crystal scanner (r 338 mm), %d prompts "
+                       "(%d trues, 10%% randoms), 3 subsets, 3 mm FWHM T_rr, attenuation + normalisation" % (
+                           n_ev, n_true),
+           "step": "one listmode OSEM iteration (3 subiterations over all events) from f0 = 1",
+           "events_per_s": replica_throughput(world, k, n_ev, ms), "ms_per_iteration": ms / k,
+           "kernel_avg_ms": {kk: round(v[1] / v[0], 3) for kk, v in prof.items()},
+           # each joseph_em launch walks one subset: 1/M of the events
+           "joseph_em_samples_per_s": samples * (em[0] / M) / (em[1] * 1e-3) if em[0] else None}
+    l2 = os.path.join(ROOT, "profiles", "l2_petlm204.json")
+    if os.path.exists(l2):
+        with open(l2) as fh:
+            prof_l2 = json.load(fh).get("joseph_em")
+        # the walk gathers from and scatters into an image held in L2: its
+        # bound is L2 throughput, measured by ncu as a fraction of L2 peak
+        leg["roofline"] = {"bound": "l2", "kernel": "joseph_em", "frac": prof_l2["lts_throughput_frac"],
+                           "source": "ncu lts__throughput of the same kernel (profiles/pet_lm_em_petlm204.md)"}
+    if with_cpu:
+        leg["cpu_baseline"] = pet_cpu_baseline(wl, act, mu, lors, mult, s, sens, cpu_seconds)
+    plan.close()
+    return leg
+
+
+def pet_sample_count(lors, wl):
+    """Joseph samples of each line (planes of its principal axis inside the
+    image), counted on the host from the line ends: the work of one pass."""
+    L = lors.double().cpu().numpy()
+    v = np.asarray(wl.voxel)
+    n = np.asarray(wl.shape)
+    d = np.abs(L[:, 3:] - L[:, :3]) / v
+    a = np.argmax(d, axis=1)
+    org = -0.5 * (n - 1) * v
+    s1 = (L[np.arange(len(L)), a] - org[a]) / v[a]
+    s2 = (L[np.arange(len(L)), 3 + a] - org[a]) / v[a]
+    lo = np.clip(np.ceil(np.minimum(s1, s2)), 0, None)
+    hi = np.minimum(np.floor(np.maximum(s1, s2)), n[a] - 1)
+    return [float(np.clip(hi - lo + 1, 0, None).sum())]
+
+
+def pet_cpu_baseline(wl, act, mu, lors, mult, s, sens, seconds):
+    """The FP64 oracle's listmode OSEM on the host cores for a bounded sample:
+    one subiteration over the first events of subset 0, as many as fit in
+    about `seconds` (measured on a small probe first), scaled to events/s."""
+    from oracle import pet as opet
+    og = opet.PetGeom(wl.shape, wl.voxel, rr_sigma_mm=float(np.float32(wl.rr_sigma_mm)), rr_nsigma=3.0)
+    M = wl.n_subsets
+    L = lors[:M * 20000].cpu().numpy()
+    m = mult[:M * 20000].cpu().numpy()
+    sv = s[:M * 20000].cpu().numpy()
+    sn = sens.cpu().numpy()
+    t0 = time.perf_counter()
+    opet.lm_osem(L, m, sv, sn, og, M, count=1)
+    el = time.perf_counter() - t0
+    n = int(min(lors.shape[0], M * 20000 * max(1.0, seconds / max(el, 1e-3))))
+    L = lors[:n].cpu().numpy()
+    t0 = time.perf_counter()
+    opet.lm_osem(L, mult[:n].cpu().numpy(), s[:n].cpu().numpy(), sn, og, M, count=1)
+    el = time.perf_counter() - t0
+    import oracle
+    return {"value": (n // M) / el, "unit": "events/s", "cores": oracle.n_threads(), "kind": "oracle",
+            "sample": "one listmode subiteration over %d events of petlm204 (FP64, %.1f s)" % (n // M, el)}
+
+
 def run_libspect(args):
     import torch
     import torch.distributed as dist
@@ -576,6 +682,9 @@ def run_libspect(args):
     if not args.no_multipeak:
         legs["multipeak"] = run_multipeak_leg(spect, torch, dev, wl, g, plan, f_raw, mu, y_dev, s, x, timed,
                                               max_over_ranks, world, max(2, args.steps // 2))
+    if not args.no_pet:
+        legs["pet"] = run_pet_leg(torch, dev, timed, max_over_ranks, world, max(2, args.steps // 8),
+                                  args.cpu_seconds / 2, rank == 0 and world == 1 and not args.no_cpu_baseline)
     if not args.no_orbit:
         legs["orbit"] = run_orbit_leg(spect, torch, dev, wl, g, f_raw, mu, x, timed, max_over_ranks, world,
                                       max(2, args.steps // 2))
@@ -608,10 +717,39 @@ def run_libspect(args):
     return 0
 
 
+def run_pet_only(args):
+    """The listmode PET leg alone, on one GPU, timed like the main legs."""
+    import torch
+
+    from paper_2309_01977_gb300 import spect
+    spect.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, k):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        torch.cuda.synchronize()
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return sum(e0.elapsed_time(e1) for e0, e1 in evs)
+
+    leg = run_pet_leg(torch, dev, timed, lambda v: v, 1, max(2, args.steps // 8), args.cpu_seconds / 2,
+                      not args.no_cpu_baseline, prompts=args.pet_prompts)
+    print(json.dumps({"pet": leg}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.pet_only:
+        return run_pet_only(args)
     return run_libspect(args)
 
 

@@ -40,6 +40,7 @@ struct PetGrid {
     int n[3];
     float v[3];
     long long stride[3];  // elements between neighbours along x, y, z
+    long long total;      // voxels
 };
 
 enum PetMode { kModeFwd = 0, kModeMult = 1, kModeBack = 2, kModeEm = 3 };
@@ -51,6 +52,14 @@ struct Walk {
     int a, b, c, q0, count;
     float u0, du, w0, dw, step;
 };
+
+// Element i of a three-element array with constant indices only, so that
+// the array stays in registers.
+template <class T>
+__device__ __forceinline__ T sel3(const T (&v)[3], int i)
+{
+    return i == 0 ? v[0] : i == 1 ? v[1] : v[2];
+}
 
 __device__ __forceinline__ bool walk_setup(const float* __restrict__ lor, const PetGrid& g, Walk& k)
 {
@@ -64,17 +73,18 @@ __device__ __forceinline__ bool walk_setup(const float* __restrict__ lor, const 
 #pragma unroll
     for (int c = 0; c < 3; ++c) sc[c] = __fdiv_rn(fabsf(__fsub_rn(p2[c], p1[c])), g.v[c]);
     int a = 0;
-    if (sc[1] > sc[a]) a = 1;
-    if (sc[2] > sc[a]) a = 2;
-    if (!(sc[a] > 0.f)) return false;
-    const float va = g.v[a];
-    const float half = __fmul_rn(0.5f, (float)(g.n[a] - 1));
+    if (sc[1] > sc[0]) a = 1;
+    if (sc[2] > sel3(sc, a)) a = 2;
+    if (!(sel3(sc, a) > 0.f)) return false;
+    const float va = sel3(g.v, a);
+    const int na = sel3(g.n, a);
+    const float half = __fmul_rn(0.5f, (float)(na - 1));
     const float org = -__fmul_rn(half, va);
-    const float s1 = __fdiv_rn(__fsub_rn(p1[a], org), va);
-    const float s2 = __fdiv_rn(__fsub_rn(p2[a], org), va);
+    const float s1 = __fdiv_rn(__fsub_rn(sel3(p1, a), org), va);
+    const float s2 = __fdiv_rn(__fsub_rn(sel3(p2, a), org), va);
     float lo = ceilf(s1 < s2 ? s1 : s2), hi = floorf(s1 < s2 ? s2 : s1);
     if (lo < 0.f) lo = 0.f;
-    if (hi > (float)(g.n[a] - 1)) hi = (float)(g.n[a] - 1);
+    if (hi > (float)(na - 1)) hi = (float)(na - 1);
     if (!(lo <= hi)) return false;
     k.a = a;
     k.b = a == 0 ? 1 : 0;
@@ -92,23 +102,25 @@ __device__ __forceinline__ bool walk_setup(const float* __restrict__ lor, const 
         const double d = (double)p2[c] - (double)p1[c];
         len2 += d * d;
     }
-    const double da = e2[a] - e1[a];
-    const double t0 = ((double)k.q0 - e1[a]) / da;
-    const double db = e2[k.b] - e1[k.b], dc = e2[k.c] - e1[k.c];
-    k.u0 = (float)(e1[k.b] + t0 * db);
-    k.w0 = (float)(e1[k.c] + t0 * dc);
+    const double da = sel3(e2, a) - sel3(e1, a);
+    const double t0 = ((double)k.q0 - sel3(e1, a)) / da;
+    const double db = sel3(e2, k.b) - sel3(e1, k.b), dc = sel3(e2, k.c) - sel3(e1, k.c);
+    k.u0 = (float)(sel3(e1, k.b) + t0 * db);
+    k.w0 = (float)(sel3(e1, k.c) + t0 * dc);
     k.du = (float)(db / da);
     k.dw = (float)(dc / da);
-    k.step = (float)((double)va * sqrt(len2) / fabs((double)p2[a] - (double)p1[a]));
+    k.step = (float)((double)va * sqrt(len2) / fabs((double)sel3(p2, a) - (double)sel3(p1, a)));
     return true;
 }
 
-// Visits the in-image bilinear taps of every sample: fn(index, weight).
+// Visits the in-image bilinear taps of every sample, one image row of the
+// b axis at a time: fn(idx, ok0, ok1, w0, w1) for the taps idx (along c at
+// iw) and idx + stride_c (at iw + 1), each present only where ok.
 template <class F>
 __device__ __forceinline__ void walk(const Walk& k, const PetGrid& g, F&& fn)
 {
-    const long long sa = g.stride[k.a], sb = g.stride[k.b], sc = g.stride[k.c];
-    const int nb = g.n[k.b], nc = g.n[k.c];
+    const long long sa = sel3(g.stride, k.a), sb = sel3(g.stride, k.b), sc = sel3(g.stride, k.c);
+    const int nb = sel3(g.n, k.b), nc = sel3(g.n, k.c);
     for (int i = 0; i < k.count; ++i) {
         const float u = fmaf((float)i, k.du, k.u0);
         const float w = fmaf((float)i, k.dw, k.w0);
@@ -118,12 +130,48 @@ __device__ __forceinline__ void walk(const Walk& k, const PetGrid& g, F&& fn)
         const int iu = (int)fu, iw = (int)fw;
         const float tu = u - fu, tw = w - fw;
         const long long base = (long long)(k.q0 + i) * sa + (long long)iu * sb + (long long)iw * sc;
-        const bool u0ok = iu >= 0, u1ok = iu + 1 < nb, w0ok = iw >= 0, w1ok = iw + 1 < nc;
-        if (u0ok && w0ok) fn(base, (1.f - tu) * (1.f - tw));
-        if (u0ok && w1ok) fn(base + sc, (1.f - tu) * tw);
-        if (u1ok && w0ok) fn(base + sb, tu * (1.f - tw));
-        if (u1ok && w1ok) fn(base + sb + sc, tu * tw);
+        const bool w0ok = iw >= 0, w1ok = iw + 1 < nc;
+        if (iu >= 0) fn(base, w0ok, w1ok, (1.f - tu) * (1.f - tw), (1.f - tu) * tw);
+        if (iu + 1 < nb) fn(base + sb, w0ok, w1ok, tu * (1.f - tw), tu * tw);
     }
+}
+
+// w0 img[idx] + w1 img[idx + sc] over the present taps.  Two taps next to
+// each other in memory (sc == 1) inside one aligned 16-byte quad of the
+// image are read with one vector load.
+__device__ __forceinline__ float gather_pair(const float* __restrict__ img, long long idx, long long sc,
+                                             long long total, bool ok0, bool ok1, float w0, float w1)
+{
+    const long long q = idx & ~3LL;
+    const int r = (int)(idx & 3);
+    if (sc == 1 && ok0 && ok1 && r < 3 && q + 3 < total) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(img + q));
+        const float a = r == 0 ? v.x : r == 1 ? v.y : v.z;
+        const float b = r == 0 ? v.y : r == 1 ? v.z : v.w;
+        return fmaf(w1, b, w0 * a);
+    }
+    float acc = 0.f;
+    if (ok0) acc = w0 * __ldg(img + idx);
+    if (ok1) acc = fmaf(w1, __ldg(img + idx + sc), acc);
+    return acc;
+}
+
+// bp[idx] += v0, bp[idx + sc] += v1 over the present taps: one 16-byte
+// vector atomic when both fall in one aligned quad (the other two lanes add
+// +0, which leaves every non-negative value unchanged), else scalar atomics.
+__device__ __forceinline__ void scatter_pair(float* bp, long long idx, long long sc, long long total, bool ok0,
+                                             bool ok1, float v0, float v1)
+{
+    const long long q = idx & ~3LL;
+    const int r = (int)(idx & 3);
+    if (sc == 1 && ok0 && ok1 && r < 3 && q + 3 < total) {
+        const float4 v = make_float4(r == 0 ? v0 : 0.f, r == 0 ? v1 : r == 1 ? v0 : 0.f,
+                                     r == 1 ? v1 : r == 2 ? v0 : 0.f, r == 2 ? v1 : 0.f);
+        atomicAdd(reinterpret_cast<float4*>(bp + q), v);
+        return;
+    }
+    if (ok0) atomicAdd(bp + idx, v0);
+    if (ok1) atomicAdd(bp + idx + sc, v1);
 }
 
 struct LmArgs {
@@ -177,12 +225,19 @@ __global__ void __launch_bounds__(kPetThreads) pet_lm_kernel(LmArgs a)
             const float val = __ldg(a.vals + e) * (a.mult ? __ldg(a.mult + e) : 1.f);
             if (!hit || val == 0.f) continue;
             const float sv = val * k.step;
-            walk(k, a.g, [&](long long idx, float w) { atomicAdd(a.bp + idx, sv * w); });
+            const long long sc = sel3(a.g.stride, k.c);
+            walk(k, a.g, [&](long long idx, bool o0, bool o1, float w0, float w1) {
+                scatter_pair(a.bp, idx, sc, a.g.total, o0, o1, sv * w0, sv * w1);
+            });
             continue;
         }
         float acc = 0.f;
-        if (hit && (kMode != kModeMult || a.img != nullptr))
-            walk(k, a.g, [&](long long idx, float w) { acc = fmaf(w, __ldg(a.img + idx), acc); });
+        if (hit && (kMode != kModeMult || a.img != nullptr)) {
+            const long long sc = sel3(a.g.stride, k.c);
+            walk(k, a.g, [&](long long idx, bool o0, bool o1, float w0, float w1) {
+                acc += gather_pair(a.img, idx, sc, a.g.total, o0, o1, w0, w1);
+            });
+        }
         const float line = hit ? acc * k.step : 0.f;
         if (kMode == kModeFwd) {
             a.out[e] = a.mult ? __ldg(a.mult + e) * line : line;
@@ -197,7 +252,12 @@ __global__ void __launch_bounds__(kPetThreads) pet_lm_kernel(LmArgs a)
             cons += (double)p / (double)den;
             used += 1.0;
             const float sv = m / den * k.step;
-            if (hit) walk(k, a.g, [&](long long idx, float w) { atomicAdd(a.bp + idx, sv * w); });
+            if (hit) {
+                const long long sc = sel3(a.g.stride, k.c);
+                walk(k, a.g, [&](long long idx, bool o0, bool o1, float w0, float w1) {
+                    scatter_pair(a.bp, idx, sc, a.g.total, o0, o1, sv * w0, sv * w1);
+                });
+            }
         }
     }
     if (kMode == kModeEm && a.diag) block_add2(cons, used, a.diag);
@@ -436,6 +496,7 @@ int pet_plan_create(const pet_geom* geom, const float* mu_dev, void* stream, pet
     p->grid.stride[1] = g.nz;
     p->grid.stride[2] = 1;
     p->voxels = (long long)g.nx * g.ny * g.nz;
+    p->grid.total = p->voxels;
     // T_rr taps per axis, in double, stored as float
     for (int c = 0; c < 3; ++c) {
         RrTaps& t = p->taps[c];
