@@ -140,8 +140,8 @@ def draw_events(wl: PetWorkload, act: torch.Tensor, semi, device="cpu", chunk: i
     eff = (0.85 + 0.3 * torch.rand(sc.n_crystals, generator=cpu_gen, dtype=torch.float64)).to(device)
     n_rand = int(round(wl.randoms_frac * wl.prompts))
     n_true = wl.prompts - n_rand
-    p_vox = act.double().flatten().to(device)
-    p_vox = p_vox / p_vox.sum()
+    cdf = torch.cumsum(act.double().flatten().to(device), 0)
+    cdf = cdf / cdf[-1]
     shape = torch.tensor(wl.shape, device=device)
     vox = torch.tensor(wl.voxel, dtype=torch.float64, device=device)
     half = 0.5 * (shape.double() - 1.0)
@@ -149,7 +149,9 @@ def draw_events(wl: PetWorkload, act: torch.Tensor, semi, device="cpu", chunk: i
     have = 0
     while have < n_true:
         m = min(chunk, max(4 * (n_true - have), 1024))
-        idx = torch.multinomial(p_vox, m, replacement=True, generator=gen)
+        # emission voxel by inverse transform sampling of the activity
+        u = torch.rand(m, generator=gen, dtype=torch.float64, device=device)
+        idx = torch.clamp(torch.searchsorted(cdf, u, right=True), max=cdf.numel() - 1)
         k = idx % wl.shape[2]
         j = torch.div(idx, wl.shape[2], rounding_mode="floor") % wl.shape[1]
         i = torch.div(idx, wl.shape[1] * wl.shape[2], rounding_mode="floor")
