@@ -34,6 +34,15 @@
  *     A non-positive sigma turns it off.
  *   - T_omega: omega = exp(-(P_Sigma mu)) with mu in 1/mm (no T_rr on mu);
  *     T_eta: one factor eta per LOR.  mult = eta * omega.
+ *   - time of flight (or_pet_set_tof): n_b bins of width D (mm) centred at
+ *     c_b = (b - (n_b - 1)/2) D on the line's signed arc length l from its
+ *     midpoint (positive towards p2); a sample at l in bin b is weighted by
+ *     Phi((l - c_b + D/2)/sigma) - Phi((l - c_b - D/2)/sigma) (the Gaussian
+ *     timing kernel integrated over the bin).  Only samples of the window
+ *     |l - c_b| <= nsigma sigma + D/2 count; the window is a range of sample
+ *     indices taken in double precision from the line's set-up values with
+ *     the operation order written in tof_window() (the kernel's order).  The
+ *     attenuation factors never use time of flight.
  *   - listmode OSEM: subsets of events {e : e mod M == m}, visited
  *     m = 0..M-1; with p_e = mult_e (P_Sigma T_rr f)_e and the additive term
  *     s_e (randoms and scatter expected on that LOR),
@@ -90,12 +99,54 @@ static size_t vox(const pet_img* g, int i, int j, int k)
     return ((size_t)i * g->n[1] + j) * g->n[2] + k;
 }
 
+/* Time-of-flight model (module state, set by or_pet_set_tof; bins == NULL
+ * means no time of flight). */
+typedef struct {
+    int nb;
+    double bin_mm, sigma_mm, nsigma;
+    const int* bins;  /* per LOR index */
+} pet_tof;
+
+static pet_tof g_tof = {0, 0.0, 0.0, 0.0, NULL};
+
+void or_pet_set_tof(int n_bins, double bin_mm, double sigma_mm, double nsigma, const int* bins)
+{
+    g_tof.nb = n_bins;
+    g_tof.bin_mm = bin_mm;
+    g_tof.sigma_mm = sigma_mm;
+    g_tof.nsigma = nsigma;
+    g_tof.bins = n_bins > 0 ? bins : NULL;
+}
+
+/* Sample index window [*i_lo, *i_hi] of a line whose first sample sits at
+ * arc length l0 and whose samples are dl apart, for TOF bin `bin`. */
+static void tof_window(const pet_tof* tf, int bin, double l0, double dl, int count, int* i_lo, int* i_hi)
+{
+    const double c = ((double)bin - 0.5 * (double)(tf->nb - 1)) * tf->bin_mm;
+    const double w = tf->nsigma * tf->sigma_mm + 0.5 * tf->bin_mm;
+    double lo = (c - w - l0) / dl, hi = (c + w - l0) / dl;
+    if (dl < 0.0) {
+        const double t = lo;
+        lo = hi;
+        hi = t;
+    }
+    lo = ceil(lo);
+    hi = floor(hi);
+    if (lo < 0.0) lo = 0.0;
+    if (hi > (double)(count - 1)) hi = (double)(count - 1);
+    *i_lo = (int)lo;
+    *i_hi = lo <= hi ? (int)hi : (int)lo - 1;
+}
+
+static double std_normal_cdf(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
+
 /* Visit the samples of one LOR: for every plane q of the principal axis, the
- * four bilinear taps (voxel index, weight including the step length).  Taps
- * outside the image are skipped (they read 0 / receive nothing). */
+ * four bilinear taps (voxel index, weight including the step length and, with
+ * time of flight, the bin's timing weight).  Taps outside the image are
+ * skipped (they read 0 / receive nothing). */
 typedef void (*tap_fn)(size_t idx, double w, void* ctx);
 
-static void lor_walk(const pet_img* g, const double* lor, tap_fn fn, void* ctx)
+static void lor_walk(const pet_img* g, const double* lor, const pet_tof* tf, int bin, tap_fn fn, void* ctx)
 {
     int a, q_lo, q_hi;
     lor_planes(g, lor, &a, &q_lo, &q_hi);
@@ -109,8 +160,25 @@ static void lor_walk(const pet_img* g, const double* lor, tap_fn fn, void* ctx)
         d[t] = lor[3 + t] - lor[t];
         len2 += d[t] * d[t];
     }
-    const double step = g->v[a] * sqrt(len2) / fabs(d[a]);
-    for (int q = q_lo; q <= q_hi; ++q) {
+    const double len = sqrt(len2);
+    const double step = g->v[a] * len / fabs(d[a]);
+    int i_lo = 0, i_hi = q_hi - q_lo;
+    double l0 = 0.0, dl = 0.0, cb = 0.0;
+    if (tf) {
+        const double da = e2[a] - e1[a];
+        const double t0 = ((double)q_lo - e1[a]) / da;
+        l0 = (t0 - 0.5) * len;
+        dl = len / da;
+        tof_window(tf, bin, l0, dl, q_hi - q_lo + 1, &i_lo, &i_hi);
+        cb = ((double)bin - 0.5 * (double)(tf->nb - 1)) * tf->bin_mm;
+    }
+    for (int q = q_lo + i_lo; q <= q_lo + i_hi; ++q) {
+        double wt_tof = 1.0;
+        if (tf) {
+            const double l = ((q - e1[a]) / (e2[a] - e1[a]) - 0.5) * len;
+            wt_tof = std_normal_cdf((l - cb + 0.5 * tf->bin_mm) / tf->sigma_mm) -
+                     std_normal_cdf((l - cb - 0.5 * tf->bin_mm) / tf->sigma_mm);
+        }
         const double t = (q - e1[a]) / (e2[a] - e1[a]);
         const double u = e1[b] + t * (e2[b] - e1[b]);
         const double w = e1[c] + t * (e2[c] - e1[c]);
@@ -125,7 +193,7 @@ static void lor_walk(const pet_img* g, const double* lor, tap_fn fn, void* ctx)
                 idx[a] = q;
                 idx[b] = (int)iu;
                 idx[c] = (int)iw;
-                fn(vox(g, idx[0], idx[1], idx[2]), step * wt, ctx);
+                fn(vox(g, idx[0], idx[1], idx[2]), step * wt * wt_tof, ctx);
             }
     }
 }
@@ -169,17 +237,28 @@ void or_pet_planes(const double* lors, long n_lors, int nx, int ny, int nz, cons
     for (long e = 0; e < n_lors; ++e) lor_planes(&g, lors + 6 * e, out3 + 3 * e, out3 + 3 * e + 1, out3 + 3 * e + 2);
 }
 
-/* P_Sigma: line integral of f along each LOR (Joseph). */
+static const pet_tof* tof_on(void) { return g_tof.bins ? &g_tof : NULL; }
+
+static int tof_bin(const pet_tof* tf, long e) { return tf ? tf->bins[e] : 0; }
+
+static void joseph_fwd(const double* f, const pet_img* g, const double* lors, long n_lors, const pet_tof* tf,
+                       double* out)
+{
+#pragma omp parallel for schedule(dynamic, 256)
+    for (long e = 0; e < n_lors; ++e) {
+        fwd_ctx k = {f, 0.0};
+        lor_walk(g, lors + 6 * e, tf, tof_bin(tf, e), fwd_tap, &k);
+        out[e] = k.acc;
+    }
+}
+
+/* P_Sigma: line integral of f along each LOR (Joseph; with time of flight
+ * when or_pet_set_tof gave bins). */
 void or_joseph_fwd(const double* f, int nx, int ny, int nz, const double* v, const double* lors, long n_lors,
                    double* out)
 {
     const pet_img g = make_img(nx, ny, nz, v);
-#pragma omp parallel for schedule(dynamic, 256)
-    for (long e = 0; e < n_lors; ++e) {
-        fwd_ctx k = {f, 0.0};
-        lor_walk(&g, lors + 6 * e, fwd_tap, &k);
-        out[e] = k.acc;
-    }
+    joseph_fwd(f, &g, lors, n_lors, tof_on(), out);
 }
 
 /* P_Sigma^T: each LOR's value spread back along its samples (serial, so the
@@ -191,7 +270,7 @@ void or_joseph_back(const double* vals, const double* lors, long n_lors, int nx,
     memset(out, 0, sizeof(double) * (size_t)nx * ny * nz);
     for (long e = 0; e < n_lors; ++e) {
         back_ctx k = {out, vals[e]};
-        if (vals[e] != 0.0) lor_walk(&g, lors + 6 * e, back_tap, &k);
+        if (vals[e] != 0.0) lor_walk(&g, lors + 6 * e, tof_on(), tof_bin(tof_on(), e), back_tap, &k);
     }
 }
 
@@ -262,7 +341,8 @@ void or_pet_blur(const double* f, int nx, int ny, int nz, const double* v, doubl
 void or_pet_mult(const double* mu, int nx, int ny, int nz, const double* v, const double* lors, long n_lors,
                  const double* eta, double* out)
 {
-    if (mu) or_joseph_fwd(mu, nx, ny, nz, v, lors, n_lors, out);
+    const pet_img g = make_img(nx, ny, nz, v);
+    if (mu) joseph_fwd(mu, &g, lors, n_lors, NULL, out);
     for (long e = 0; e < n_lors; ++e) {
         const double om = mu ? exp(-out[e]) : 1.0;
         out[e] = (eta ? eta[e] : 1.0) * om;
@@ -316,14 +396,14 @@ void or_pet_lm_osem(const double* lors, const double* mult, const double* s, lon
         double cons = 0.0, used = 0.0;
         for (long e = m; e < n_ev; e += n_subsets) {
             fwd_ctx k = {fb, 0.0};
-            lor_walk(&g, lors + 6 * e, fwd_tap, &k);
+            lor_walk(&g, lors + 6 * e, tof_on(), tof_bin(tof_on(), e), fwd_tap, &k);
             const double p = mult[e] * k.acc;
             const double den = p + (s ? s[e] : 0.0);
             if (!(den > 0.0)) continue;
             cons += p / den;
             used += 1.0;
             back_ctx b = {bp, mult[e] / den};
-            lor_walk(&g, lors + 6 * e, back_tap, &b);
+            lor_walk(&g, lors + 6 * e, tof_on(), tof_bin(tof_on(), e), back_tap, &b);
         }
         or_pet_blur(bp, nx, ny, nz, v, sigma_mm, nsigma, bpb);
         for (size_t i = 0; i < total; ++i) {

@@ -12,6 +12,7 @@ with ``ndimage.convolve1d`` and taps from ``signal.windows.gaussian``.
 import numpy as np
 from scipy import ndimage
 from scipy.signal import windows
+from scipy.stats import norm
 
 
 def decisions(lor, shape, voxel):
@@ -57,25 +58,62 @@ def samples(lor, shape, voxel):
     return pts, step
 
 
-def joseph(f, lors, voxel):
+def tof_weights(lor, shape, voxel, tof, b):
+    """Timing weights of one line's samples for TOF bin b (tof = (n_bins,
+    bin_mm, sigma_mm, nsigma)): the Gaussian integrated over the bin, by
+    scipy's normal CDF, inside the window of sample indices (restated from
+    the reading, in double precision, same operation order)."""
+    nb, width, sigma, nsig = tof
+    a, q0, q1 = decisions(lor, shape, voxel)
+    lor = np.asarray(lor, dtype=np.float64)
+    v = np.asarray(voxel, dtype=np.float64)
+    e1 = np.empty(3)
+    e2 = np.empty(3)
+    len2 = 0.0
+    for t in range(3):
+        org = -0.5 * (shape[t] - 1) * v[t]
+        e1[t] = (lor[t] - org) / v[t]
+        e2[t] = (lor[3 + t] - org) / v[t]
+        d = lor[3 + t] - lor[t]
+        len2 += d * d
+    ln = np.sqrt(len2)
+    da = e2[a] - e1[a]
+    l0 = ((q0 - e1[a]) / da - 0.5) * ln
+    dl = ln / da
+    c = (b - 0.5 * (nb - 1)) * width
+    w = nsig * sigma + 0.5 * width
+    lo, hi = (c - w - l0) / dl, (c + w - l0) / dl
+    if dl < 0:
+        lo, hi = hi, lo
+    lo, hi = max(np.ceil(lo), 0.0), min(np.floor(hi), float(q1 - q0))
+    q = np.arange(q0, q1 + 1, dtype=np.float64)
+    ell = ((q - e1[a]) / da - 0.5) * ln
+    wt = norm.cdf((ell - c + 0.5 * width) / sigma) - norm.cdf((ell - c - 0.5 * width) / sigma)
+    i = np.arange(len(q))
+    return np.where((i >= lo) & (i <= hi), wt, 0.0)
+
+
+def joseph(f, lors, voxel, tof=None, bins=None):
     f = np.asarray(f, dtype=np.float64)
     out = np.zeros(len(lors))
     for e, lor in enumerate(lors):
         pts, step = samples(lor, f.shape, voxel)
         if len(pts):
             vals = ndimage.map_coordinates(f, pts.T, order=1, mode="grid-constant", cval=0.0, prefilter=False)
+            if tof is not None:
+                vals = vals * tof_weights(lor, f.shape, voxel, tof, bins[e])
             out[e] = step * vals.sum()
     return out
 
 
-def dense(lors, shape, voxel):
+def dense(lors, shape, voxel, tof=None, bins=None):
     """[n_lors][nvox] matrix of P_Sigma (from unit images)."""
     nvox = int(np.prod(shape))
     H = np.zeros((len(lors), nvox))
     for vx in range(nvox):
         b = np.zeros(nvox)
         b[vx] = 1.0
-        H[:, vx] = joseph(b.reshape(shape), lors, voxel)
+        H[:, vx] = joseph(b.reshape(shape), lors, voxel, tof, bins)
     return H
 
 

@@ -222,3 +222,86 @@ def test_listmode_osem_conserves_counts(s_val):
         if s_val == 0.0:
             assert diag[0, 1] == len(sub)
         x = xn
+
+
+# ---------------------------------------------------------------- time of flight
+
+TOF = (9, 6.0, 5.0, 3.0)  # bins, bin width (mm), sigma (mm), truncation
+
+
+def _tof(bins, tof=TOF):
+    return pet.Tof(n_bins=tof[0], bin_mm=tof[1], sigma_mm=tof[2], nsigma=tof[3], bins=bins)
+
+
+def test_tof_point_source_closed_form():
+    """A line along x through the centre of one hot voxel: its projection in
+    bin b is the step times the Gaussian integrated over the bin at the
+    voxel's arc length (scipy's normal CDF)."""
+    from scipy.stats import norm
+    shape, voxel = (21, 5, 5), (2.0, 2.0, 2.0)
+    g = pet.PetGeom(shape, voxel)
+    f = np.zeros(shape)
+    f[13, 2, 2] = 1.0
+    nb, width, sigma, nsig = 11, 4.0, 3.0, 3.0
+    lor = np.array([-30.0, 0.0, 0.0, 34.0, 0.0, 0.0])  # midpoint at x = 2 mm
+    x_hot = (13 - 10) * 2.0
+    ell = x_hot - 2.0
+    got = [pet.joseph_fwd(f, lor[None], g, _tof([b], (nb, width, sigma, nsig)))[0] for b in range(nb)]
+    for b in range(nb):
+        c = (b - 0.5 * (nb - 1)) * width
+        want = 2.0 * (norm.cdf((ell - c + width / 2) / sigma) - norm.cdf((ell - c - width / 2) / sigma))
+        if abs(ell - c) > nsig * sigma + width / 2:
+            want = 0.0
+        assert abs(got[b] - want) <= 1e-14
+
+
+def test_tof_bins_sum_to_non_tof():
+    """Bins that cover the line and a window wide enough to cut nothing:
+    the bins' projections add up to the non-TOF projection."""
+    lors = mixed_lors(21, count=40)
+    g = pet.PetGeom(SHAPE, VOXEL)
+    f = _rng(22).uniform(size=SHAPE)
+    ref = pet.joseph_fwd(f, lors, g)
+    nb, width, sigma = 81, 10.0, 4.0
+    tot = np.zeros(len(lors))
+    for b in range(nb):
+        tot += pet.joseph_fwd(f, lors, g, _tof([b] * len(lors), (nb, width, sigma, 40.0)))
+    assert np.max(np.abs(tot - ref)) <= 1e-12 * max(1.0, np.max(ref))
+
+
+def test_tof_joseph_equals_scipy_dense_matrix():
+    lors = mixed_lors(23, count=40)
+    bins = _rng(24).integers(0, TOF[0], size=len(lors))
+    g = pet.PetGeom(SHAPE, VOXEL)
+    H = pet_brute.dense(lors, SHAPE, VOXEL, TOF, bins)
+    f = _rng(25).uniform(size=SHAPE)
+    got = pet.joseph_fwd(f, lors, g, _tof(bins))
+    assert np.max(np.abs(got - H @ f.ravel())) <= 1e-12 * max(1.0, np.max(np.abs(got)))
+    v = _rng(26).normal(size=len(lors))
+    back = pet.joseph_back(v, lors, g, _tof(bins)).ravel()
+    assert np.max(np.abs(back - H.T @ v)) <= 1e-12 * max(1.0, np.max(np.abs(back)))
+    assert np.count_nonzero(H.sum(axis=1)) > len(lors) // 3
+
+
+def test_tof_listmode_em_equals_binned_mlem():
+    rng = _rng(27)
+    lines = mixed_lors(27, count=25)
+    g = pet.PetGeom(SHAPE, VOXEL, rr_sigma_mm=1.5)
+    bins = rng.integers(0, TOF[0], size=len(lines))
+    m_line = rng.uniform(0.6, 1.0, size=len(lines))
+    H = m_line[:, None] * (pet_brute.dense(lines, SHAPE, VOXEL, TOF, bins) @
+                           pet_brute.dense_blur(SHAPE, VOXEL, 1.5))
+    keep = H.sum(axis=1) > 0
+    lines, bins, m_line, H = lines[keep], bins[keep], m_line[keep], H[keep]
+    y = rng.integers(0, 4, size=len(lines))
+    ev = np.repeat(np.arange(len(lines)), y)
+    rng.shuffle(ev)
+    sens = H.sum(axis=0) + 0.1  # any positive sensitivity image
+    x0 = rng.uniform(0.5, 1.5, size=SHAPE)
+    s_val = 0.02
+    x, diag = pet.lm_osem(lines[ev], m_line[ev], np.full(len(ev), s_val), sens.reshape(SHAPE), g, 1, x0=x0,
+                          tof=_tof(bins[ev]))
+    p = H @ x0.ravel()
+    ref = x0.ravel() * (H.T @ (y / (p + s_val))) / sens
+    assert np.max(np.abs(x.ravel() - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert abs(diag[0, 0] - np.sum(y * p / (p + s_val))) <= 1e-11 * diag[0, 0]
