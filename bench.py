@@ -66,6 +66,8 @@ def parse_args():
     ap.add_argument("--pet-only", action="store_true",
                     help="run only the listmode PET leg (one GPU) and print it as one JSON line")
     ap.add_argument("--pet-prompts", type=int, default=None, help="prompts of the PET leg (default 30 M)")
+    ap.add_argument("--pet-workload", default="petlm204tof", choices=["petlm204tof", "petlm204"],
+                    help="PET workload of --pet-only")
     return ap.parse_args()
 
 
@@ -441,23 +443,26 @@ def run_orbit_leg(spect, torch, dev, wl, g, f_raw, mu, x, timed, max_over_ranks,
             "subset_iters_per_s": replica_throughput(world, k, n_sub, ms), "ms_per_recon": ms / k}
 
 
-def run_pet_leg(torch, dev, timed, max_over_ranks, world, k, cpu_seconds: float, with_cpu: bool, prompts=None):
+def run_pet_leg(torch, dev, timed, max_over_ranks, world, k, cpu_seconds: float, with_cpu: bool, prompts=None,
+                workload: str = "petlm204tof"):
     """Listmode PET (Eq. PET_SM, Joseph projector, listmode OSEM) on the
     paper's PET grid: 204 x 204 x 154 voxels of 1.25 mm, a 338 mm scanner of
     64 rings x 448 crystals, 3 mm FWHM resolution model, 30 M prompts (10 %
-    randoms) in 3 subsets.  The sensitivity image comes from the pairs of
-    every 4th crystal of every 2nd ring, each weighted 64 (plan-time input,
-    not timed).  Timed: one listmode OSEM iteration (3 subiterations over all
-    30 M events) per step."""
+    randoms) in 3 subsets; petlm204tof adds the paper's time of flight
+    (550 ps, 21 bins over 30 cm).  The sensitivity image comes from the
+    pairs of every 4th crystal of every 2nd ring, each weighted 64 (plan-time
+    input, not timed).  Timed: one listmode OSEM iteration (3 subiterations
+    over all 30 M events) per step."""
     from paper_2309_01977_gb300 import pet, pet_phantom as pp
     import dataclasses
-    wl = pp.PET_WORKLOADS["petlm204"]
+    wl = pp.PET_WORKLOADS[workload]
     if prompts:
         wl = dataclasses.replace(wl, prompts=int(prompts))
     act, mu, semi = pp.head_phantom(wl.shape, wl.voxel, wl.seed, device=dev)
-    lors, eta, s, n_true = pp.draw_events(wl, act, semi, device=dev)
+    lors, eta, s, n_true, tof_bin = pp.draw_events(wl, act, semi, device=dev)
     torch.cuda.empty_cache()
-    g = pet.PetGeometry(wl.shape, wl.voxel, rr_sigma_mm=wl.rr_sigma_mm, n_subsets=wl.n_subsets)
+    g = pet.PetGeometry(wl.shape, wl.voxel, rr_sigma_mm=wl.rr_sigma_mm, n_subsets=wl.n_subsets,
+                        n_tof_bins=wl.tof_bins, tof_bin_mm=wl.tof_bin_mm, tof_sigma_mm=wl.tof_sigma_mm)
     plan = pet.PetPlan(g, mu)
     mult = plan.mult(lors, eta)
     L_all, eta_all, w = pp.scanner_lors(wl.scanner, angle_step=4, ring_step=2, device=dev, eff_seed=wl.seed)
@@ -470,7 +475,7 @@ def run_pet_leg(torch, dev, timed, max_over_ranks, world, k, cpu_seconds: float,
 
     def step():
         x.fill_(1.0)
-        plan.lm_osem(lors, mult, s, sens, x, 0, M)
+        plan.lm_osem(lors, mult, s, sens, x, 0, M, tof_bin=tof_bin)
     step()
     torch.cuda.synchronize()
     ms = max_over_ranks(timed(step, k))
@@ -479,26 +484,32 @@ def run_pet_leg(torch, dev, timed, max_over_ranks, world, k, cpu_seconds: float,
     timed(step, k)
     prof = plan.profile_read(reset=True)
     plan.profile_enable(False)
-    em = prof.get("joseph_em", (1, float("nan")))
-    samples = float(sum(pet_sample_count(lors, wl)))  # bilinear samples per pass over all events
-    leg = {"workload": "petlm204: 204x204x154 (1.25 mm), 64x448-crystal scanner (r 338 mm), %d prompts "
-                       "(%d trues, 10%% randoms), 3 subsets, 3 mm FWHM T_rr, attenuation + normalisation" % (
-                           n_ev, n_true),
+    em_name = "joseph_em_tof" if tof_bin is not None else "joseph_em"
+    em = prof.get(em_name, (0, float("nan")))
+    samples = float(sum(pet_sample_count(lors, wl)))  # Joseph planes per pass over all events
+    leg = {"workload": "%s: 204x204x154 (1.25 mm), 64x448-crystal scanner (r 338 mm), %d prompts "
+                       "(%d trues, 10%% randoms), 3 subsets, 3 mm FWHM T_rr, attenuation + normalisation%s" % (
+                           wl.name, n_ev, n_true,
+                           ", TOF %d bins of %.2f mm, sigma %.1f mm (%.0f ps)" % (
+                               wl.tof_bins, wl.tof_bin_mm, wl.tof_sigma_mm, wl.tof_fwhm_ps) if wl.tof_bins else ""),
            "step": "one listmode OSEM iteration (3 subiterations over all events) from f0 = 1",
            "events_per_s": replica_throughput(world, k, n_ev, ms), "ms_per_iteration": ms / k,
            "kernel_avg_ms": {kk: round(v[1] / v[0], 3) for kk, v in prof.items()},
-           # each joseph_em launch walks one subset: 1/M of the events
-           "joseph_em_samples_per_s": samples * (em[0] / M) / (em[1] * 1e-3) if em[0] else None}
+           # each launch walks one subset: 1/M of the events (planes of the
+           # whole line; with time of flight only the window is visited)
+           "em_kernel": em_name,
+           "em_planes_per_s": samples * (em[0] / M) / (em[1] * 1e-3) if em[0] else None}
     l2 = os.path.join(ROOT, "profiles", "l2_petlm204.json")
     if os.path.exists(l2):
         with open(l2) as fh:
             prof_l2 = json.load(fh).get("joseph_em")
         # the walk gathers from and scatters into an image held in L2: its
         # bound is L2 throughput, measured by ncu as a fraction of L2 peak
-        leg["roofline"] = {"bound": "l2", "kernel": "joseph_em", "frac": prof_l2["lts_throughput_frac"],
-                           "source": "ncu lts__throughput of the same kernel (profiles/pet_lm_em_petlm204.md)"}
+        if prof_l2 and tof_bin is None:
+            leg["roofline"] = {"bound": "l2", "kernel": "joseph_em", "frac": prof_l2["lts_throughput_frac"],
+                               "source": "ncu lts__throughput of the same kernel (profiles/pet_lm_em_petlm204.md)"}
     if with_cpu:
-        leg["cpu_baseline"] = pet_cpu_baseline(wl, act, mu, lors, mult, s, sens, cpu_seconds)
+        leg["cpu_baseline"] = pet_cpu_baseline(wl, act, mu, lors, mult, s, sens, cpu_seconds, tof_bin)
     plan.close()
     return leg
 
@@ -519,28 +530,34 @@ def pet_sample_count(lors, wl):
     return [float(np.clip(hi - lo + 1, 0, None).sum())]
 
 
-def pet_cpu_baseline(wl, act, mu, lors, mult, s, sens, seconds):
+def pet_cpu_baseline(wl, act, mu, lors, mult, s, sens, seconds, tof_bin=None):
     """The FP64 oracle's listmode OSEM on the host cores for a bounded sample:
     one subiteration over the first events of subset 0, as many as fit in
     about `seconds` (measured on a small probe first), scaled to events/s."""
     from oracle import pet as opet
     og = opet.PetGeom(wl.shape, wl.voxel, rr_sigma_mm=float(np.float32(wl.rr_sigma_mm)), rr_nsigma=3.0)
     M = wl.n_subsets
+
+    def tof(n):
+        if tof_bin is None:
+            return None
+        return opet.Tof(n_bins=wl.tof_bins, bin_mm=float(np.float32(wl.tof_bin_mm)),
+                        sigma_mm=float(np.float32(wl.tof_sigma_mm)), bins=tof_bin[:n].cpu().numpy())
     L = lors[:M * 20000].cpu().numpy()
     m = mult[:M * 20000].cpu().numpy()
     sv = s[:M * 20000].cpu().numpy()
     sn = sens.cpu().numpy()
     t0 = time.perf_counter()
-    opet.lm_osem(L, m, sv, sn, og, M, count=1)
+    opet.lm_osem(L, m, sv, sn, og, M, count=1, tof=tof(M * 20000))
     el = time.perf_counter() - t0
     n = int(min(lors.shape[0], M * 20000 * max(1.0, seconds / max(el, 1e-3))))
     L = lors[:n].cpu().numpy()
     t0 = time.perf_counter()
-    opet.lm_osem(L, mult[:n].cpu().numpy(), s[:n].cpu().numpy(), sn, og, M, count=1)
+    opet.lm_osem(L, mult[:n].cpu().numpy(), s[:n].cpu().numpy(), sn, og, M, count=1, tof=tof(n))
     el = time.perf_counter() - t0
     import oracle
     return {"value": (n // M) / el, "unit": "events/s", "cores": oracle.n_threads(), "kind": "oracle",
-            "sample": "one listmode subiteration over %d events of petlm204 (FP64, %.1f s)" % (n // M, el)}
+            "sample": "one listmode subiteration over %d events of %s (FP64, %.1f s)" % (n // M, wl.name, el)}
 
 
 def run_libspect(args):
@@ -683,8 +700,11 @@ def run_libspect(args):
         legs["multipeak"] = run_multipeak_leg(spect, torch, dev, wl, g, plan, f_raw, mu, y_dev, s, x, timed,
                                               max_over_ranks, world, max(2, args.steps // 2))
     if not args.no_pet:
+        with_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
         legs["pet"] = run_pet_leg(torch, dev, timed, max_over_ranks, world, max(2, args.steps // 8),
-                                  args.cpu_seconds / 2, rank == 0 and world == 1 and not args.no_cpu_baseline)
+                                  args.cpu_seconds / 2, with_cpu, workload="petlm204tof")
+        legs["pet_nontof"] = run_pet_leg(torch, dev, timed, max_over_ranks, world, max(2, args.steps // 8),
+                                         args.cpu_seconds / 2, False, workload="petlm204")
     if not args.no_orbit:
         legs["orbit"] = run_orbit_leg(spect, torch, dev, wl, g, f_raw, mu, x, timed, max_over_ranks, world,
                                       max(2, args.steps // 2))
@@ -739,7 +759,7 @@ def run_pet_only(args):
         return sum(e0.elapsed_time(e1) for e0, e1 in evs)
 
     leg = run_pet_leg(torch, dev, timed, lambda v: v, 1, max(2, args.steps // 8), args.cpu_seconds / 2,
-                      not args.no_cpu_baseline, prompts=args.pet_prompts)
+                      not args.no_cpu_baseline, prompts=args.pet_prompts, workload=args.pet_workload)
     print(json.dumps({"pet": leg}), flush=True)
     return 0
 

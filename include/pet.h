@@ -28,6 +28,13 @@
  *     |t| <= ceil(rr_nsigma s), normalised to sum 1, zero padding; off when
  *     rr_sigma_mm <= 0.
  *   - mu in 1/mm; mult_e = eta_e exp(-(P_Sigma mu)_e) (no T_rr on mu).
+ *   - time of flight (n_tof_bins > 0 and a tof_bin array): bin b is centred
+ *     at c_b = (b - (n_tof_bins - 1)/2) tof_bin_mm on the arc length l from
+ *     the line's midpoint (positive towards the second end); each sample is
+ *     weighted by Phi((l - c_b + w/2)/sigma) - Phi((l - c_b - w/2)/sigma),
+ *     w the bin width, over the window |l - c_b| <= nsigma sigma + w/2 taken
+ *     as a range of sample indices in double precision.  Attenuation factors
+ *     and the sensitivity image are computed without time of flight.
  *   - listmode OSEM: subsets {e : e mod n_subsets == m}, visited m = 0..M-1;
  *     p_e = mult_e (P_Sigma T_rr f)_e,
  *       f <- f * T_rr P_Sigma^T(mult / (p + s))|_{S_m} / (sens / M),
@@ -61,6 +68,10 @@ typedef struct pet_geom {
     float rr_sigma_mm;    /* T_rr standard deviation, mm (<= 0: off) */
     float rr_nsigma;      /* T_rr truncation in standard deviations (3) */
     int n_subsets;        /* listmode subsets {e mod n_subsets} (>= 1) */
+    int n_tof_bins;       /* time-of-flight bins (0: no time of flight) */
+    float tof_bin_mm;     /* bin width along the line, mm */
+    float tof_sigma_mm;   /* standard deviation of the Gaussian timing kernel, mm */
+    float tof_nsigma;     /* kernel truncation: |l - c_b| <= tof_nsigma sigma + width / 2 (3) */
 } pet_geom;
 
 typedef struct pet_plan pet_plan;
@@ -74,23 +85,26 @@ int pet_plan_destroy(pet_plan* plan);
  * plan without mu: omega = 1). */
 int pet_mult(pet_plan* plan, const float* lors, const float* eta, int64_t n, float* mult_out, void* stream);
 
-/* out[e] = mult[e] * (P_Sigma T_rr x)_e (mult NULL: 1). */
-int pet_forward(pet_plan* plan, const float* x, const float* lors, const float* mult, int64_t n, float* out,
-                void* stream);
+/* out[e] = mult[e] * (P_Sigma T_rr x)_e (mult NULL: 1; tof_bin NULL: no
+ * time of flight, else the bin of every LOR). */
+int pet_forward(pet_plan* plan, const float* x, const float* lors, const float* mult, const int* tof_bin, int64_t n,
+                float* out, void* stream);
 
-/* x_out = T_rr P_Sigma^T (mult * q) over n LORs (overwrites x_out). */
-int pet_back(pet_plan* plan, const float* q, const float* lors, const float* mult, int64_t n, float* x_out,
-             void* stream);
+/* x_out = T_rr P_Sigma^T (mult * q) over n LORs (overwrites x_out; tof_bin
+ * as for pet_forward). */
+int pet_back(pet_plan* plan, const float* q, const float* lors, const float* mult, const int* tof_bin, int64_t n,
+             float* x_out, void* stream);
 
 /* Listmode OSEM subiterations first_subiter .. first_subiter + n_subiters - 1
  * (subset = subiteration mod n_subsets) on events lors[n] with factors
- * mult[n] and additive terms s[n] (NULL: 0); sens = T_rr P_Sigma^T mult over
- * all scanner LORs.  diag_out (host, NULL or 2 * n_subiters doubles): per
+ * mult[n], additive terms s[n] (NULL: 0) and time-of-flight bins tof_bin[n]
+ * (NULL: no time of flight); sens = T_rr P_Sigma^T mult over all scanner
+ * LORs (without time of flight).  diag_out (host, NULL or 2 * n_subiters doubles): per
  * subiteration sum_e p_e / (p_e + s_e) over its events and the number of its
  * events with p_e + s_e > 0, in FP64; filling it synchronises the stream. */
-int pet_lm_osem_run(pet_plan* plan, const float* lors, const float* mult, const float* s, int64_t n,
-                    const float* sens, float* x_inout, int first_subiter, int n_subiters, double* diag_out,
-                    void* stream);
+int pet_lm_osem_run(pet_plan* plan, const float* lors, const float* mult, const float* s, const int* tof_bin,
+                    int64_t n, const float* sens, float* x_inout, int first_subiter, int n_subiters,
+                    double* diag_out, void* stream);
 
 /* Per-kernel CUDA-event timing on the launch stream (off by default). */
 int pet_profile_enable(pet_plan* plan, int on);

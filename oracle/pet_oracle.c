@@ -133,9 +133,11 @@ static void tof_window(const pet_tof* tf, int bin, double l0, double dl, int cou
     lo = ceil(lo);
     hi = floor(hi);
     if (lo < 0.0) lo = 0.0;
+    if (lo > (double)count) lo = (double)count;
     if (hi > (double)(count - 1)) hi = (double)(count - 1);
+    if (hi < -1.0) hi = -1.0;
     *i_lo = (int)lo;
-    *i_hi = lo <= hi ? (int)hi : (int)lo - 1;
+    *i_hi = (int)hi;
 }
 
 static double std_normal_cdf(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }

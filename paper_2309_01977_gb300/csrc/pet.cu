@@ -51,6 +51,18 @@ enum PetMode { kModeFwd = 0, kModeMult = 1, kModeBack = 2, kModeEm = 3 };
 struct Walk {
     int a, b, c, q0, count;
     float u0, du, w0, dw, step;
+    int i0, i1;       // samples visited (the time-of-flight window, else 0 .. count - 1)
+    float l0, dl;     // arc length of sample 0 from the line's midpoint and its step (mm)
+};
+
+// Time of flight: bins of `width` mm centred at (b - (nb - 1)/2) width on the
+// arc length from the line's midpoint (positive towards the second end);
+// the Gaussian timing kernel integrated over the bin, truncated at
+// nsigma sigma + width / 2.
+struct TofParams {
+    int nb;             // bins (0: no time of flight)
+    float width, sigma, nsigma;
+    float inv_s2;       // 1 / (sqrt(2) sigma)
 };
 
 // Element i of a three-element array with constant indices only, so that
@@ -61,7 +73,9 @@ __device__ __forceinline__ T sel3(const T (&v)[3], int i)
     return i == 0 ? v[0] : i == 1 ? v[1] : v[2];
 }
 
-__device__ __forceinline__ bool walk_setup(const float* __restrict__ lor, const PetGrid& g, Walk& k)
+template <bool kTof>
+__device__ __forceinline__ bool walk_setup(const float* __restrict__ lor, const PetGrid& g, Walk& k,
+                                           const TofParams& tp, int bin, float& cb)
 {
     const float2 l0 = __ldg(reinterpret_cast<const float2*>(lor));
     const float2 l1 = __ldg(reinterpret_cast<const float2*>(lor) + 1);
@@ -92,36 +106,72 @@ __device__ __forceinline__ bool walk_setup(const float* __restrict__ lor, const 
     k.q0 = (int)lo;
     k.count = (int)hi - k.q0 + 1;
     // sample positions in double precision from the single-precision ends
+    // (double operations spelled out where the time-of-flight window, an
+    // integer, depends on their rounding)
     double e1[3], e2[3], len2 = 0.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const double v = (double)g.v[c];
-        const double o = -0.5 * (double)(g.n[c] - 1) * v;
-        e1[c] = ((double)p1[c] - o) / v;
-        e2[c] = ((double)p2[c] - o) / v;
-        const double d = (double)p2[c] - (double)p1[c];
-        len2 += d * d;
+        const double o = __dmul_rn(-0.5 * (double)(g.n[c] - 1), v);
+        e1[c] = __ddiv_rn(__dsub_rn((double)p1[c], o), v);
+        e2[c] = __ddiv_rn(__dsub_rn((double)p2[c], o), v);
+        const double d = __dsub_rn((double)p2[c], (double)p1[c]);
+        len2 = __dadd_rn(len2, __dmul_rn(d, d));
     }
-    const double da = sel3(e2, a) - sel3(e1, a);
-    const double t0 = ((double)k.q0 - sel3(e1, a)) / da;
+    const double da = __dsub_rn(sel3(e2, a), sel3(e1, a));
+    const double t0 = __ddiv_rn(__dsub_rn((double)k.q0, sel3(e1, a)), da);
     const double db = sel3(e2, k.b) - sel3(e1, k.b), dc = sel3(e2, k.c) - sel3(e1, k.c);
     k.u0 = (float)(sel3(e1, k.b) + t0 * db);
     k.w0 = (float)(sel3(e1, k.c) + t0 * dc);
     k.du = (float)(db / da);
     k.dw = (float)(dc / da);
-    k.step = (float)((double)va * sqrt(len2) / fabs((double)sel3(p2, a) - (double)sel3(p1, a)));
+    const double len = __dsqrt_rn(len2);
+    k.step = (float)((double)va * len / fabs((double)sel3(p2, a) - (double)sel3(p1, a)));
+    k.i0 = 0;
+    k.i1 = k.count - 1;
+    if (kTof) {
+        const double l0 = __dmul_rn(__dsub_rn(t0, 0.5), len);
+        const double dl = __ddiv_rn(len, da);
+        const double width = (double)tp.width;
+        const double c = __dmul_rn(__dsub_rn((double)bin, __dmul_rn(0.5, (double)(tp.nb - 1))), width);
+        const double w = __dadd_rn(__dmul_rn((double)tp.nsigma, (double)tp.sigma), __dmul_rn(0.5, width));
+        double lo = __ddiv_rn(__dsub_rn(__dsub_rn(c, w), l0), dl);
+        double hi = __ddiv_rn(__dsub_rn(__dadd_rn(c, w), l0), dl);
+        if (dl < 0.0) {
+            const double t = lo;
+            lo = hi;
+            hi = t;
+        }
+        lo = ceil(lo);
+        hi = floor(hi);
+        if (lo < 0.0) lo = 0.0;
+        if (lo > (double)k.count) lo = (double)k.count;
+        if (hi > (double)(k.count - 1)) hi = (double)(k.count - 1);
+        if (hi < -1.0) hi = -1.0;
+        k.i0 = (int)lo;
+        k.i1 = (int)hi;
+        k.l0 = (float)l0;
+        k.dl = (float)dl;
+        cb = (float)c;
+    }
     return true;
 }
 
 // Visits the in-image bilinear taps of every sample, one image row of the
 // b axis at a time: fn(idx, ok0, ok1, w0, w1) for the taps idx (along c at
 // iw) and idx + stride_c (at iw + 1), each present only where ok.
-template <class F>
-__device__ __forceinline__ void walk(const Walk& k, const PetGrid& g, F&& fn)
+template <bool kTof, class F>
+__device__ __forceinline__ void walk(const Walk& k, const PetGrid& g, const TofParams& tp, float cb, F&& fn)
 {
     const long long sa = sel3(g.stride, k.a), sb = sel3(g.stride, k.b), sc = sel3(g.stride, k.c);
     const int nb = sel3(g.n, k.b), nc = sel3(g.n, k.c);
-    for (int i = 0; i < k.count; ++i) {
+    const float hw = 0.5f * tp.width;
+    for (int i = k.i0; i <= k.i1; ++i) {
+        float wt = 1.f;
+        if (kTof) {
+            const float l = fmaf((float)i, k.dl, k.l0) - cb;
+            wt = 0.5f * (erff((l + hw) * tp.inv_s2) - erff((l - hw) * tp.inv_s2));
+        }
         const float u = fmaf((float)i, k.du, k.u0);
         const float w = fmaf((float)i, k.dw, k.w0);
         const float fu = floorf(u), fw = floorf(w);
@@ -131,8 +181,9 @@ __device__ __forceinline__ void walk(const Walk& k, const PetGrid& g, F&& fn)
         const float tu = u - fu, tw = w - fw;
         const long long base = (long long)(k.q0 + i) * sa + (long long)iu * sb + (long long)iw * sc;
         const bool w0ok = iw >= 0, w1ok = iw + 1 < nc;
-        if (iu >= 0) fn(base, w0ok, w1ok, (1.f - tu) * (1.f - tw), (1.f - tu) * tw);
-        if (iu + 1 < nb) fn(base + sb, w0ok, w1ok, tu * (1.f - tw), tu * tw);
+        const float ru = (1.f - tu) * wt, su = tu * wt;
+        if (iu >= 0) fn(base, w0ok, w1ok, ru * (1.f - tw), ru * tw);
+        if (iu + 1 < nb) fn(base + sb, w0ok, w1ok, su * (1.f - tw), su * tw);
     }
 }
 
@@ -183,8 +234,10 @@ struct LmArgs {
     const float* s;       // kModeEm: [n] or nullptr (0)
     float* out;           // kModeFwd / kModeMult: [n]
     double* diag;         // kModeEm: 2 doubles (sum p/(p+s), events used) or nullptr
+    const int* tof_bin;   // [n] time-of-flight bins (kTof kernels)
     long long first, stride, count;  // events first + t * stride, t < count
     PetGrid g;
+    TofParams tof;
 };
 
 __device__ __forceinline__ void block_add2(double a, double b, double* dst)
@@ -212,7 +265,7 @@ __device__ __forceinline__ void block_add2(double a, double b, double* dst)
     }
 }
 
-template <int kMode>
+template <int kMode, bool kTof>
 __global__ void __launch_bounds__(kPetThreads) pet_lm_kernel(LmArgs a)
 {
     double cons = 0.0, used = 0.0;
@@ -220,13 +273,14 @@ __global__ void __launch_bounds__(kPetThreads) pet_lm_kernel(LmArgs a)
          t += (long long)gridDim.x * blockDim.x) {
         const long long e = a.first + t * a.stride;
         Walk k;
-        const bool hit = walk_setup(a.lors + 6 * e, a.g, k);
+        float cb = 0.f;
+        const bool hit = walk_setup<kTof>(a.lors + 6 * e, a.g, k, a.tof, kTof ? __ldg(a.tof_bin + e) : 0, cb);
         if (kMode == kModeBack) {
             const float val = __ldg(a.vals + e) * (a.mult ? __ldg(a.mult + e) : 1.f);
             if (!hit || val == 0.f) continue;
             const float sv = val * k.step;
             const long long sc = sel3(a.g.stride, k.c);
-            walk(k, a.g, [&](long long idx, bool o0, bool o1, float w0, float w1) {
+            walk<kTof>(k, a.g, a.tof, cb, [&](long long idx, bool o0, bool o1, float w0, float w1) {
                 scatter_pair(a.bp, idx, sc, a.g.total, o0, o1, sv * w0, sv * w1);
             });
             continue;
@@ -234,7 +288,7 @@ __global__ void __launch_bounds__(kPetThreads) pet_lm_kernel(LmArgs a)
         float acc = 0.f;
         if (hit && (kMode != kModeMult || a.img != nullptr)) {
             const long long sc = sel3(a.g.stride, k.c);
-            walk(k, a.g, [&](long long idx, bool o0, bool o1, float w0, float w1) {
+            walk<kTof>(k, a.g, a.tof, cb, [&](long long idx, bool o0, bool o1, float w0, float w1) {
                 acc += gather_pair(a.img, idx, sc, a.g.total, o0, o1, w0, w1);
             });
         }
@@ -254,7 +308,7 @@ __global__ void __launch_bounds__(kPetThreads) pet_lm_kernel(LmArgs a)
             const float sv = m / den * k.step;
             if (hit) {
                 const long long sc = sel3(a.g.stride, k.c);
-                walk(k, a.g, [&](long long idx, bool o0, bool o1, float w0, float w1) {
+                walk<kTof>(k, a.g, a.tof, cb, [&](long long idx, bool o0, bool o1, float w0, float w1) {
                     scatter_pair(a.bp, idx, sc, a.g.total, o0, o1, sv * w0, sv * w1);
                 });
             }
@@ -352,6 +406,7 @@ struct pet_plan {
     PetGrid grid{};
     RrTaps taps[3]{};
     bool rr = false;
+    TofParams tof{};
     long long voxels = 0;
     float* mu = nullptr;
     float* t1 = nullptr;
@@ -449,7 +504,15 @@ LmArgs base_args(const pet_plan* p, const float* lors, long long n)
     a.stride = 1;
     a.count = n;
     a.g = p->grid;
+    a.tof = p->tof;
     return a;
+}
+
+int check_tof(const pet_plan* p, const int* tof_bin, int64_t n)
+{
+    if (tof_bin && p->tof.nb == 0) return pfail(SPECT_EINVAL, "tof_bin given to a plan without time of flight");
+    if (tof_bin && n > 0 && !aligned(tof_bin, 4)) return pfail(SPECT_EINVAL, "tof_bin must be 4-byte aligned");
+    return SPECT_OK;
 }
 
 int check_lors(const pet_plan* p, const float* lors, int64_t n)
@@ -483,9 +546,19 @@ int pet_plan_create(const pet_geom* geom, const float* mu_dev, void* stream, pet
     const bool rr = g.rr_sigma_mm > 0.f;
     if (rr && !(g.rr_nsigma > 0.f)) return pfail(SPECT_EINVAL, "rr_nsigma must be > 0");
     if (mu_dev && !aligned(mu_dev, 16)) return pfail(SPECT_EINVAL, "mu must be a 16-byte aligned device pointer");
+    if (g.n_tof_bins < 0 || g.n_tof_bins > 4096) return pfail(SPECT_EINVAL, "n_tof_bins must be in [0, 4096]");
+    if (g.n_tof_bins > 0 && (!(g.tof_bin_mm > 0.f) || !(g.tof_sigma_mm > 0.f) || !(g.tof_nsigma > 0.f)))
+        return pfail(SPECT_EINVAL, "time of flight needs tof_bin_mm, tof_sigma_mm and tof_nsigma > 0");
     pet_plan* p = new pet_plan();
     p->geom = g;
     p->rr = rr;
+    p->tof.nb = g.n_tof_bins;
+    if (g.n_tof_bins > 0) {
+        p->tof.width = g.tof_bin_mm;
+        p->tof.sigma = g.tof_sigma_mm;
+        p->tof.nsigma = g.tof_nsigma;
+        p->tof.inv_s2 = (float)(1.0 / (std::sqrt(2.0) * (double)g.tof_sigma_mm));
+    }
     const float v[3] = {g.vx, g.vy, g.vz};
     const int n[3] = {g.nx, g.ny, g.nz};
     for (int c = 0; c < 3; ++c) {
@@ -577,13 +650,14 @@ int pet_mult(pet_plan* p, const float* lors, const float* eta, int64_t n, float*
     a.vals = eta;
     a.out = mult_out;
     return launch(p, "joseph_mult", st, 1,
-                  [&] { pet_lm_kernel<kModeMult><<<blocks_for(n), kPetThreads, 0, st>>>(a); });
+                  [&] { pet_lm_kernel<kModeMult, false><<<blocks_for(n), kPetThreads, 0, st>>>(a); });
 }
 
-int pet_forward(pet_plan* p, const float* x, const float* lors, const float* mult, int64_t n, float* out,
-                void* stream)
+int pet_forward(pet_plan* p, const float* x, const float* lors, const float* mult, const int* tof_bin, int64_t n,
+                float* out, void* stream)
 {
     if (int rc = check_lors(p, lors, n)) return rc;
+    if (int rc = check_tof(p, tof_bin, n)) return rc;
     if (int rc = check_image(x, "x")) return rc;
     if (n > 0 && !out) return pfail(SPECT_EINVAL, "out is NULL");
     if (n == 0) return SPECT_OK;
@@ -599,13 +673,20 @@ int pet_forward(pet_plan* p, const float* x, const float* lors, const float* mul
     a.img = img;
     a.mult = mult;
     a.out = out;
-    return launch(p, "joseph_fwd", st, 1, [&] { pet_lm_kernel<kModeFwd><<<blocks_for(n), kPetThreads, 0, st>>>(a); });
+    a.tof_bin = tof_bin;
+    return launch(p, tof_bin ? "joseph_fwd_tof" : "joseph_fwd", st, 1, [&] {
+        if (tof_bin)
+            pet_lm_kernel<kModeFwd, true><<<blocks_for(n), kPetThreads, 0, st>>>(a);
+        else
+            pet_lm_kernel<kModeFwd, false><<<blocks_for(n), kPetThreads, 0, st>>>(a);
+    });
 }
 
-int pet_back(pet_plan* p, const float* q, const float* lors, const float* mult, int64_t n, float* x_out,
-             void* stream)
+int pet_back(pet_plan* p, const float* q, const float* lors, const float* mult, const int* tof_bin, int64_t n,
+             float* x_out, void* stream)
 {
     if (int rc = check_lors(p, lors, n)) return rc;
+    if (int rc = check_tof(p, tof_bin, n)) return rc;
     if (int rc = check_image(x_out, "x_out")) return rc;
     if (n > 0 && !q) return pfail(SPECT_EINVAL, "q is NULL");
     DevGuard guard(p->device);
@@ -619,18 +700,24 @@ int pet_back(pet_plan* p, const float* q, const float* lors, const float* mult, 
         a.bp = acc;
         a.vals = q;
         a.mult = mult;
-        if (int rc = launch(p, "joseph_back", st, 1,
-                            [&] { pet_lm_kernel<kModeBack><<<blocks_for(n), kPetThreads, 0, st>>>(a); }))
+        a.tof_bin = tof_bin;
+        if (int rc = launch(p, tof_bin ? "joseph_back_tof" : "joseph_back", st, 1, [&] {
+                if (tof_bin)
+                    pet_lm_kernel<kModeBack, true><<<blocks_for(n), kPetThreads, 0, st>>>(a);
+                else
+                    pet_lm_kernel<kModeBack, false><<<blocks_for(n), kPetThreads, 0, st>>>(a);
+            }))
             return rc;
     }
     if (p->rr) return rr_apply(p, p->bp, x_out, nullptr, st);
     return SPECT_OK;
 }
 
-int pet_lm_osem_run(pet_plan* p, const float* lors, const float* mult, const float* s, int64_t n,
-                    const float* sens, float* x, int first, int count, double* diag_out, void* stream)
+int pet_lm_osem_run(pet_plan* p, const float* lors, const float* mult, const float* s, const int* tof_bin,
+                    int64_t n, const float* sens, float* x, int first, int count, double* diag_out, void* stream)
 {
     if (int rc = check_lors(p, lors, n)) return rc;
+    if (int rc = check_tof(p, tof_bin, n)) return rc;
     if (int rc = check_image(x, "x_inout")) return rc;
     if (int rc = check_image(sens, "sens")) return rc;
     if (n > 0 && !mult) return pfail(SPECT_EINVAL, "mult is NULL");
@@ -674,8 +761,13 @@ int pet_lm_osem_run(pet_plan* p, const float* lors, const float* mult, const flo
             a.mult = mult;
             a.s = s;
             a.diag = diag_out ? p->diag + 2 * (it - first) : nullptr;
-            if (int rc = launch(p, "joseph_em", st, 1,
-                                [&] { pet_lm_kernel<kModeEm><<<blocks_for(cnt), kPetThreads, 0, st>>>(a); }))
+            a.tof_bin = tof_bin;
+            if (int rc = launch(p, tof_bin ? "joseph_em_tof" : "joseph_em", st, 1, [&] {
+                    if (tof_bin)
+                        pet_lm_kernel<kModeEm, true><<<blocks_for(cnt), kPetThreads, 0, st>>>(a);
+                    else
+                        pet_lm_kernel<kModeEm, false><<<blocks_for(cnt), kPetThreads, 0, st>>>(a);
+                }))
                 return rc;
         }
         if (p->rr) {

@@ -22,6 +22,8 @@ from dataclasses import dataclass
 import torch
 
 WATER_MU_MM = 0.0096   # 511 keV, 1/mm
+C_MM_PER_PS = 0.299792458
+FWHM_PER_SIGMA = 2.0 * math.sqrt(2.0 * math.log(2.0))
 BONE_MU_MM = 0.0172
 
 
@@ -60,10 +62,22 @@ class PetWorkload:
     n_iters: int
     fwhm_mm: float
     seed: int
+    tof_bins: int = 0          # time-of-flight bins (0: none)
+    tof_range_mm: float = 0.0  # total extent of the bins along the line
+    tof_fwhm_ps: float = 0.0   # coincidence timing resolution
 
     @property
     def rr_sigma_mm(self) -> float:
-        return self.fwhm_mm / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+        return self.fwhm_mm / FWHM_PER_SIGMA
+
+    @property
+    def tof_bin_mm(self) -> float:
+        return self.tof_range_mm / self.tof_bins if self.tof_bins else 0.0
+
+    @property
+    def tof_sigma_mm(self) -> float:
+        # a timing difference dt moves the annihilation point by c dt / 2
+        return 0.5 * C_MM_PER_PS * self.tof_fwhm_ps / FWHM_PER_SIGMA
 
 
 PET_WORKLOADS = {
@@ -71,6 +85,9 @@ PET_WORKLOADS = {
     # high-count LM OSEM; 30 M prompts
     "petlm204": PetWorkload("petlm204", (204, 204, 154), (1.25, 1.25, 1.25), Scanner(), 30_000_000, 0.1, 3, 1,
                             3.0, 11),
+    # the same with the paper's time of flight: 550 ps, 21 bins over 30 cm
+    "petlm204tof": PetWorkload("petlm204tof", (204, 204, 154), (1.25, 1.25, 1.25), Scanner(), 30_000_000, 0.1, 3, 1,
+                               3.0, 11, 21, 300.0, 550.0),
     # a small case for parity tests
     "petlm_small": PetWorkload("petlm_small", (40, 40, 28), (3.0, 3.0, 3.5),
                                Scanner(radius_mm=110.0, crystals_per_ring=96, rings=12, ring_pitch_mm=7.5),
@@ -131,9 +148,12 @@ def _ellipsoid_chord(p, d, semi):
 
 def draw_events(wl: PetWorkload, act: torch.Tensor, semi, device="cpu", chunk: int = 20_000_000):
     """Listmode events: (lors [n][6] float32 mm, eta [n] float32, s [n]
-    float32, true_count).  Prompts = trues + randoms in random order; eta is
-    the product of the two crystals' efficiencies; s is the expected number
-    of randoms on one crystal pair."""
+    float32, true_count, tof_bin [n] int32 or None).  Prompts = trues +
+    randoms in random order; eta is the product of the two crystals'
+    efficiencies; s is the expected number of randoms on one crystal pair
+    (and time-of-flight bin).  A true event's bin is its emission point's
+    arc length from the line's midpoint plus Gaussian timing noise; a
+    random's bin is uniform."""
     sc = wl.scanner
     gen = torch.Generator(device=device).manual_seed(wl.seed)
     cpu_gen = torch.Generator(device="cpu").manual_seed(wl.seed + 1)
@@ -145,7 +165,7 @@ def draw_events(wl: PetWorkload, act: torch.Tensor, semi, device="cpu", chunk: i
     shape = torch.tensor(wl.shape, device=device)
     vox = torch.tensor(wl.voxel, dtype=torch.float64, device=device)
     half = 0.5 * (shape.double() - 1.0)
-    got_a, got_b = [], []
+    got_a, got_b, got_l = [], [], []
     have = 0
     while have < n_true:
         m = min(chunk, max(4 * (n_true - have), 1024))
@@ -176,19 +196,31 @@ def draw_events(wl: PetWorkload, act: torch.Tensor, semi, device="cpu", chunk: i
         keep = (torch.rand(ca.shape[0], generator=gen, dtype=torch.float64, device=device) < eta / 1.15 ** 2) & (ca != cb)
         got_a.append(ca[keep])
         got_b.append(cb[keep])
+        if wl.tof_bins:
+            p1, p2 = sc.crystal_xyz(ca[keep]), sc.crystal_xyz(cb[keep])
+            u = (p2 - p1) / torch.linalg.norm(p2 - p1, dim=-1, keepdim=True)
+            got_l.append(((pos[ok][keep] - 0.5 * (p1 + p2)) * u).sum(-1))
         have += int(keep.sum())
     ca = torch.cat(got_a)[:n_true]
     cb = torch.cat(got_b)[:n_true]
     ra = torch.randint(0, sc.n_crystals, (n_rand,), generator=gen, device=device)
     rb = (ra + torch.randint(1, sc.n_crystals, (n_rand,), generator=gen, device=device)) % sc.n_crystals
     ca, cb = torch.cat([ca, ra]), torch.cat([cb, rb])
+    tof = None
+    if wl.tof_bins:
+        ell = torch.cat(got_l)[:n_true]
+        ell = ell + wl.tof_sigma_mm * torch.randn(n_true, generator=gen, dtype=torch.float64, device=device)
+        tb = torch.round(ell / wl.tof_bin_mm + 0.5 * (wl.tof_bins - 1)).long().clamp(0, wl.tof_bins - 1)
+        tof = torch.cat([tb, torch.randint(0, wl.tof_bins, (n_rand,), generator=gen, device=device)])
     perm = torch.randperm(ca.shape[0], generator=gen, device=device)
     ca, cb = ca[perm], cb[perm]
     lors = torch.cat([sc.crystal_xyz(ca), sc.crystal_xyz(cb)], dim=-1).float().contiguous()
     eta = (eff[ca] * eff[cb]).float().contiguous()
     pairs = sc.n_crystals * (sc.n_crystals - 1) / 2
-    s = torch.full((ca.shape[0],), n_rand / pairs, dtype=torch.float32, device=device)
-    return lors, eta, s, n_true
+    s = torch.full((ca.shape[0],), n_rand / pairs / max(wl.tof_bins, 1), dtype=torch.float32, device=device)
+    if tof is not None:
+        tof = tof[perm].int().contiguous()
+    return lors, eta, s, n_true, tof
 
 
 def _snap(sc: Scanner, pts: torch.Tensor) -> torch.Tensor:

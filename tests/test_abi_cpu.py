@@ -103,6 +103,8 @@ def test_serve_config_validation(spect_lib):
     (dict(n_subsets=0), "n_subsets"),
     (dict(rr_sigma_mm=2.0, rr_nsigma=0.0), "rr_nsigma"),
     (dict(rr_sigma_mm=40.0), "radius"),
+    (dict(n_tof_bins=-1), "n_tof_bins"),
+    (dict(n_tof_bins=5, tof_bin_mm=10.0), "time of flight"),
 ])
 def test_pet_geometry_validation(spect_lib, bad, msg):
     from paper_2309_01977_gb300 import pet
@@ -119,5 +121,5 @@ def test_pet_geometry_validation(spect_lib, bad, msg):
 def test_pet_null_plan_rejected(spect_lib):
     from paper_2309_01977_gb300 import pet
     lib = pet.load()
-    assert lib.pet_forward(None, None, None, None, 0, None, None) == spect_lib.SPECT_EINVAL
-    assert lib.pet_lm_osem_run(None, None, None, None, 0, None, None, 0, 1, None, None) == spect_lib.SPECT_EINVAL
+    assert lib.pet_forward(None, None, None, None, None, 0, None, None) == spect_lib.SPECT_EINVAL
+    assert lib.pet_lm_osem_run(None, None, None, None, None, 0, None, None, 0, 1, None, None) == spect_lib.SPECT_EINVAL

@@ -32,7 +32,7 @@ def small(pet_mods):
     pet, pp, opet = pet_mods
     wl = pp.PET_WORKLOADS["petlm_small"]
     act, mu, semi = pp.head_phantom(wl.shape, wl.voxel, wl.seed)
-    lors, eta, s, _ = pp.draw_events(wl, act, semi)
+    lors, eta, s, _, _ = pp.draw_events(wl, act, semi)
     og = opet.PetGeom(wl.shape, wl.voxel, rr_sigma_mm=np.float32(wl.rr_sigma_mm), rr_nsigma=3.0)
     return wl, act.numpy(), mu.numpy(), lors.numpy(), eta.numpy(), s.numpy(), og
 
@@ -72,7 +72,8 @@ def _t(a, dev):
 
 def _plan(pet, wl, mu, dev, rr=True, subsets=None):
     g = pet.PetGeometry(wl.shape, wl.voxel, rr_sigma_mm=wl.rr_sigma_mm if rr else 0.0,
-                        n_subsets=subsets or wl.n_subsets)
+                        n_subsets=subsets or wl.n_subsets, n_tof_bins=wl.tof_bins, tof_bin_mm=wl.tof_bin_mm,
+                        tof_sigma_mm=wl.tof_sigma_mm)
     return pet.PetPlan(g, None if mu is None else _t(mu, dev), stream=torch.cuda.current_stream())
 
 
@@ -210,7 +211,7 @@ def test_full_grid_sampled_lines_and_count_identity(pet_mods, cuda):
     pet, pp, opet = pet_mods
     wl = dataclasses.replace(pp.PET_WORKLOADS["petlm204"], prompts=3_000_000)
     act, mu, semi = pp.head_phantom(wl.shape, wl.voxel, wl.seed, device=cuda)
-    lors, eta, s, _ = pp.draw_events(wl, act, semi, device=cuda)
+    lors, eta, s, _, _ = pp.draw_events(wl, act, semi, device=cuda)
     plan = _plan(pet, wl, mu.cpu().numpy(), cuda)
     mult = plan.mult(lors, eta)
     p = plan.forward(act, lors, mult)
@@ -234,4 +235,93 @@ def test_full_grid_sampled_lines_and_count_identity(pet_mods, cuda):
     d = plan.lm_osem(lors, mult, s, sens, x, 0, 1, diag=True)[0]
     lhs = float((sens.double() / wl.n_subsets * x.double())[sens > 0].sum())
     assert abs(lhs - d[0]) <= 1e-4 * d[0]
+    plan.close()
+
+
+# ---------------------------------------------------------------- time of flight
+
+@pytest.fixture(scope="module")
+def small_tof(pet_mods):
+    """The small case with time of flight: 15 bins over 240 mm, 250 ps."""
+    pet, pp, opet = pet_mods
+    wl = dataclasses.replace(pp.PET_WORKLOADS["petlm_small"], tof_bins=15, tof_range_mm=240.0, tof_fwhm_ps=250.0)
+    act, mu, semi = pp.head_phantom(wl.shape, wl.voxel, wl.seed)
+    lors, eta, s, _, tb = pp.draw_events(wl, act, semi)
+    og = opet.PetGeom(wl.shape, wl.voxel, rr_sigma_mm=np.float32(wl.rr_sigma_mm), rr_nsigma=3.0)
+    return wl, act.numpy(), mu.numpy(), lors.numpy(), eta.numpy(), s.numpy(), tb.numpy(), og
+
+
+def _otof(opet, wl, bins):
+    # the library holds the model in single precision; the oracle gets the same values
+    return opet.Tof(n_bins=wl.tof_bins, bin_mm=float(np.float32(wl.tof_bin_mm)),
+                    sigma_mm=float(np.float32(wl.tof_sigma_mm)), bins=bins, nsigma=3.0)
+
+
+def _ti(a, dev):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.int32))).to(dev)
+
+
+def test_tof_forward_and_back_match_oracle(pet_mods, small_tof, cuda):
+    pet, pp, opet = pet_mods
+    wl, act, mu, lors, eta, s, tb, og = small_tof
+    L, B = lors[:8000], tb[:8000]
+    rng = np.random.Generator(np.random.PCG64(30))
+    x = (act + rng.uniform(0, 0.5, size=act.shape)).astype(np.float32)
+    m = rng.uniform(0.5, 1.0, size=len(L)).astype(np.float32)
+    plan = _plan(pet, wl, mu, cuda)
+    got = plan.forward(_t(x, cuda), _t(L, cuda), _t(m, cuda), tof_bin=_ti(B, cuda)).cpu().numpy()
+    ref = opet.forward(x, L, og, m, tof=_otof(opet, wl, B))
+    err = rel_l2(got, ref)
+    print("PET TOF forward rel L2 vs FP64: %.2e" % err)
+    assert err <= 1e-5
+    q = rng.uniform(0.0, 2.0, size=len(L)).astype(np.float32)
+    gb = plan.back(_t(q, cuda), _t(L, cuda), _t(m, cuda), tof_bin=_ti(B, cuda)).cpu().numpy()
+    rb = opet.back(q, L, og, m, tof=_otof(opet, wl, B))
+    errb = rel_l2(gb, rb)
+    print("PET TOF back rel L2 vs FP64: %.2e" % errb)
+    assert errb <= 1e-5
+    lhs = float(np.dot(got.astype(np.float64), q))
+    rhs = float(np.sum(x.astype(np.float64) * gb))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+    plan.close()
+
+
+def test_tof_lm_osem_matches_oracle(pet_mods, small_tof, cuda):
+    pet, pp, opet = pet_mods
+    wl, act, mu, lors, eta, s, tb, og = small_tof
+    sens, mult = _osem_inputs(pet, pp, opet, wl, mu, lors, eta, og)
+    M, n_sub = wl.n_subsets, wl.n_subsets * wl.n_iters
+    ref, rdiag = opet.lm_osem(lors, mult, s, sens, og, M, count=n_sub, tof=_otof(opet, wl, tb))
+    plan = _plan(pet, wl, mu, cuda)
+    x = torch.ones(wl.shape, device=cuda)
+    diag = plan.lm_osem(_t(lors, cuda), _t(mult, cuda), _t(s, cuda), _t(sens, cuda), x, 0, n_sub, diag=True,
+                        tof_bin=_ti(tb, cuda))
+    err = rel_l2(x.cpu().numpy(), ref)
+    print("PET TOF listmode OSEM %dx%d image rel L2 vs FP64: %.2e" % (wl.n_iters, M, err))
+    assert err <= 2e-5
+    for k in range(n_sub):
+        assert diag[k][1] == rdiag[k][1]
+        assert abs(diag[k][0] - rdiag[k][0]) <= 2e-5 * rdiag[k][0]
+    plan.close()
+
+
+def test_tof_full_grid_sampled_lines(pet_mods, cuda):
+    """The paper's TOF model (550 ps, 21 bins over 30 cm) on the 204^3 grid,
+    3 M prompts: 2000 sampled lines match the oracle one by one."""
+    pet, pp, opet = pet_mods
+    wl = dataclasses.replace(pp.PET_WORKLOADS["petlm204tof"], prompts=3_000_000)
+    act, mu, semi = pp.head_phantom(wl.shape, wl.voxel, wl.seed, device=cuda)
+    lors, eta, s, _, tb = pp.draw_events(wl, act, semi, device=cuda)
+    plan = _plan(pet, wl, mu.cpu().numpy(), cuda)
+    mult = plan.mult(lors, eta)
+    p = plan.forward(act, lors, mult, tof_bin=tb)
+    rng = np.random.Generator(np.random.PCG64(31))
+    pick = np.sort(rng.choice(lors.shape[0], 2000, replace=False))
+    og = opet.PetGeom(wl.shape, wl.voxel, rr_sigma_mm=np.float32(wl.rr_sigma_mm), rr_nsigma=3.0)
+    ref = opet.forward(act.cpu().numpy(), lors.cpu().numpy()[pick], og, mult.cpu().numpy()[pick],
+                       tof=_otof(opet, wl, tb.cpu().numpy()[pick]))
+    got = p.cpu().numpy()[pick]
+    err = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-3 * np.max(np.abs(ref)))
+    print("PET TOF 204^3-grid sampled lines: max rel err %.2e" % float(err.max()))
+    assert float(err.max()) <= 1e-5
     plan.close()
