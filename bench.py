@@ -502,12 +502,14 @@ def run_pet_leg(torch, dev, timed, max_over_ranks, world, k, cpu_seconds: float,
     l2 = os.path.join(ROOT, "profiles", "l2_petlm204.json")
     if os.path.exists(l2):
         with open(l2) as fh:
-            prof_l2 = json.load(fh).get("joseph_em")
+            prof_l2 = json.load(fh).get(em_name)
         # the walk gathers from and scatters into an image held in L2: its
         # bound is L2 throughput, measured by ncu as a fraction of L2 peak
-        if prof_l2 and tof_bin is None:
-            leg["roofline"] = {"bound": "l2", "kernel": "joseph_em", "frac": prof_l2["lts_throughput_frac"],
-                               "source": "ncu lts__throughput of the same kernel (profiles/pet_lm_em_petlm204.md)"}
+        # (with time of flight the erf weights also keep the issue slots busy)
+        if prof_l2:
+            leg["roofline"] = {"bound": "l2", "kernel": em_name, "frac": prof_l2["lts_throughput_frac"],
+                               "issue_active_frac": prof_l2["issue_active_frac"],
+                               "source": "ncu of the same kernel at 3 M prompts (profiles/pet_lm_em_petlm204.md)"}
     if with_cpu:
         leg["cpu_baseline"] = pet_cpu_baseline(wl, act, mu, lors, mult, s, sens, cpu_seconds, tof_bin)
     plan.close()
@@ -699,12 +701,6 @@ def run_libspect(args):
     if not args.no_multipeak:
         legs["multipeak"] = run_multipeak_leg(spect, torch, dev, wl, g, plan, f_raw, mu, y_dev, s, x, timed,
                                               max_over_ranks, world, max(2, args.steps // 2))
-    if not args.no_pet:
-        with_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
-        legs["pet"] = run_pet_leg(torch, dev, timed, max_over_ranks, world, max(2, args.steps // 8),
-                                  args.cpu_seconds / 2, with_cpu, workload="petlm204tof")
-        legs["pet_nontof"] = run_pet_leg(torch, dev, timed, max_over_ranks, world, max(2, args.steps // 8),
-                                         args.cpu_seconds / 2, False, workload="petlm204")
     if not args.no_orbit:
         legs["orbit"] = run_orbit_leg(spect, torch, dev, wl, g, f_raw, mu, x, timed, max_over_ranks, world,
                                       max(2, args.steps // 2))
@@ -716,6 +712,16 @@ def run_libspect(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, y, s, mu.astype(np.float64), args.cpu_seconds)
+
+    # listmode PET last: its event lists are the largest allocations of the run
+    if not args.no_pet:
+        with_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+        legs["pet"] = run_pet_leg(torch, dev, timed, max_over_ranks, world, max(2, args.steps // 8),
+                                  args.cpu_seconds / 2, with_cpu, workload="petlm204tof")
+        torch.cuda.empty_cache()
+        legs["pet_nontof"] = run_pet_leg(torch, dev, timed, max_over_ranks, world, max(2, args.steps // 8),
+                                         args.cpu_seconds / 2, False, workload="petlm204")
+        torch.cuda.empty_cache()
 
     if rank == 0:
         cfg = workload_desc(wl)
