@@ -245,9 +245,20 @@ def cpu_baseline(wl, y, s, mu64, seconds: float, steps=None):
                 break
         elif el >= seconds:
             break
-    return {"value": done / el, "unit": UNIT, "cores": oracle.n_threads(), "kind": "oracle",
-            "sample": "first %d subiteration(s) of the %dx%d OSEM on %s (FP64, %.1f s)" % (
-                done, wl.n_iters, wl.n_subsets, wl.name, el)}
+    out = {"value": done / el, "unit": UNIT, "cores": oracle.n_threads(), "kind": "oracle",
+           "sample": "first %d subiteration(s) of the %dx%d OSEM on %s (FP64, %.1f s)" % (
+               done, wl.n_iters, wl.n_subsets, wl.name, el)}
+    if steps is None:
+        # the same oracle on one thread: one subiteration
+        threads = oracle.n_threads()
+        oracle.set_threads(1)
+        try:
+            t1 = time.perf_counter()
+            oracle.osem(y, s, og, wl.n_subsets, 0, 1, np.ones((wl.n, wl.n, wl.nz)))
+            out["one_thread_value"] = 1.0 / (time.perf_counter() - t1)
+        finally:
+            oracle.set_threads(threads)
+    return out
 
 
 def make_inputs_host(wl):
