@@ -62,8 +62,18 @@ struct Walk {
 struct TofParams {
     int nb;             // bins (0: no time of flight)
     float width, sigma, nsigma;
-    float inv_s2;       // 1 / (sqrt(2) sigma)
+    float half_win;     // nsigma sigma + width / 2: the table covers [-half_win, half_win]
+    float inv_h;        // table entries per mm
 };
+
+// The bin-integrated timing weight as a function of the distance x from the
+// bin centre, tabulated at kTofTab + 1 points over [-half_win, half_win] and
+// read with linear interpolation: the step is (2 nsigma + width / sigma)
+// sigma / kTofTab, and the error (interpolation plus single-precision
+// entries) stays near 4e-7 of the peak weight for bin widths of 0.5 to 2
+// sigma.
+constexpr int kTofTab = 4096;
+constexpr size_t kTofSmem = (kTofTab + 1) * sizeof(float);
 
 // Element i of a three-element array with constant indices only, so that
 // the array stays in registers.
@@ -161,16 +171,20 @@ __device__ __forceinline__ bool walk_setup(const float* __restrict__ lor, const 
 // b axis at a time: fn(idx, ok0, ok1, w0, w1) for the taps idx (along c at
 // iw) and idx + stride_c (at iw + 1), each present only where ok.
 template <bool kTof, class F>
-__device__ __forceinline__ void walk(const Walk& k, const PetGrid& g, const TofParams& tp, float cb, F&& fn)
+__device__ __forceinline__ void walk(const Walk& k, const PetGrid& g, const TofParams& tp, float cb,
+                                     const float* tof_tab, F&& fn)
 {
     const long long sa = sel3(g.stride, k.a), sb = sel3(g.stride, k.b), sc = sel3(g.stride, k.c);
     const int nb = sel3(g.n, k.b), nc = sel3(g.n, k.c);
-    const float hw = 0.5f * tp.width;
     for (int i = k.i0; i <= k.i1; ++i) {
         float wt = 1.f;
         if (kTof) {
-            const float l = fmaf((float)i, k.dl, k.l0) - cb;
-            wt = 0.5f * (erff((l + hw) * tp.inv_s2) - erff((l - hw) * tp.inv_s2));
+            const float x = (fmaf((float)i, k.dl, k.l0) - cb + tp.half_win) * tp.inv_h;
+            const float xc = fminf(fmaxf(x, 0.f), (float)kTofTab);
+            const int j = min((int)xc, kTofTab - 1);
+            const float fr = xc - (float)j;
+            const float t0 = tof_tab[j], t1 = tof_tab[j + 1];
+            wt = fmaf(fr, t1 - t0, t0);
         }
         const float u = fmaf((float)i, k.du, k.u0);
         const float w = fmaf((float)i, k.dw, k.w0);
@@ -235,6 +249,7 @@ struct LmArgs {
     float* out;           // kModeFwd / kModeMult: [n]
     double* diag;         // kModeEm: 2 doubles (sum p/(p+s), events used) or nullptr
     const int* tof_bin;   // [n] time-of-flight bins (kTof kernels)
+    const float* tof_tab; // [kTofTab + 1] timing weights (kTof kernels)
     long long first, stride, count;  // events first + t * stride, t < count
     PetGrid g;
     TofParams tof;
@@ -268,6 +283,11 @@ __device__ __forceinline__ void block_add2(double a, double b, double* dst)
 template <int kMode, bool kTof>
 __global__ void __launch_bounds__(kPetThreads) pet_lm_kernel(LmArgs a)
 {
+    extern __shared__ float tof_s[];  // kTof: the timing-weight table
+    if (kTof) {
+        for (int i = threadIdx.x; i <= kTofTab; i += blockDim.x) tof_s[i] = __ldg(a.tof_tab + i);
+        __syncthreads();
+    }
     double cons = 0.0, used = 0.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < a.count;
          t += (long long)gridDim.x * blockDim.x) {
@@ -280,7 +300,7 @@ __global__ void __launch_bounds__(kPetThreads) pet_lm_kernel(LmArgs a)
             if (!hit || val == 0.f) continue;
             const float sv = val * k.step;
             const long long sc = sel3(a.g.stride, k.c);
-            walk<kTof>(k, a.g, a.tof, cb, [&](long long idx, bool o0, bool o1, float w0, float w1) {
+            walk<kTof>(k, a.g, a.tof, cb, tof_s, [&](long long idx, bool o0, bool o1, float w0, float w1) {
                 scatter_pair(a.bp, idx, sc, a.g.total, o0, o1, sv * w0, sv * w1);
             });
             continue;
@@ -288,7 +308,7 @@ __global__ void __launch_bounds__(kPetThreads) pet_lm_kernel(LmArgs a)
         float acc = 0.f;
         if (hit && (kMode != kModeMult || a.img != nullptr)) {
             const long long sc = sel3(a.g.stride, k.c);
-            walk<kTof>(k, a.g, a.tof, cb, [&](long long idx, bool o0, bool o1, float w0, float w1) {
+            walk<kTof>(k, a.g, a.tof, cb, tof_s, [&](long long idx, bool o0, bool o1, float w0, float w1) {
                 acc += gather_pair(a.img, idx, sc, a.g.total, o0, o1, w0, w1);
             });
         }
@@ -308,7 +328,7 @@ __global__ void __launch_bounds__(kPetThreads) pet_lm_kernel(LmArgs a)
             const float sv = m / den * k.step;
             if (hit) {
                 const long long sc = sel3(a.g.stride, k.c);
-                walk<kTof>(k, a.g, a.tof, cb, [&](long long idx, bool o0, bool o1, float w0, float w1) {
+                walk<kTof>(k, a.g, a.tof, cb, tof_s, [&](long long idx, bool o0, bool o1, float w0, float w1) {
                     scatter_pair(a.bp, idx, sc, a.g.total, o0, o1, sv * w0, sv * w1);
                 });
             }
@@ -409,6 +429,7 @@ struct pet_plan {
     TofParams tof{};
     long long voxels = 0;
     float* mu = nullptr;
+    float* tof_tab = nullptr;  // [kTofTab + 1] timing weights
     float* t1 = nullptr;
     float* t2 = nullptr;
     float* fb = nullptr;
@@ -505,6 +526,7 @@ LmArgs base_args(const pet_plan* p, const float* lors, long long n)
     a.count = n;
     a.g = p->grid;
     a.tof = p->tof;
+    a.tof_tab = p->tof_tab;
     return a;
 }
 
@@ -553,11 +575,21 @@ int pet_plan_create(const pet_geom* geom, const float* mu_dev, void* stream, pet
     p->geom = g;
     p->rr = rr;
     p->tof.nb = g.n_tof_bins;
+    std::vector<float> tof_tab;
     if (g.n_tof_bins > 0) {
         p->tof.width = g.tof_bin_mm;
         p->tof.sigma = g.tof_sigma_mm;
         p->tof.nsigma = g.tof_nsigma;
-        p->tof.inv_s2 = (float)(1.0 / (std::sqrt(2.0) * (double)g.tof_sigma_mm));
+        const double hw = (double)g.tof_nsigma * g.tof_sigma_mm + 0.5 * (double)g.tof_bin_mm;
+        p->tof.half_win = (float)hw;
+        p->tof.inv_h = (float)(kTofTab / (2.0 * hw));
+        tof_tab.resize(kTofTab + 1);
+        const double s2 = std::sqrt(2.0) * (double)g.tof_sigma_mm, h = 0.5 * (double)g.tof_bin_mm;
+        for (int i = 0; i <= kTofTab; ++i) {
+            // Phi((x + h)/sigma) - Phi((x - h)/sigma) with Phi(t) = erfc(-t/sqrt 2) / 2
+            const double x = -hw + 2.0 * hw * i / kTofTab;
+            tof_tab[i] = (float)(0.5 * (std::erfc(-(x + h) / s2) - std::erfc(-(x - h) / s2)));
+        }
     }
     const float v[3] = {g.vx, g.vy, g.vz};
     const int n[3] = {g.nx, g.ny, g.nz};
@@ -606,6 +638,14 @@ int pet_plan_create(const pet_geom* geom, const float* mu_dev, void* stream, pet
     if (!rc) {
         p->diag_cap = 64;
         rc = palloc(p, &p->diag, 2 * (size_t)p->diag_cap);
+    }
+    if (!rc && !tof_tab.empty()) {
+        rc = palloc(p, &p->tof_tab, tof_tab.size());
+        if (!rc) {
+            cudaError_t e = cudaMemcpy(p->tof_tab, tof_tab.data(), tof_tab.size() * sizeof(float),
+                                       cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) rc = pcuda(e, "copy of the timing table");
+        }
     }
     if (!rc && mu_dev) {
         rc = palloc(p, &p->mu, nv);
@@ -676,7 +716,7 @@ int pet_forward(pet_plan* p, const float* x, const float* lors, const float* mul
     a.tof_bin = tof_bin;
     return launch(p, tof_bin ? "joseph_fwd_tof" : "joseph_fwd", st, 1, [&] {
         if (tof_bin)
-            pet_lm_kernel<kModeFwd, true><<<blocks_for(n), kPetThreads, 0, st>>>(a);
+            pet_lm_kernel<kModeFwd, true><<<blocks_for(n), kPetThreads, kTofSmem, st>>>(a);
         else
             pet_lm_kernel<kModeFwd, false><<<blocks_for(n), kPetThreads, 0, st>>>(a);
     });
@@ -703,7 +743,7 @@ int pet_back(pet_plan* p, const float* q, const float* lors, const float* mult, 
         a.tof_bin = tof_bin;
         if (int rc = launch(p, tof_bin ? "joseph_back_tof" : "joseph_back", st, 1, [&] {
                 if (tof_bin)
-                    pet_lm_kernel<kModeBack, true><<<blocks_for(n), kPetThreads, 0, st>>>(a);
+                    pet_lm_kernel<kModeBack, true><<<blocks_for(n), kPetThreads, kTofSmem, st>>>(a);
                 else
                     pet_lm_kernel<kModeBack, false><<<blocks_for(n), kPetThreads, 0, st>>>(a);
             }))
@@ -764,7 +804,7 @@ int pet_lm_osem_run(pet_plan* p, const float* lors, const float* mult, const flo
             a.tof_bin = tof_bin;
             if (int rc = launch(p, tof_bin ? "joseph_em_tof" : "joseph_em", st, 1, [&] {
                     if (tof_bin)
-                        pet_lm_kernel<kModeEm, true><<<blocks_for(cnt), kPetThreads, 0, st>>>(a);
+                        pet_lm_kernel<kModeEm, true><<<blocks_for(cnt), kPetThreads, kTofSmem, st>>>(a);
                     else
                         pet_lm_kernel<kModeEm, false><<<blocks_for(cnt), kPetThreads, 0, st>>>(a);
                 }))
