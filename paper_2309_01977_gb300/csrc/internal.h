@@ -92,7 +92,6 @@ struct BlurBackArgs {
     int chunks;            // depth chunks: contiguous plane ranges of equal work
     PlaneTiling t;
     float* bvol;           // [batch][n_sel][n][n][nz] rotated-frame volumes A . (K_i r)
-    int accumulate;        // add to bvol instead of storing (several photopeaks share one gather)
     int* err;              // SPECT_ETIMEDOUT when a bounded wait runs out
 };
 

@@ -549,13 +549,7 @@ __device__ __forceinline__ bool back_blur_plane(const float4* P, float4* Q, cons
                     const int j = js * kStrip + r;
                     if (j < n) {
                         const float2 av = *reinterpret_cast<const float2*>(As + (size_t)j * KT + kk);
-                        float2* dst = reinterpret_cast<float2*>(brow + (size_t)j * nz + k);
-                        float2 v = make_float2(o[r].x * av.x, o[r].y * av.y);
-                        if (a.accumulate) {
-                            const float2 old = *dst;
-                            v = make_float2(old.x + v.x, old.y + v.y);
-                        }
-                        *dst = v;
+                        *reinterpret_cast<float2*>(brow + (size_t)j * nz + k) = make_float2(o[r].x * av.x, o[r].y * av.y);
                     }
                 }
             } else {
@@ -570,15 +564,9 @@ __device__ __forceinline__ bool back_blur_plane(const float4* P, float4* Q, cons
 #pragma unroll
                 for (int r = 0; r < kStrip; ++r) {
                     const int j = js * kStrip + r;
-                    if (j < n) {
-                        float2* dst = reinterpret_cast<float2*>(brow + (size_t)j * nz + k);
-                        float2 v = make_float2(o[r].x * aw[r].x, o[r].y * aw[r].y);
-                        if (a.accumulate) {
-                            const float2 old = *dst;
-                            v = make_float2(old.x + v.x, old.y + v.y);
-                        }
-                        *dst = v;
-                    }
+                    if (j < n)
+                        *reinterpret_cast<float2*>(brow + (size_t)j * nz + k) =
+                            make_float2(o[r].x * aw[r].x, o[r].y * aw[r].y);
                 }
             }
         }

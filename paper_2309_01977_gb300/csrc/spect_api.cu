@@ -318,13 +318,8 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
 
 // x_out (per batch entry) = sum over sel of H_a^T proj_a, optionally fused with
 // the OSEM update x_out <- x_out * bp / sens (then batch must be 1).
-// H^T of the selected angles into x_out (or the update of x_out when upd is
-// set).  `extra` photopeak plans (FP32, same geometry) add their back-blurred
-// planes, from their projections extra_proj, to p's before the one gather:
-// the adjoint rotation is linear, so the peaks share it.
 int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev, int n_sel, int batch,
-             const UpdateSpec* upd, cudaStream_t st, bool accumulate = false, spect_plan* const* extra = nullptr,
-             const float* const* extra_proj = nullptr, int n_extra = 0)
+             const UpdateSpec* upd, cudaStream_t st, bool accumulate = false)
 {
     const size_t vol = vol_elems(p), plane = plane_elems(p);
     const int gmax = (int)std::min<size_t>(16, p->bvol_cap);
@@ -358,33 +353,26 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
                 bb.err = p->d_err;
                 e = timed(p, "blur_back_bf16", st, 1, [&] { return launch_blur_back_bf16(bb, st); });
             } else {
-                for (int q = 0; q <= n_extra; ++q) {
-                    spect_plan* pq = q == 0 ? p : extra[q - 1];
-                    const float* prq = q == 0 ? proj : extra_proj[q - 1];
-                    BlurBackArgs bb{};
-                    bb.proj = prq ? prq + ((size_t)b0 * n_sel + g0) * plane : nullptr;
-                    bb.proj_bstride = (size_t)n_sel * plane;
-                    bb.atten = pq->d_atten;
-                    bb.taps = pq->d_taps;
-                    bb.rad = pq->d_rad;
-                    bb.work = pq->d_rad + 2 * pq->n + 1;  // blur_back work prefix
-                    bb.taps_stride = pq->psf_tables > 1 ? (size_t)pq->n * kTapW : 0;
-                    bb.rad_stride = pq->psf_tables > 1 ? 3 * pq->n + 2 : 0;
-                    bb.sel = sel_dev + g0;
-                    bb.n = pq->n;
-                    bb.nz = pq->nz;
-                    bb.n_sel = ng;
-                    bb.batch = nb;
-                    bb.t = pq->tiling;
-                    const int chunks = chunk_target(pq, (long)nb * ng * pq->tiling.ntiles);
-                    bb.chunks = chunks;
-                    bb.bvol = p->d_bvol;
-                    bb.accumulate = q > 0;
-                    bb.err = pq->d_err;
-                    e = timed(p, "blur_back", st, 1,
-                              [&] { return launch_blur_back(bb, chunks * pq->tiling.ntiles, st); });
-                    if (e != cudaSuccess) break;
-                }
+                BlurBackArgs bb{};
+                bb.proj = proj ? proj + ((size_t)b0 * n_sel + g0) * plane : nullptr;
+                bb.proj_bstride = (size_t)n_sel * plane;
+                bb.atten = p->d_atten;
+                bb.taps = p->d_taps;
+                bb.rad = p->d_rad;
+                bb.work = p->d_rad + 2 * p->n + 1;  // blur_back work prefix
+                bb.taps_stride = p->psf_tables > 1 ? (size_t)p->n * kTapW : 0;
+                bb.rad_stride = p->psf_tables > 1 ? 3 * p->n + 2 : 0;
+                bb.sel = sel_dev + g0;
+                bb.n = p->n;
+                bb.nz = p->nz;
+                bb.n_sel = ng;
+                bb.batch = nb;
+                bb.t = p->tiling;
+                const int chunks = chunk_target(p, (long)nb * ng * p->tiling.ntiles);
+                bb.chunks = chunks;
+                bb.bvol = p->d_bvol;
+                bb.err = p->d_err;
+                e = timed(p, "blur_back", st, 1, [&] { return launch_blur_back(bb, chunks * p->tiling.ntiles, st); });
             }
             if (e != cudaSuccess) return cuda_fail(e, "blur_back kernel launch");
             if (p->gather_tiled) {
@@ -576,10 +564,6 @@ int multi_core(spect_plan* const* plans, const float* scales, int P, const float
     const size_t vol = vol_elems(p0);
     int rc;
     if (!p0->d_msens && ((rc = dev_alloc(p0, &p0->d_msens, vol)))) return rc;
-    // FP32 peaks share the adjoint rotation: their back-blurred planes add up
-    // in plans[0]'s buffer before one gather
-    bool share = P > 1;
-    for (int n = 0; n < P; ++n) share = share && !plans[n]->bf16;
     for (int t = first; t < first + count; ++t) {
         const int m = t % p0->M;
         const int ns = (int)p0->subsets[m].size();
@@ -592,16 +576,6 @@ int multi_core(spect_plan* const* plans, const float* scales, int P, const float
         }
         cudaError_t e = timed(p0, "sens_sum", st, 1, [&] { return launch_wsum(p0->d_msens, sens, scales, P, vol, st); });
         if (e != cudaSuccess) return cuda_fail(e, "weighted sum kernel");
-        if (share) {
-            UpdateSpec u{};
-            u.mode = kUpdOsem;
-            u.sens = p0->d_msens;
-            const float* eproj[kMaxPeaks];
-            for (int n = 1; n < P; ++n) eproj[n - 1] = plans[n]->d_ratio;
-            rc = run_back(p0, p0->d_ratio, x, p0->d_sel[m], ns, 1, &u, st, false, plans + 1, eproj, P - 1);
-            if (rc) return rc;
-            continue;
-        }
         for (int n = 0; n + 1 < P; ++n) {
             rc = run_back(plans[n], plans[n]->d_ratio, p0->d_bp, plans[n]->d_sel[m], ns, 1, nullptr, st, n > 0);
             if (rc) return rc;
