@@ -63,6 +63,7 @@ def parse_args():
     ap.add_argument("--no-multipeak", action="store_true", help="skip the two-photopeak OSEM leg")
     ap.add_argument("--no-orbit", action="store_true", help="skip the non-circular orbit OSEM leg")
     ap.add_argument("--no-pet", action="store_true", help="skip the listmode PET leg")
+    ap.add_argument("--no-autograd", action="store_true", help="skip the batch-of-4 192^3 gradient leg")
     ap.add_argument("--pet-only", action="store_true",
                     help="run only the listmode PET leg (one GPU) and print it as one JSON line")
     ap.add_argument("--pet-prompts", type=int, default=None, help="prompts of the PET leg (default 30 M)")
@@ -573,6 +574,45 @@ def pet_cpu_baseline(wl, act, mu, lors, mult, s, sens, seconds, tof_bin=None):
             "sample": "one listmode subiteration over %d events of %s (FP64, %.1f s)" % (n // M, wl.name, el)}
 
 
+def run_autograd_leg(spect, torch, dev, timed, max_over_ranks, world, k):
+    """The differentiable projector on the grad192 workload (batch of 4
+    volumes of 192^3, 128 angles, 192 x 192 bins): one step is the Poisson
+    log-likelihood of the batch and its gradient through torch.autograd
+    (H x of all angles, L and dL/dp, H^T of all angles)."""
+    from paper_2309_01977_gb300 import autograd, phantom
+    wl = phantom.WORKLOADS["grad192"]
+    f_raw, mu = phantom.make_phantom(wl.n, wl.nz, wl.seed)
+    g = spect.Geometry(n=wl.n, nz=wl.nz, n_angles=wl.n_angles, n_subsets=1, voxel_cm=wl.voxel_cm,
+                       psf_sigma0=wl.sigma0, psf_slope=wl.slope, psf_nsigma=wl.nsigma)
+    plan = spect.Plan(g, torch.from_numpy(mu.astype(np.float32)).to(dev))
+    batch = 4
+    rng = np.random.Generator(np.random.PCG64(wl.seed))
+    f0 = torch.from_numpy(f_raw.astype(np.float32)).to(dev)
+    scales = torch.from_numpy(rng.uniform(0.5, 1.5, size=(batch, 1, 1, 1)).astype(np.float32)).to(dev)
+    x = (f0[None] * scales).contiguous().requires_grad_(True)
+    with torch.no_grad():
+        p = autograd.SpectProjector.apply(x, plan, -1)
+        counts = torch.poisson(p + 1.0).contiguous()
+    s = 1.0
+
+    def step():
+        x.grad = None
+        autograd.poisson_loss(x, counts, s, plan).backward()
+    step()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(timed(step, k))
+    spect.spect_profile_enable(plan.handle, True)
+    spect.spect_profile_read(plan.handle, reset=True)
+    timed(step, k)
+    prof = spect.spect_profile_read(plan.handle, reset=True)
+    spect.spect_profile_enable(plan.handle, False)
+    plan.close()
+    return {"workload": "grad192: batch 4 x 192^3 (0.48 cm), 128 angles, 192 x 192 bins, attenuation + PSF",
+            "step": "Poisson log-likelihood of the batch and its gradient through torch.autograd",
+            "gradients_per_s": replica_throughput(world, k, batch, ms), "ms_per_step": ms / k,
+            "kernel_avg_us": {kk: round(1e3 * v[1] / v[0], 1) for kk, v in prof.items()}}
+
+
 def run_libspect(args):
     import torch
     import torch.distributed as dist
@@ -712,6 +752,9 @@ def run_libspect(args):
     if not args.no_multipeak:
         legs["multipeak"] = run_multipeak_leg(spect, torch, dev, wl, g, plan, f_raw, mu, y_dev, s, x, timed,
                                               max_over_ranks, world, max(2, args.steps // 2))
+    if not args.no_autograd:
+        legs["autograd"] = run_autograd_leg(spect, torch, dev, timed, max_over_ranks, world, max(2, args.steps // 8))
+        torch.cuda.empty_cache()
     if not args.no_orbit:
         legs["orbit"] = run_orbit_leg(spect, torch, dev, wl, g, f_raw, mu, x, timed, max_over_ranks, world,
                                       max(2, args.steps // 2))
