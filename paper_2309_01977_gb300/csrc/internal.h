@@ -20,6 +20,14 @@ constexpr int kFwdThreads = 512;     // most threads of the forward / blur kerne
 constexpr int kMaxCand = 9;          // rotated-grid samples that can touch one voxel
 constexpr int kMaxIpt = 4;           // largest j-blur strips per thread
 constexpr int kTcTile = 128 * 128;   // BF16 Toeplitz tile, elements
+// Depth-chunk boundaries precomputed for 1..kBoundChunks chunks per angle
+// (more chunks: split on the device); chunks c start at bound_offset(c).
+constexpr int kBoundChunks = 64;
+constexpr int kBoundInts = kBoundChunks * (kBoundChunks + 1) / 2 + kBoundChunks;
+__host__ __device__ constexpr int bound_offset(int c) { return (c - 1) * (c + 2) / 2; }
+// Per PSF table ints: radii [n], forward and back work prefixes [n + 1]
+// each, forward and back chunk boundaries [kBoundInts] each.
+__host__ __device__ constexpr int psf_int_stride(int n) { return 3 * n + 2 + 2 * kBoundInts; }
 
 
 // Shape of one plane-blur launch: which columns of z a CTA owns and the
@@ -51,6 +59,7 @@ struct ForwardArgs {
     const float* taps;     // [n][kTapW] centred at kMaxR
     const int* rad;        // [n]
     const int* work;       // [n+1] prefix sums of the per-plane work estimate
+    const int* bounds;     // [kBoundInts] depth-chunk boundaries (see bound_offset)
     size_t taps_stride;    // floats between the angles' tap tables (0: one table)
     int rad_stride;        // ints between the angles' radius / work tables (0: one table)
     const int* sel;        // [n_sel] angle ids
@@ -85,6 +94,7 @@ struct BlurBackArgs {
     const float* taps;
     const int* rad;
     const int* work;       // [n+1] prefix sums of the per-plane work estimate
+    const int* bounds;     // [kBoundInts] depth-chunk boundaries (see bound_offset)
     size_t taps_stride;    // as ForwardArgs
     int rad_stride;
     const int* sel;        // [n_sel] angle ids

@@ -219,6 +219,20 @@ __device__ __forceinline__ void chunk_range(const int* __restrict__ work, int n,
     }
 }
 
+// The plane range of depth chunk `chunk`: from the host's boundary table
+// (the contiguous split whose heaviest chunk is lightest) when it covers
+// this chunk count, else chunk_range.  Every thread of the CTA must call it.
+__device__ __forceinline__ void chunk_planes(const int* __restrict__ bounds, const int* __restrict__ work, int n,
+                                             int chunks, int chunk, int& lo, int& hi)
+{
+    if (bounds && chunks <= kBoundChunks) {
+        lo = __ldg(bounds + bound_offset(chunks) + chunk);
+        hi = __ldg(bounds + bound_offset(chunks) + chunk + 1);
+        return;
+    }
+    chunk_range(work, n, chunks, chunk, lo, hi);
+}
+
 #define SPECT_R_CASES(M) \
     M(0) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16) M(17) M(18) M(19) M(20)
 
@@ -399,6 +413,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) forward_kernel(ForwardArgs a)
     const float* taps_g = a.taps + (size_t)angle * a.taps_stride;
     const int* rad_g = a.rad + (size_t)angle * a.rad_stride;
     const int* work_g = a.work + (size_t)angle * a.rad_stride;
+    const int* bounds_g = a.bounds ? a.bounds + (size_t)angle * a.rad_stride : nullptr;
     const float2 cs = a.cs[angle];
     const float c = 0.5f * (float)(n - 1);
     const int kt0 = tile * t.ktile;
@@ -433,7 +448,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) forward_kernel(ForwardArgs a)
 
     const float* xb = a.x + (size_t)b * n * n * nz;
     int i_lo, i_hi;
-    chunk_range(work_g, n, a.chunks, chunk, i_lo, i_hi);
+    chunk_planes(bounds_g, work_g, n, a.chunks, chunk, i_lo, i_hi);
     TapPrefetch tp;
     if (i_lo < i_hi) {
         tp.load(taps_g, i_lo);
@@ -592,6 +607,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) blur_back_kernel(BlurBackArgs 
     const float* taps_g = a.taps + (size_t)angle * a.taps_stride;
     const int* rad_g = a.rad + (size_t)angle * a.rad_stride;
     const int* work_g = a.work + (size_t)angle * a.rad_stride;
+    const int* bounds_g = a.bounds ? a.bounds + (size_t)angle * a.rad_stride : nullptr;
     const int kt0 = tile * t.ktile;
     const int KT = min(t.ktile, nz - kt0);
     const int kw0 = kt0 - t.rh;
@@ -639,7 +655,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) blur_back_kernel(BlurBackArgs 
         }
     }
     int i_lo, i_hi;
-    chunk_range(work_g, n, a.chunks, chunk, i_lo, i_hi);
+    chunk_planes(bounds_g, work_g, n, a.chunks, chunk, i_lo, i_hi);
     TapPrefetch tp;
     if (i_lo < i_hi) {
         tp.load(taps_g, i_lo);

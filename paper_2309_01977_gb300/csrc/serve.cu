@@ -170,7 +170,7 @@ size_t request_bytes(const spect_geom& g, int num_sms)
     if (g.flags & SPECT_FLAG_ATTEN) b += na * vol * 4;                   // attenuation cache
     const size_t tables = g.det_offsets ? na : 1;                        // PSF tables (orbit)
     if (g.flags & SPECT_FLAG_PSF_BF16) b += tables * n * 2 * 128 * 128 * 2;  // Toeplitz tiles
-    b += tables * n * (41 * 4 + 3 * 4);                                   // taps, radii, work
+    b += tables * (n * 41 * 4 + spect::psf_int_stride((int)n) * 4);             // taps, radii, work, chunk bounds
     b += 3 * vol * 4 + na * plane * 4;                                   // mu, x, y
     b += 1 << 20;                                                        // tables, small scratch
     return b;

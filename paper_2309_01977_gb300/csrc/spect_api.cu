@@ -70,6 +70,49 @@ cudaError_t timed(spect_plan* p, const char* name, cudaStream_t st, int kernels,
     return e;
 }
 
+// Boundaries out[0..c] of the split of planes 0..n-1 (work prefix sums w)
+// into c contiguous depth chunks whose heaviest chunk is as light as
+// possible: the smallest feasible cap by bisection, then greedy filling
+// that leaves at least one plane for every later chunk.  With c >= n the
+// chunks hold one plane each and the rest are empty.
+void chunk_bounds(const int* w, int n, int c, int* out)
+{
+    if (c >= n) {
+        for (int j = 0; j <= c; ++j) out[j] = std::min(j, n);
+        return;
+    }
+    long long lo = 0, hi = w[n];
+    for (int i = 0; i < n; ++i) lo = std::max<long long>(lo, w[i + 1] - w[i]);
+    auto feasible = [&](long long cap) {
+        int parts = 1;
+        long long s = 0;
+        for (int i = 0; i < n; ++i) {
+            const long long x = w[i + 1] - w[i];
+            if (s + x > cap) {
+                ++parts;
+                s = x;
+            } else {
+                s += x;
+            }
+        }
+        return parts <= c;
+    };
+    while (lo < hi) {
+        const long long mid = (lo + hi) / 2;
+        if (feasible(mid)) hi = mid;
+        else lo = mid + 1;
+    }
+    int pos = 0;
+    for (int j = 0; j < c; ++j) {
+        out[j] = pos;
+        if (j == c - 1) break;
+        const int rem = c - j - 1;
+        ++pos;  // at least one plane
+        while (pos < n && w[pos + 1] - w[out[j]] <= lo && n - (pos + 1) >= rem) ++pos;
+    }
+    out[c] = n;
+}
+
 int fail(int status, const char* fmt, ...)
 {
     char buf[512];
@@ -278,8 +321,9 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
             a.taps = p->d_taps;
             a.rad = p->d_rad;
             a.work = p->d_rad + p->n;  // forward work prefix
+            a.bounds = p->d_rad + 3 * p->n + 2;
             a.taps_stride = p->psf_tables > 1 ? (size_t)p->n * kTapW : 0;
-            a.rad_stride = p->psf_tables > 1 ? 3 * p->n + 2 : 0;
+            a.rad_stride = p->psf_tables > 1 ? psf_int_stride(p->n) : 0;
             a.sel = sel_dev;
             a.n = p->n;
             a.nz = p->nz;
@@ -360,8 +404,9 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
                 bb.taps = p->d_taps;
                 bb.rad = p->d_rad;
                 bb.work = p->d_rad + 2 * p->n + 1;  // blur_back work prefix
+                bb.bounds = p->d_rad + 3 * p->n + 2 + kBoundInts;
                 bb.taps_stride = p->psf_tables > 1 ? (size_t)p->n * kTapW : 0;
-                bb.rad_stride = p->psf_tables > 1 ? 3 * p->n + 2 : 0;
+                bb.rad_stride = p->psf_tables > 1 ? psf_int_stride(p->n) : 0;
                 bb.sel = sel_dev + g0;
                 bb.n = p->n;
                 bb.nz = p->nz;
@@ -733,7 +778,7 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     p->bvol_cap = (size_t)std::max(p->max_subset, 16);
     if ((rc = dev_alloc(p, &p->d_cs, p->na)) ||
         (rc = dev_alloc(p, &p->d_taps, taps.size())) ||
-        (rc = dev_alloc(p, &p->d_rad, (size_t)p->psf_tables * (3 * p->n + 2))) ||
+        (rc = dev_alloc(p, &p->d_rad, (size_t)p->psf_tables * psf_int_stride(p->n))) ||
         (rc = dev_alloc(p, &p->d_sel_all, (size_t)p->na)) ||
         (rc = dev_alloc(p, &p->d_sens, (size_t)p->M * vol)) ||
         (rc = dev_alloc(p, &p->d_partials, p->partial_planes * plane)) ||
@@ -783,7 +828,7 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     // attenuation loads) plus a cost per tap, in the ratios measured on
     // GB300 with per-CTA timers: about 43 taps' worth per plane for the
     // forward and 27 for the back blur
-    const size_t rstride = 3 * (size_t)p->n + 2;  // per table: radii, forward and back work prefixes
+    const size_t rstride = psf_int_stride(p->n);  // per table: radii, work prefixes, chunk boundaries
     std::vector<int> radw(p->psf_tables * rstride, 0);
     for (int a = 0; a < p->psf_tables; ++a) {
         int* rw = radw.data() + a * rstride;
@@ -793,6 +838,12 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
             rw[i] = rad[(size_t)a * p->n + i];
             wf[i + 1] = wf[i] + 43 + (2 * rw[i] + 1);
             wb[i + 1] = wb[i] + 27 + (2 * rw[i] + 1);
+        }
+        int* bf = wb + p->n + 1;
+        int* bb = bf + kBoundInts;
+        for (int c = 1; c <= kBoundChunks; ++c) {
+            chunk_bounds(wf, p->n, c, bf + bound_offset(c));
+            chunk_bounds(wb, p->n, c, bb + bound_offset(c));
         }
     }
     SPECT_CK(cudaMemcpyAsync(p->d_rad, radw.data(), radw.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy radii");
