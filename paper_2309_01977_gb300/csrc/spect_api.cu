@@ -825,9 +825,10 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     SPECT_CK(cudaMemcpyAsync(p->d_taps, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice, st), "copy taps");
     // radii, then per kernel the prefix sums of a per-plane work estimate
     // for the depth chunks: a fixed cost per plane (staging, barriers,
-    // attenuation loads) plus a cost per tap, in the ratios measured on
-    // GB300 with per-CTA timers: about 43 taps' worth per plane for the
-    // forward and 27 for the back blur
+    // attenuation loads) plus a cost per tap, in the ratios fitted to
+    // per-CTA timers on GB300 at 128^3 (1,500 CTAs of 2 to 26 planes, RMS
+    // error 4 % / 8 %): 28 taps' worth per plane for the forward (4.28 us +
+    // 0.155 us per tap) and 15 for the back blur (2.41 us + 0.157 us per tap)
     const size_t rstride = psf_int_stride(p->n);  // per table: radii, work prefixes, chunk boundaries
     std::vector<int> radw(p->psf_tables * rstride, 0);
     for (int a = 0; a < p->psf_tables; ++a) {
@@ -836,8 +837,8 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
         int* wb = wf + p->n + 1;
         for (int i = 0; i < p->n; ++i) {
             rw[i] = rad[(size_t)a * p->n + i];
-            wf[i + 1] = wf[i] + 43 + (2 * rw[i] + 1);
-            wb[i + 1] = wb[i] + 27 + (2 * rw[i] + 1);
+            wf[i + 1] = wf[i] + 28 + (2 * rw[i] + 1);
+            wb[i + 1] = wb[i] + 15 + (2 * rw[i] + 1);
         }
         int* bf = wb + p->n + 1;
         int* bb = bf + kBoundInts;
