@@ -139,13 +139,25 @@ __global__ void __launch_bounds__(256) forward_reduce_kernel(ReduceArgs a)
         const int item = (int)(e / plane4);
         const int off4 = (int)(e - (size_t)item * plane4);
         const float4* src = reinterpret_cast<const float4*>(a.partials) + (size_t)item * a.chunks * plane4 + off4;
+        // the partials summed in chunk order, up to 12 of their loads in
+        // flight together (the order of the sums, and so the result, is that
+        // of a plain loop)
         float4 p = __ldcg(src);
-        for (int c = 1; c < a.chunks; ++c) {
-            const float4 v = __ldcg(src + (size_t)c * plane4);
-            p.x += v.x;
-            p.y += v.y;
-            p.z += v.z;
-            p.w += v.w;
+        int c = 1;
+        for (; c < a.chunks; c += 12) {
+            float4 v[12];
+#pragma unroll
+            for (int u = 0; u < 12; ++u)
+                if (c + u < a.chunks) v[u] = __ldcg(src + (size_t)(c + u) * plane4);
+#pragma unroll
+            for (int u = 0; u < 12; ++u) {
+                if (c + u < a.chunks) {
+                    p.x += v[u].x;
+                    p.y += v[u].y;
+                    p.z += v[u].z;
+                    p.w += v[u].w;
+                }
+            }
         }
         float4 o = p;
         if (a.y) {
