@@ -238,15 +238,18 @@ __global__ void __launch_bounds__(kGatherTiledThreads) gather_tiled_kernel(Gathe
         for (int k = 0; k < kCols; ++k) {
             const int cl = warp + 8 * k;
             if (landed && cl < ncols) {
-                // the column's entries, one per lane, then broadcast in order
-                const int2 ent = lane < kMaxCand ? tab[cl * kMaxCand + lane] : make_int2(0, 0);
+                // the column's entries in order, each read by the whole warp
+                // from one shared-memory word (a broadcast); the table keeps
+                // a column's candidates first, so the first empty entry ends
+                // the list
+                const int2* ce = tab + cl * kMaxCand;
 #pragma unroll
                 for (int e = 0; e < kMaxCand; ++e) {
-                    const int row = __shfl_sync(0xffffffffu, ent.x, e);
-                    const int wb = __shfl_sync(0xffffffffu, ent.y, e);
-                    if (wb != 0 && lane < zw) {
-                        const float w = __int_as_float(wb);
-                        const float4 v = buf[(size_t)row * zw + lane];
+                    const int2 ent = ce[e];
+                    if (ent.y == 0) break;
+                    if (lane < zw) {
+                        const float w = __int_as_float(ent.y);
+                        const float4 v = buf[(size_t)ent.x * zw + lane];
                         const float2 lo = __ffma2_rn(make_float2(w, w), make_float2(v.x, v.y),
                                                      make_float2(acc[k].x, acc[k].y));
                         const float2 hi = __ffma2_rn(make_float2(w, w), make_float2(v.z, v.w),
