@@ -44,6 +44,13 @@ CASES = {
     # non-circular (elliptical) orbit: every angle has its own PSF table
     "orbit48x40": (dict(n=48, nz=40, n_angles=12, n_subsets=3,
                         det_offsets=[2.0 + 1.5 * math.cos(2 * 2 * math.pi * a / 12) for a in range(12)]), 16),
+    # the largest supported PSF radius (R = 20 at the deepest plane), one
+    # angle per subset
+    "max_radius": (dict(n=48, nz=32, n_angles=6, n_subsets=6, psf_slope=0.129), 17),
+    # a single angle
+    "one_angle": (dict(n=16, nz=16, n_angles=1, n_subsets=1), 18),
+    # a wide plane (256 x 256 rows, tiled gather) with short z rows
+    "wide256x32": (dict(n=256, nz=32, n_angles=4, n_subsets=2, psf_slope=0.02), 19),
 }
 
 
