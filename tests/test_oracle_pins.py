@@ -374,3 +374,23 @@ def test_multi_peak_count_conservation(oracle_mod):
         meas = y1[sel].sum() + y2[sel].sum()
         assert pred == pytest.approx(meas, rel=1e-11)
         f = f_new
+
+
+def test_rotation_keeps_a_constant_field_inside_the_grid(oracle_mod):
+    """Bilinear weights sum to one: a constant volume stays constant at every
+    rotated voxel whose four taps lie inside the grid (the inscribed region),
+    for arbitrary angles; voxels whose sample point leaves the grid by a full
+    voxel read zero."""
+    n, nz, c0 = 20, 3, 2.75
+    f = np.full((n, n, nz), c0)
+    cen = 0.5 * (n - 1)
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    for theta in (0.3, 1.1, 2.5, 4.0, 5.9):
+        out = oracle_mod.rotate(f, theta)
+        u = cen + np.cos(theta) * (ii - cen) - np.sin(theta) * (jj - cen)
+        v = cen + np.sin(theta) * (ii - cen) + np.cos(theta) * (jj - cen)
+        inside = (u >= 0) & (u <= n - 1) & (v >= 0) & (v <= n - 1)
+        np.testing.assert_allclose(out[inside], c0, rtol=0, atol=1e-13)
+        outside = (u < -1) | (u > n) | (v < -1) | (v > n)
+        assert np.all(out[outside] == 0.0)
+        assert inside.sum() > n * n // 2
