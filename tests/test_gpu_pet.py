@@ -325,3 +325,30 @@ def test_tof_full_grid_sampled_lines(pet_mods, cuda):
     print("PET TOF 204^3-grid sampled lines: max rel err %.2e" % float(err.max()))
     assert float(err.max()) <= 1e-5
     plan.close()
+
+
+def test_tof_bins_outside_the_range_and_bad_arguments(pet_mods, small_tof, cuda):
+    """Bins past either end of the range move the window off the line (the
+    projection is the Gaussian's far tail or zero on both sides); a bin array
+    for a plan without time of flight and misaligned lines are rejected."""
+    pet, pp, opet = pet_mods
+    wl, act, mu, lors, eta, s, tb, og = small_tof
+    L = lors[:400]
+    B = np.where(np.arange(400) % 2 == 0, -3, wl.tof_bins + 2).astype(np.int32)
+    plan = _plan(pet, wl, mu, cuda)
+    got = plan.forward(_t(act, cuda), _t(L, cuda), tof_bin=_ti(B, cuda)).cpu().numpy()
+    ref = opet.forward(act, L, og, tof=_otof(opet, wl, B))
+    assert np.max(np.abs(got - ref)) <= 1e-5 * max(1.0, float(np.max(np.abs(opet.forward(act, L, og)))))
+    plan.close()
+    no_tof = pet.PetPlan(pet.PetGeometry(wl.shape, wl.voxel), None, stream=torch.cuda.current_stream())
+    with pytest.raises(pet.SpectError) as e:
+        no_tof.forward(_t(act, cuda), _t(L, cuda), tof_bin=_ti(B, cuda))
+    assert e.value.status == pet.SPECT_EINVAL
+    lib = pet.load()
+    Ld = _t(L, cuda)
+    out = torch.empty(len(L) - 1, device=cuda)
+    bad = Ld.data_ptr() + 4  # 4-byte offset: not 8-byte aligned
+    rc = lib.pet_forward(no_tof.handle, _t(act, cuda).data_ptr(), bad, None, None, len(L) - 1, out.data_ptr(),
+                         torch.cuda.current_stream().cuda_stream)
+    assert rc == pet.SPECT_EINVAL
+    no_tof.close()
