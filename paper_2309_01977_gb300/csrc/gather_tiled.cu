@@ -234,27 +234,41 @@ __global__ void __launch_bounds__(kGatherTiledThreads) gather_tiled_kernel(Gathe
         const bool landed = mbar_wait(smem_u32(bars + q), (uint32_t)((g / S) & 1));
         const float4* buf = bufs + q * buf_f4;
         const int2* tab = reinterpret_cast<const int2*>(buf + (size_t)a.rows_cap * zw);
+        // Columns in groups of kGroup, candidate slot by slot: the slot's
+        // entries of the group's columns are read together (each a
+        // warp-wide broadcast of one shared-memory word), then their data
+        // rows, then the sums, so that the group's loads are in flight at
+        // once.  A column's candidates come first in its list, in the order
+        // they are summed; a slot empty in every column of the group ends it.
+        constexpr int kGroup = 4;
 #pragma unroll
-        for (int k = 0; k < kCols; ++k) {
-            const int cl = warp + 8 * k;
-            if (landed && cl < ncols) {
-                // the column's entries in order, each read by the whole warp
-                // from one shared-memory word (a broadcast); the table keeps
-                // a column's candidates first, so the first empty entry ends
-                // the list
-                const int2* ce = tab + cl * kMaxCand;
+        for (int k0 = 0; k0 < kCols; k0 += kGroup) {
+#pragma unroll 1
+            for (int e = 0; e < kMaxCand; ++e) {
+                int2 ent[kGroup];
+                bool any = false;
 #pragma unroll
-                for (int e = 0; e < kMaxCand; ++e) {
-                    const int2 ent = ce[e];
-                    if (ent.y == 0) break;
-                    if (lane < zw) {
-                        const float w = __int_as_float(ent.y);
-                        const float4 v = buf[(size_t)ent.x * zw + lane];
-                        const float2 lo = __ffma2_rn(make_float2(w, w), make_float2(v.x, v.y),
-                                                     make_float2(acc[k].x, acc[k].y));
-                        const float2 hi = __ffma2_rn(make_float2(w, w), make_float2(v.z, v.w),
-                                                     make_float2(acc[k].z, acc[k].w));
-                        acc[k] = make_float4(lo.x, lo.y, hi.x, hi.y);
+                for (int u = 0; u < kGroup; ++u) {
+                    const int cl = warp + 8 * (k0 + u);
+                    ent[u] = (landed && k0 + u < kCols && cl < ncols) ? tab[cl * kMaxCand + e] : make_int2(0, 0);
+                    any |= ent[u].y != 0;
+                }
+                if (!any) break;
+                if (lane < zw) {
+                    float4 v[kGroup];
+#pragma unroll
+                    for (int u = 0; u < kGroup; ++u)
+                        if (k0 + u < kCols && ent[u].y != 0) v[u] = buf[(size_t)ent[u].x * zw + lane];
+#pragma unroll
+                    for (int u = 0; u < kGroup; ++u) {
+                        if (k0 + u >= kCols || ent[u].y == 0) continue;
+                        const float w = __int_as_float(ent[u].y);
+                        float4& a4 = acc[k0 + u];
+                        const float2 lo = __ffma2_rn(make_float2(w, w), make_float2(v[u].x, v[u].y),
+                                                     make_float2(a4.x, a4.y));
+                        const float2 hi = __ffma2_rn(make_float2(w, w), make_float2(v[u].z, v[u].w),
+                                                     make_float2(a4.z, a4.w));
+                        a4 = make_float4(lo.x, lo.y, hi.x, hi.y);
                     }
                 }
             }
