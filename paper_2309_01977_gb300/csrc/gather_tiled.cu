@@ -183,9 +183,10 @@ __device__ __forceinline__ void issue_footprint(const GatherTiledArgs& a, const 
 }  // namespace
 
 // 256 threads: warp w sums columns w, w + 8, ... of the T x T tile; lane l
-// holds float4 l of the z segment (lanes past zs/4 idle).
+// holds float4 l of the z segment (lanes past zs/4 idle).  Two CTAs per SM
+// (their shared memory allows two): at most 128 registers.
 template <int T>
-__global__ void __launch_bounds__(kGatherTiledThreads) gather_tiled_kernel(GatherTiledArgs a)
+__global__ void __launch_bounds__(kGatherTiledThreads, 2) gather_tiled_kernel(GatherTiledArgs a)
 {
     extern __shared__ __align__(16) float4 gsm[];
     const int tile = blockIdx.x, b = blockIdx.y;
@@ -234,13 +235,14 @@ __global__ void __launch_bounds__(kGatherTiledThreads) gather_tiled_kernel(Gathe
         const bool landed = mbar_wait(smem_u32(bars + q), (uint32_t)((g / S) & 1));
         const float4* buf = bufs + q * buf_f4;
         const int2* tab = reinterpret_cast<const int2*>(buf + (size_t)a.rows_cap * zw);
-        // Columns in groups of kGroup, candidate slot by slot: the slot's
+        // Columns in groups of kGroup (all of a warp's columns at T = 8),
+        // candidate slot by slot: the slot's
         // entries of the group's columns are read together (each a
         // warp-wide broadcast of one shared-memory word), then their data
         // rows, then the sums, so that the group's loads are in flight at
         // once.  A column's candidates come first in its list, in the order
         // they are summed; a slot empty in every column of the group ends it.
-        constexpr int kGroup = 4;
+        constexpr int kGroup = 8;
 #pragma unroll
         for (int k0 = 0; k0 < kCols; k0 += kGroup) {
 #pragma unroll 1
