@@ -11,7 +11,11 @@ a wrong sign or index, a transposed operand) fails at least one of them:
   - adjointness <Hx, y> = <x, H^T y>;
   - OSEM count conservation (s = 0) and its s > 0 form;
   - the Poisson gradient of Table 1 against central finite differences of
-    the log-likelihood.
+    the log-likelihood;
+  - MAP algorithms: the optimality condition of the MAP objective at the
+    limit (one subset, and M identical subsets for the beta / M weight),
+    plain MLEM steps and the relaxation schedule of BSREM on identical
+    subsets, and BSREM's approach to the MAP point with distinct subsets.
 """
 import math
 
@@ -306,6 +310,111 @@ def test_map_prior_smooths(oracle_mod, algorithm):
     f1 = oracle_mod.map_recon(y, s, g, 4, 0, 8, algorithm, "rdp", beta=0.3)
     assert oracle_mod.prior_value(f1, "rdp") < oracle_mod.prior_value(f0, "rdp")
     assert np.isfinite(f1).all() and f1.min() >= 0.0
+
+
+# MAP algorithms pinned by the optimality condition of the MAP objective
+# Phi(f) = L(f) - beta V(f) (Eq. PGA with the Poisson gradient of Table 1):
+# at a maximiser f >= 0, f (grad L(f) - beta grad V(f)) = 0 voxel by voxel.
+# grad L comes from the oracle's H and H^T (pinned by the dense H above) and
+# grad V from the prior gradient (pinned by finite differences above), so
+# the check is independent of or_map's update formulas.  The subset
+# scalings are pinned by data sets whose M subsets are identical (every
+# angle listed M times): then L = M L_K (L_K the likelihood of one copy), so
+# the MAP point of beta is the MAP point of L_K - (beta / M) V, and a
+# BSREM step of one subset is a plain MLEM step of L_K.
+
+_MAP_K, _MAP_M = 12, 4
+
+
+def _map_problem(oracle_mod, copies=1):
+    """8^3 x 4 volume, 12 angles (each listed `copies` times in a row), y = H f + s."""
+    n, nz, K = 8, 4, _MAP_K
+    rng = _rng(7)
+    base = [2 * math.pi * k / K + 0.3 for k in range(K)]
+    f_true = rng.uniform(0.5, 2.0, size=(n, n, nz))
+    mu = np.full((n, n, nz), 0.1)
+    kw = dict(n=n, nz=nz, mu=mu, sigma0=0.6, slope=0.05)
+    g1 = oracle_mod.Geom(n_angles=K, angles=base, **kw)
+    y1 = oracle_mod.forward(f_true, g1)
+    s = 0.05 * y1.mean()
+    y1 = y1 + s
+    if copies == 1:
+        return g1, y1, s
+    # angle a = k * copies + m: subset m of `copies` subsets holds each base angle once
+    g = oracle_mod.Geom(n_angles=K * copies, angles=[base[a // copies] for a in range(K * copies)], **kw)
+    return g, np.repeat(y1, copies, axis=0), s
+
+
+def _kkt(oracle_mod, f, g, y, s, beta, prior):
+    """|| f (grad L - beta grad V) || relative to || f H^T 1 ||."""
+    p = oracle_mod.forward(f, g)
+    ones = np.ones_like(p)
+    gl = oracle_mod.back(y / (p + s), g) - oracle_mod.back(ones, g)
+    gv = oracle_mod.prior_grad(f, prior, delta=1.0, gamma=2.0)
+    return np.linalg.norm(f * (gl - beta * gv)) / np.linalg.norm(f * oracle_mod.back(ones, g))
+
+
+@pytest.mark.parametrize("prior", ["quadratic", "rdp"])
+def test_osmaposl_one_subset_converges_to_the_map_point(oracle_mod, prior):
+    """One subset: the one-step-late fixed point satisfies the MAP optimality
+    condition of L - beta V; the same image is far from optimal for 2 beta
+    (a prior term scaled or signed wrongly would fail)."""
+    g, y, s = _map_problem(oracle_mod)
+    beta = 0.1
+    f = oracle_mod.map_recon(y, s, g, 1, 0, 600, "osmaposl", prior, beta=beta)
+    assert _kkt(oracle_mod, f, g, y, s, beta, prior) <= 1e-12
+    assert _kkt(oracle_mod, f, g, y, s, 2 * beta, prior) >= 1e-3
+
+
+def test_osmaposl_identical_subsets_weight_the_prior_by_one_over_m(oracle_mod):
+    """M identical subsets: the limit is the MAP point of the whole data set
+    for beta (so the per-subset weight is beta / M), not of beta M."""
+    g, y, s = _map_problem(oracle_mod, copies=_MAP_M)
+    beta = 0.1
+    f = oracle_mod.map_recon(y, s, g, _MAP_M, 0, 400 * _MAP_M, "osmaposl", "quadratic", beta=beta)
+    assert _kkt(oracle_mod, f, g, y, s, beta, "quadratic") <= 1e-12
+    assert _kkt(oracle_mod, f, g, y, s, beta * _MAP_M, "quadratic") >= 1e-3
+    # each subiteration is a one-subset step on one copy with the prior weight beta / M
+    g1, y1, _ = _map_problem(oracle_mod)
+    f1 = oracle_mod.map_recon(y1, s, g1, 1, 0, 400 * _MAP_M, "osmaposl", "quadratic", beta=beta / _MAP_M)
+    np.testing.assert_allclose(f, f1, rtol=1e-12, atol=0)
+
+
+def test_bsrem_identical_subsets_are_mlem_steps_with_the_relaxation_schedule(oracle_mod):
+    """M identical subsets, beta = 0, alpha0 = 1: H^T 1 = M H_K^T 1, so with
+    c_n = 1/M each subiteration of the first iteration is an MLEM step of one
+    copy (alpha = 1); the first subiteration of the second iteration has
+    alpha = 1/2 and lands halfway between its start and that MLEM step."""
+    g, y, s = _map_problem(oracle_mod, copies=_MAP_M)
+    g1, y1, _ = _map_problem(oracle_mod)
+    f_b = oracle_mod.map_recon(y, s, g, _MAP_M, 0, _MAP_M, "bsrem", "quadratic", beta=0.0, alpha0=1.0)
+    f_m, _ = oracle_mod.osem(y1, s, g1, 1, 0, _MAP_M)
+    np.testing.assert_allclose(f_b, f_m, rtol=1e-13, atol=0)
+    f_b1 = oracle_mod.map_recon(y, s, g, _MAP_M, 0, _MAP_M + 1, "bsrem", "quadratic", beta=0.0, alpha0=1.0)
+    f_m1, _ = oracle_mod.osem(y1, s, g1, 1, 0, 1, f_m)
+    np.testing.assert_allclose(f_b1, 0.5 * (f_m + f_m1), rtol=1e-13, atol=0)
+
+
+def test_bsrem_converges_to_the_map_point(oracle_mod):
+    """Distinct subsets: the relaxed BSREM iterates approach the MAP point of
+    L - beta V (the OSMAPOSL limit of one subset, pinned above), and get
+    closer as the relaxation shrinks; unrelaxed OSMAPOSL with the same
+    subsets stalls further away (a limit cycle)."""
+    g, y, s = _map_problem(oracle_mod)
+    beta, M = 0.1, _MAP_M
+    f_map = oracle_mod.map_recon(y, s, g, 1, 0, 600, "osmaposl", "quadratic", beta=beta)
+
+    def dist(f):
+        return np.linalg.norm(f - f_map) / np.linalg.norm(f_map)
+
+    f_200 = oracle_mod.map_recon(y, s, g, M, 0, 200 * M, "bsrem", "quadratic", beta=beta, alpha0=1.0)
+    f_800 = oracle_mod.map_recon(y, s, g, M, 0, 800 * M, "bsrem", "quadratic", beta=beta, alpha0=1.0)
+    f_osl = oracle_mod.map_recon(y, s, g, M, 0, 400 * M, "osmaposl", "quadratic", beta=beta)
+    assert dist(f_800) <= 6e-4
+    assert dist(f_800) < 0.6 * dist(f_200)
+    assert dist(f_osl) > 5 * dist(f_800)
+    assert _kkt(oracle_mod, f_800, g, y, s, beta, "quadratic") <= 1e-4
+    assert _kkt(oracle_mod, f_800, g, y, s, beta * M, "quadratic") >= 1e-2
 
 
 # ---------------------------------------------------------------- non-circular orbits
