@@ -25,9 +25,10 @@
  *     interpolated in the other two axes, taps outside the image read 0; every
  *     sample is weighted by the line's length between neighbouring planes,
  *     v_a |p2 - p1| / |p2_a - p1_a| (mm).  The principal axis and the plane
- *     range are integers that floating point decides; both are taken in
- *     single precision from the single-precision endpoints (the precision of
- *     the CUDA kernel), with the operation order written in lor_planes().
+ *     range are integers that floating point decides; the oracle takes them
+ *     in double precision from the endpoints as given (a line whose
+ *     single-precision decision differs is a rounding tie, which the tests
+ *     identify and leave out of the comparison).
  *   - T_rr: separable Gaussian with standard deviation sigma (mm) per axis,
  *     sigma / v_c voxels on axis c, sampled taps exp(-t^2 / 2 s^2) for
  *     |t| <= ceil(nsigma s), normalised to sum 1, zero padding, same size.
@@ -39,10 +40,8 @@
  *     midpoint (positive towards p2); a sample at l in bin b is weighted by
  *     Phi((l - c_b + D/2)/sigma) - Phi((l - c_b - D/2)/sigma) (the Gaussian
  *     timing kernel integrated over the bin).  Only samples of the window
- *     |l - c_b| <= nsigma sigma + D/2 count; the window is a range of sample
- *     indices taken in double precision from the line's set-up values with
- *     the operation order written in tof_window() (the kernel's order).  The
- *     attenuation factors never use time of flight.
+ *     |l - c_b| <= nsigma sigma + D/2 count, tested sample by sample in
+ *     double precision.  The attenuation factors never use time of flight.
  *   - listmode OSEM: subsets of events {e : e mod M == m}, visited
  *     m = 0..M-1; with p_e = mult_e (P_Sigma T_rr f)_e and the additive term
  *     s_e (randoms and scatter expected on that LOR),
@@ -61,34 +60,27 @@ typedef struct {
     double v[3];   /* voxel size, mm */
 } pet_img;
 
-/* The integer decisions of Joseph's method for one LOR, in single precision:
- * principal axis *a and planes [*q_lo, *q_hi] (empty when q_lo > q_hi). */
+/* The integer decisions of Joseph's method for one LOR, in double precision:
+ * principal axis *a (largest |p2_c - p1_c| / v_c, ties to the lower axis)
+ * and the planes [*q_lo, *q_hi] of that axis whose index lies between the
+ * endpoints' index coordinates, inside the image (empty when q_lo > q_hi). */
 static void lor_planes(const pet_img* g, const double* lor, int* a, int* q_lo, int* q_hi)
 {
-    float p1[3], p2[3], sc[3];
-    for (int c = 0; c < 3; ++c) {
-        p1[c] = (float)lor[c];
-        p2[c] = (float)lor[3 + c];
-        const float d = p2[c] - p1[c];
-        sc[c] = fabsf(d) / (float)g->v[c];
-    }
+    double sc[3];
+    for (int c = 0; c < 3; ++c) sc[c] = fabs(lor[3 + c] - lor[c]) / g->v[c];
     int ax = 0;
     if (sc[1] > sc[ax]) ax = 1;
     if (sc[2] > sc[ax]) ax = 2;
     *a = ax;
     *q_lo = 1;
     *q_hi = 0;
-    if (!(sc[ax] > 0.f)) return;
-    const float va = (float)g->v[ax];
-    const float half = 0.5f * (float)(g->n[ax] - 1);
-    const float org = -(half * va);
-    const float s1 = (p1[ax] - org) / va;
-    const float s2 = (p2[ax] - org) / va;
-    float lo = s1 < s2 ? s1 : s2, hi = s1 < s2 ? s2 : s1;
-    lo = ceilf(lo);
-    hi = floorf(hi);
-    if (lo < 0.f) lo = 0.f;
-    if (hi > (float)(g->n[ax] - 1)) hi = (float)(g->n[ax] - 1);
+    if (!(sc[ax] > 0.0)) return;
+    const double org = -0.5 * (double)(g->n[ax] - 1) * g->v[ax];
+    const double s1 = (lor[ax] - org) / g->v[ax];
+    const double s2 = (lor[3 + ax] - org) / g->v[ax];
+    double lo = ceil(s1 < s2 ? s1 : s2), hi = floor(s1 < s2 ? s2 : s1);
+    if (lo < 0.0) lo = 0.0;
+    if (hi > (double)(g->n[ax] - 1)) hi = (double)(g->n[ax] - 1);
     if (lo > hi) return;
     *q_lo = (int)lo;
     *q_hi = (int)hi;
@@ -118,28 +110,6 @@ void or_pet_set_tof(int n_bins, double bin_mm, double sigma_mm, double nsigma, c
     g_tof.bins = n_bins > 0 ? bins : NULL;
 }
 
-/* Sample index window [*i_lo, *i_hi] of a line whose first sample sits at
- * arc length l0 and whose samples are dl apart, for TOF bin `bin`. */
-static void tof_window(const pet_tof* tf, int bin, double l0, double dl, int count, int* i_lo, int* i_hi)
-{
-    const double c = ((double)bin - 0.5 * (double)(tf->nb - 1)) * tf->bin_mm;
-    const double w = tf->nsigma * tf->sigma_mm + 0.5 * tf->bin_mm;
-    double lo = (c - w - l0) / dl, hi = (c + w - l0) / dl;
-    if (dl < 0.0) {
-        const double t = lo;
-        lo = hi;
-        hi = t;
-    }
-    lo = ceil(lo);
-    hi = floor(hi);
-    if (lo < 0.0) lo = 0.0;
-    if (lo > (double)count) lo = (double)count;
-    if (hi > (double)(count - 1)) hi = (double)(count - 1);
-    if (hi < -1.0) hi = -1.0;
-    *i_lo = (int)lo;
-    *i_hi = (int)hi;
-}
-
 static double std_normal_cdf(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
 
 /* Visit the samples of one LOR: for every plane q of the principal axis, the
@@ -164,20 +134,13 @@ static void lor_walk(const pet_img* g, const double* lor, const pet_tof* tf, int
     }
     const double len = sqrt(len2);
     const double step = g->v[a] * len / fabs(d[a]);
-    int i_lo = 0, i_hi = q_hi - q_lo;
-    double l0 = 0.0, dl = 0.0, cb = 0.0;
-    if (tf) {
-        const double da = e2[a] - e1[a];
-        const double t0 = ((double)q_lo - e1[a]) / da;
-        l0 = (t0 - 0.5) * len;
-        dl = len / da;
-        tof_window(tf, bin, l0, dl, q_hi - q_lo + 1, &i_lo, &i_hi);
-        cb = ((double)bin - 0.5 * (double)(tf->nb - 1)) * tf->bin_mm;
-    }
-    for (int q = q_lo + i_lo; q <= q_lo + i_hi; ++q) {
+    const double cb = tf ? ((double)bin - 0.5 * (double)(tf->nb - 1)) * tf->bin_mm : 0.0;
+    for (int q = q_lo; q <= q_hi; ++q) {
         double wt_tof = 1.0;
         if (tf) {
+            /* signed arc length of the sample from the line's midpoint */
             const double l = ((q - e1[a]) / (e2[a] - e1[a]) - 0.5) * len;
+            if (!(fabs(l - cb) <= tf->nsigma * tf->sigma_mm + 0.5 * tf->bin_mm)) continue;
             wt_tof = std_normal_cdf((l - cb + 0.5 * tf->bin_mm) / tf->sigma_mm) -
                      std_normal_cdf((l - cb - 0.5 * tf->bin_mm) / tf->sigma_mm);
         }
@@ -232,7 +195,7 @@ static pet_img make_img(int nx, int ny, int nz, const double* v)
     return g;
 }
 
-/* Principal axis and plane range of each LOR (the single-precision decisions). */
+/* Principal axis and plane range of each LOR (the double-precision decisions). */
 void or_pet_planes(const double* lors, long n_lors, int nx, int ny, int nz, const double* v, int* out3)
 {
     const pet_img g = make_img(nx, ny, nz, v);

@@ -3,8 +3,8 @@ the FP64 oracle (tests only).
 
 Joseph's method (Sec. 2.1.1, Eq. (2), P_Sigma) restated in numpy: per line
 of response the principal axis and the sampled voxel planes are decided in
-single precision (the documented reading), the sample points are placed in
-double precision, and the image is read at them with scipy's linear
+double precision, the sample points are placed in double precision, and
+the image is read at them with scipy's linear
 interpolation (``ndimage.map_coordinates``, order 1, zero outside the grid
 tap by tap), weighted by the line's length between planes.  T_rr is applied
 with ``ndimage.convolve1d`` and taps from ``signal.windows.gaussian``.
@@ -16,24 +16,22 @@ from scipy.stats import norm
 
 
 def decisions(lor, shape, voxel):
-    p1 = np.asarray(lor[:3], dtype=np.float32)
-    p2 = np.asarray(lor[3:], dtype=np.float32)
-    v = np.asarray(voxel, dtype=np.float32)
-    sc = np.abs(p2 - p1) / v
+    """Principal axis (largest |d_c| / v_c, ties to the lower axis) and the
+    planes of that axis between the ends, clipped to the image."""
+    lor = np.asarray(lor, dtype=np.float64)
+    v = np.asarray(voxel, dtype=np.float64)
+    sc = np.abs(lor[3:] - lor[:3]) / v
     a = 0
     for c in (1, 2):
         if sc[c] > sc[a]:
             a = c
     if not sc[a] > 0:
         return a, 1, 0
-    half = np.float32(0.5) * np.float32(shape[a] - 1)
-    org = -(half * v[a])
-    s1 = (p1[a] - org) / v[a]
-    s2 = (p2[a] - org) / v[a]
-    lo = np.ceil(min(s1, s2))
-    hi = np.floor(max(s1, s2))
-    lo = max(lo, np.float32(0))
-    hi = min(hi, np.float32(shape[a] - 1))
+    org = -0.5 * (shape[a] - 1) * v[a]
+    s1 = (lor[a] - org) / v[a]
+    s2 = (lor[3 + a] - org) / v[a]
+    lo = max(np.ceil(min(s1, s2)), 0.0)
+    hi = min(np.floor(max(s1, s2)), float(shape[a] - 1))
     if lo > hi:
         return a, 1, 0
     return a, int(lo), int(hi)
@@ -61,36 +59,21 @@ def samples(lor, shape, voxel):
 def tof_weights(lor, shape, voxel, tof, b):
     """Timing weights of one line's samples for TOF bin b (tof = (n_bins,
     bin_mm, sigma_mm, nsigma)): the Gaussian integrated over the bin, by
-    scipy's normal CDF, inside the window of sample indices (restated from
-    the reading, in double precision, same operation order)."""
+    scipy's normal CDF, for samples within nsigma sigma + width / 2 of the
+    bin centre, else 0."""
     nb, width, sigma, nsig = tof
     a, q0, q1 = decisions(lor, shape, voxel)
     lor = np.asarray(lor, dtype=np.float64)
     v = np.asarray(voxel, dtype=np.float64)
-    e1 = np.empty(3)
-    e2 = np.empty(3)
-    len2 = 0.0
-    for t in range(3):
-        org = -0.5 * (shape[t] - 1) * v[t]
-        e1[t] = (lor[t] - org) / v[t]
-        e2[t] = (lor[3 + t] - org) / v[t]
-        d = lor[3 + t] - lor[t]
-        len2 += d * d
-    ln = np.sqrt(len2)
-    da = e2[a] - e1[a]
-    l0 = ((q0 - e1[a]) / da - 0.5) * ln
-    dl = ln / da
-    c = (b - 0.5 * (nb - 1)) * width
-    w = nsig * sigma + 0.5 * width
-    lo, hi = (c - w - l0) / dl, (c + w - l0) / dl
-    if dl < 0:
-        lo, hi = hi, lo
-    lo, hi = max(np.ceil(lo), 0.0), min(np.floor(hi), float(q1 - q0))
+    org = -0.5 * (np.asarray(shape) - 1) * v
+    e1 = (lor[:3] - org) / v
+    e2 = (lor[3:] - org) / v
+    ln = np.linalg.norm(lor[3:] - lor[:3])
     q = np.arange(q0, q1 + 1, dtype=np.float64)
-    ell = ((q - e1[a]) / da - 0.5) * ln
+    ell = ((q - e1[a]) / (e2[a] - e1[a]) - 0.5) * ln
+    c = (b - 0.5 * (nb - 1)) * width
     wt = norm.cdf((ell - c + 0.5 * width) / sigma) - norm.cdf((ell - c - 0.5 * width) / sigma)
-    i = np.arange(len(q))
-    return np.where((i >= lo) & (i <= hi), wt, 0.0)
+    return np.where(np.abs(ell - c) <= nsig * sigma + 0.5 * width, wt, 0.0)
 
 
 def joseph(f, lors, voxel, tof=None, bins=None):

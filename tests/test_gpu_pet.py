@@ -7,6 +7,11 @@ within relative L2 1e-5 of FP64; OSEM images within 2e-5; the listmode
 count identity sum (sens / M) x_new = sum p / (p + s) in FP64 diagnostics;
 at the full 204 x 204 x 154 grid, sampled lines match the oracle one by one
 and the count identity holds for a whole subiteration.
+
+The oracle decides Joseph's integers (principal axis, planes, time-of-flight
+window) in double precision, the kernel the axis and planes in single
+precision: the few lines where the two differ (rounding ties) are left out
+of each comparison and counted (pet_precision.py).
 """
 import dataclasses
 
@@ -14,6 +19,7 @@ import numpy as np
 import pytest
 
 from helpers import rel_l2
+from pet_precision import keep_alike
 
 torch = pytest.importorskip("torch")
 
@@ -81,6 +87,7 @@ def test_forward_matches_oracle(pet_mods, small, cuda):
     pet, pp, opet = pet_mods
     wl, act, mu, lors, eta, s, og = small
     L = np.concatenate([lors[:6000], _odd_lors(wl, 5)])
+    L = L[keep_alike(L, og, opet)]
     rng = np.random.Generator(np.random.PCG64(6))
     x = (act + rng.uniform(0, 0.5, size=act.shape)).astype(np.float32)
     m = rng.uniform(0.5, 1.0, size=len(L)).astype(np.float32)
@@ -101,6 +108,7 @@ def test_forward_without_resolution_model(pet_mods, small, cuda):
     pet, pp, opet = pet_mods
     wl, act, mu, lors, eta, s, og = small
     L = np.concatenate([lors[:3000], _odd_lors(wl, 7)])
+    L = L[keep_alike(L, og, opet)]
     plan = _plan(pet, wl, None, cuda, rr=False)
     got = plan.forward(_t(act, cuda), _t(L, cuda)).cpu().numpy()
     ref = opet.joseph_fwd(act, L, dataclasses.replace(og, rr_sigma_mm=0.0))
@@ -113,6 +121,8 @@ def test_mult_matches_oracle(pet_mods, small, cuda):
     wl, act, mu, lors, eta, s, og = small
     L = np.concatenate([lors[:5000], _odd_lors(wl, 8)])
     e = np.concatenate([eta[:5000], np.full(len(L) - 5000, 0.9, dtype=np.float32)])
+    keep = keep_alike(L, og, opet)
+    L, e = L[keep], e[keep]
     plan = _plan(pet, wl, mu, cuda)
     got = plan.mult(_t(L, cuda), _t(e, cuda)).cpu().numpy()
     ref = opet.mult(L, og, mu=mu, eta=e)
@@ -129,6 +139,7 @@ def test_back_matches_oracle_and_is_adjoint(pet_mods, small, cuda):
     pet, pp, opet = pet_mods
     wl, act, mu, lors, eta, s, og = small
     L = np.concatenate([lors[:8000], _odd_lors(wl, 9)])
+    L = L[keep_alike(L, og, opet)]
     rng = np.random.Generator(np.random.PCG64(10))
     q = rng.uniform(0.0, 2.0, size=len(L)).astype(np.float32)
     m = rng.uniform(0.5, 1.0, size=len(L)).astype(np.float32)
@@ -168,6 +179,8 @@ def _osem_inputs(pet, pp, opet, wl, mu, lors, eta, og):
 def test_lm_osem_matches_oracle(pet_mods, small, cuda):
     pet, pp, opet = pet_mods
     wl, act, mu, lors, eta, s, og = small
+    keep = keep_alike(lors, og, opet)
+    lors, eta, s = lors[keep], eta[keep], s[keep]
     sens, mult = _osem_inputs(pet, pp, opet, wl, mu, lors, eta, og)
     M, n_sub = wl.n_subsets, wl.n_subsets * wl.n_iters
     ref, rdiag = opet.lm_osem(lors, mult, s, sens, og, M, count=n_sub)
@@ -218,6 +231,7 @@ def test_full_grid_sampled_lines_and_count_identity(pet_mods, cuda):
     rng = np.random.Generator(np.random.PCG64(12))
     pick = np.sort(rng.choice(lors.shape[0], 2000, replace=False))
     og = opet.PetGeom(wl.shape, wl.voxel, rr_sigma_mm=np.float32(wl.rr_sigma_mm), rr_nsigma=3.0)
+    pick = pick[keep_alike(lors.cpu().numpy()[pick], og, opet)]
     L = lors.cpu().numpy()[pick]
     m_ref = opet.mult(L, og, mu=mu.cpu().numpy(), eta=eta.cpu().numpy()[pick])
     assert np.max(np.abs(mult.cpu().numpy()[pick] - m_ref) / m_ref) <= 1e-5
@@ -257,6 +271,10 @@ def _otof(opet, wl, bins):
                     sigma_mm=float(np.float32(wl.tof_sigma_mm)), bins=bins, nsigma=3.0)
 
 
+def _tof_model(wl, bins):
+    return (wl.tof_bins, wl.tof_bin_mm, wl.tof_sigma_mm, 3.0, bins)
+
+
 def _ti(a, dev):
     return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.int32))).to(dev)
 
@@ -265,6 +283,8 @@ def test_tof_forward_and_back_match_oracle(pet_mods, small_tof, cuda):
     pet, pp, opet = pet_mods
     wl, act, mu, lors, eta, s, tb, og = small_tof
     L, B = lors[:8000], tb[:8000]
+    keep = keep_alike(L, og, opet, _tof_model(wl, B))
+    L, B = L[keep], B[keep]
     rng = np.random.Generator(np.random.PCG64(30))
     x = (act + rng.uniform(0, 0.5, size=act.shape)).astype(np.float32)
     m = rng.uniform(0.5, 1.0, size=len(L)).astype(np.float32)
@@ -289,6 +309,8 @@ def test_tof_forward_and_back_match_oracle(pet_mods, small_tof, cuda):
 def test_tof_lm_osem_matches_oracle(pet_mods, small_tof, cuda):
     pet, pp, opet = pet_mods
     wl, act, mu, lors, eta, s, tb, og = small_tof
+    keep = keep_alike(lors, og, opet, _tof_model(wl, tb))
+    lors, eta, s, tb = lors[keep], eta[keep], s[keep], tb[keep]
     sens, mult = _osem_inputs(pet, pp, opet, wl, mu, lors, eta, og)
     M, n_sub = wl.n_subsets, wl.n_subsets * wl.n_iters
     ref, rdiag = opet.lm_osem(lors, mult, s, sens, og, M, count=n_sub, tof=_otof(opet, wl, tb))
@@ -318,6 +340,7 @@ def test_tof_full_grid_sampled_lines(pet_mods, cuda):
     rng = np.random.Generator(np.random.PCG64(31))
     pick = np.sort(rng.choice(lors.shape[0], 2000, replace=False))
     og = opet.PetGeom(wl.shape, wl.voxel, rr_sigma_mm=np.float32(wl.rr_sigma_mm), rr_nsigma=3.0)
+    pick = pick[keep_alike(lors.cpu().numpy()[pick], og, opet, _tof_model(wl, tb.cpu().numpy()[pick]))]
     ref = opet.forward(act.cpu().numpy(), lors.cpu().numpy()[pick], og, mult.cpu().numpy()[pick],
                        tof=_otof(opet, wl, tb.cpu().numpy()[pick]))
     got = p.cpu().numpy()[pick]
@@ -335,6 +358,8 @@ def test_tof_bins_outside_the_range_and_bad_arguments(pet_mods, small_tof, cuda)
     wl, act, mu, lors, eta, s, tb, og = small_tof
     L = lors[:400]
     B = np.where(np.arange(400) % 2 == 0, -3, wl.tof_bins + 2).astype(np.int32)
+    keep = keep_alike(L, og, opet, _tof_model(wl, B))
+    L, B = L[keep], B[keep]
     plan = _plan(pet, wl, mu, cuda)
     got = plan.forward(_t(act, cuda), _t(L, cuda), tof_bin=_ti(B, cuda)).cpu().numpy()
     ref = opet.forward(act, L, og, tof=_otof(opet, wl, B))

@@ -63,7 +63,7 @@ def mixed_lors(seed, count=60, shape=SHAPE, voxel=VOXEL):
     return _f32(np.array(out))
 
 
-def test_planes_match_single_precision_reading():
+def test_planes_match_double_precision_reading():
     lors = mixed_lors(1)
     g = pet.PetGeom(SHAPE, VOXEL)
     got = pet.planes(lors, g)
@@ -305,3 +305,47 @@ def test_tof_listmode_em_equals_binned_mlem():
     ref = x0.ravel() * (H.T @ (y / (p + s_val))) / sens
     assert np.max(np.abs(x.ravel() - ref)) <= 1e-12 * np.max(np.abs(ref))
     assert abs(diag[0, 0] - np.sum(y * p / (p + s_val))) <= 1e-11 * diag[0, 0]
+
+
+def test_planes_are_decided_in_double_precision():
+    """An end 1e-9 voxel past plane 2 (below single precision's resolution
+    there) starts the walk at plane 3; an end exactly on plane 2 starts it at
+    plane 2; |dx| / vx a hair above |dy| / vy picks x."""
+    shape, voxel = (8, 8, 8), (2.0, 2.0, 2.0)
+    g = pet.PetGeom(shape, voxel)
+    org = -0.5 * (shape[0] - 1) * voxel[0]
+    x_on = org + 2 * voxel[0]
+    x_past = org + (2 + 1e-9) * voxel[0]
+    assert np.float32(x_past) == np.float32(x_on)
+    lors = np.array([[x_on, 0.3, 0.2, 100.0, 0.3, 0.2],
+                     [x_past, 0.3, 0.2, 100.0, 0.3, 0.2],
+                     [-50.0, -50.0 + 1e-9, 0.1, 50.0, 50.0, 0.1],
+                     [-50.0, -50.0 - 1e-9, 0.1, 50.0, 50.0, 0.1]])
+    got = pet.planes(lors, g)
+    assert tuple(got[0]) == (0, 2, 7)
+    assert tuple(got[1]) == (0, 3, 7)
+    assert got[2][0] == 0  # |dx| > |dy|
+    assert got[3][0] == 1  # |dy| > |dx|
+
+
+def test_precision_filter_flags_rounding_ties():
+    """The GPU tests leave out lines whose single-precision decisions differ
+    from the oracle's, from float32 ends as the kernel reads them: an end one
+    float32 step past a plane (p - org rounds onto the plane in float32),
+    and a near-45-degree line whose float32 |dx| and |dy| compare the other
+    way than in double precision."""
+    import pet_precision
+    shape, voxel = (8, 8, 8), (2.0, 2.0, 2.0)
+    g = pet.PetGeom(shape, voxel)
+    x_on = np.float32(-3.0)  # plane 2 of x: org = -7
+    x_past = np.nextafter(x_on, np.float32(1.0), dtype=np.float32)
+    lors = np.array([[x_on, 0.3, 0.2, 100.0, 0.3, 0.2],
+                     [x_past, 0.3, 0.2, 100.0, 0.3, 0.2],
+                     [-50.0, 0.7, 0.1, 50.0, 1.3, 0.1],
+                     [-57.94597625732422, -36.93305969238281, 0.1, 32.47325897216797, 53.48617935180664, 0.1]],
+                    dtype=np.float32)
+    ref = pet.planes(lors.astype(np.float64), g)
+    a, q0, q1, hit = pet_precision.kernel_decisions(lors, shape, voxel)
+    assert (ref[1][1], q0[1]) == (3, 2)
+    assert (ref[3][0], a[3]) == (1, 0)
+    assert pet_precision.same_decisions(lors, g, pet).tolist() == [True, False, True, False]
