@@ -123,6 +123,16 @@ int spect_plan_query(const spect_plan* plan, spect_plan_info* info);
  * bounded wait (SPECT_ETIMEDOUT; the flag is then cleared).  Synchronous. */
 int spect_plan_check(spect_plan* plan);
 
+/* Self-test of failure detection.  Every wait of the projector kernels on
+ * an asynchronous copy is bounded (about 4e9 SM cycles, ~2 s); when a wait
+ * runs out the kernel records SPECT_ETIMEDOUT in the plan's status word,
+ * leaves, and spect_plan_check reports it.  This call runs that path on
+ * purpose: a one-CTA kernel waits on a barrier that nothing arrives on,
+ * for limit_cycles SM cycles (1 .. 4e9), then records the timeout exactly
+ * like the projector kernels.  The context stays usable.  Asynchronous on
+ * `stream`.  (Not part of the paper's method.) */
+int spect_plan_selftest_timeout(spect_plan* plan, long long limit_cycles, void* stream);
+
 /* Number of angles of subset m (m == -1: all angles). */
 int spect_subset_size(const spect_plan* plan, int subset);
 
@@ -250,14 +260,18 @@ int spect_poisson_ll(spect_plan* plan, const float* y, const float* p, float s, 
  * returns SPECT_EINVAL and launches nothing).  Every GPU that loads the
  * library holds that array until the process exits.  The first call on a
  * device looks up the array's device address (with that device current);
- * make that first call before any stream capture.  The call itself makes no
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process: it does not survive cudaDeviceReset (or any
+ * other teardown of the device's primary context), after which this call
+ * must not be used.  The call itself makes no
  * allocation of any kind.  All calls on a device share the array: calls that
  * overlap on the GPU (different streams without ordering) race and give
  * wrong sums; calls ordered on one stream are safe.  Each call overwrites
  * every partial it reads, so nothing has to be cleared between calls.
  *
- * y, p, grad_proj: device float[count]; ll_dev: device double[1];
- * grad_proj may be NULL.  Asynchronous on `stream`. */
+ * y, p, grad_proj: device float[count], 16-byte aligned (else
+ * SPECT_EINVAL, as spect_poisson_ll); ll_dev: device double[1];
+ * grad_proj may be NULL; count 0 gives ll = 0.  Asynchronous on `stream`. */
 int spect_poisson_ll_noalloc(const float* y, const float* p, float s, size_t count, double* ll_dev,
                              float* grad_proj, void* stream);
 

@@ -8,6 +8,8 @@
 
 #include <cstdint>
 
+#include "spect.h"
+
 namespace spect {
 
 constexpr long long kWaitCycles = 4000000000LL;
@@ -25,7 +27,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 // Makes barrier initialisation visible to the async proxy (and the cluster).
 __device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// Wait until the phase of `bar` with the given parity has completed, for
+// at most `limit` SM clock cycles; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, long long limit)
 {
     const long long t0 = clock64();
     for (;;) {
@@ -36,8 +40,20 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
             : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) { return mbar_wait_for(bar, parity, kWaitCycles); }
+
+// A timed-out wait: one thread records SPECT_ETIMEDOUT in the status word
+// `err`; every thread of the CTA learns of it at this barrier (so that all
+// leave together).  Returns true when no thread timed out.
+__device__ __forceinline__ bool sync_ok(bool ok, int* err)
+{
+    const int bad = __syncthreads_or(!ok);
+    if (bad && threadIdx.x == 0 && err) atomicExch(err, SPECT_ETIMEDOUT);
+    return !bad;
 }
 
 // Arrive on `bar` and announce `bytes` of copies that complete on it.

@@ -211,6 +211,7 @@ constexpr int kReduceBlocks = 1024;  // largest grid of the reduction kernel
 cudaError_t launch_poisson_ll(const float* y, const float* p, float s, size_t count, double* block_part,
                               int n_blocks, double* ll, float* grad, cudaStream_t st);
 cudaError_t launch_fill(float* dst, size_t count, float value, cudaStream_t st);
+cudaError_t launch_wait_selftest(long long limit, int* err, cudaStream_t st);
 cudaError_t launch_update(float* x, const float* bp, const UpdateSpec& u, size_t count, cudaStream_t st);
 constexpr int kMaxPeaks = 8;
 cudaError_t launch_wsum(float* out, const float* const* in, const float* w, int terms, size_t count, cudaStream_t st);

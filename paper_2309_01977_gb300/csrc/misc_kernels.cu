@@ -1,6 +1,7 @@
 // Attenuation cache, FP64 count reductions and the Poisson likelihood.
 #include <cuda_runtime.h>
 
+#include "async_copy.cuh"
 #include "geometry.cuh"
 #include "internal.h"
 #include "update.cuh"
@@ -243,6 +244,30 @@ __global__ void fill_kernel(float* __restrict__ dst, size_t count, float value)
 {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
         dst[i] = value;
+}
+
+// Self-test of the bounded-wait path that every mbarrier wait of the
+// projector kernels takes: thread 0 waits on a barrier that nothing arrives
+// on, gives up after `limit` cycles, and the CTA reports SPECT_ETIMEDOUT
+// through the status word with the same helper as those kernels.  No copy
+// is in flight, so the CTA leaves at once.
+__global__ void wait_selftest_kernel(long long limit, int* err)
+{
+    __shared__ __align__(8) unsigned long long bar_word;
+    const uint32_t bar = smem_u32(&bar_word);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const bool ok = threadIdx.x == 0 ? mbar_wait_for(bar, 0, limit) : true;
+    sync_ok(ok, err);
+}
+
+cudaError_t launch_wait_selftest(long long limit, int* err, cudaStream_t st)
+{
+    wait_selftest_kernel<<<1, 64, 0, st>>>(limit, err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fill(float* dst, size_t count, float value, cudaStream_t st)

@@ -7,6 +7,7 @@
 // no cudaMalloc, cudaFree or allocating library routine.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <cstdio>
 #include <mutex>
 
@@ -55,13 +56,18 @@ __global__ void __launch_bounds__(kLlThreads) ll_partial_kernel(const float* __r
     if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
-__global__ void ll_total_kernel(const double* __restrict__ partials, int n_blocks, double* __restrict__ out)
+// Sum of the block partials in a fixed order: thread t adds partials t,
+// t + 256, t + 512, ... in turn, then the block reduction of
+// block_sum_f64.  The order depends only on n_blocks, so a given count
+// always gives bitwise the same total.  With n_blocks == 0 the total is 0.
+__global__ void __launch_bounds__(kLlThreads) ll_total_kernel(const double* __restrict__ partials, int n_blocks,
+                                                              double* __restrict__ out)
 {
-    if (threadIdx.x == 0) {
-        double total = 0.0;
-        for (int b = 0; b < n_blocks; ++b) total += partials[b];
-        out[0] = total;
-    }
+    __shared__ double red[kLlThreads / 32];
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < n_blocks; b += kLlThreads) acc += partials[b];
+    const double total = spect::block_sum_f64(acc, red);
+    if (threadIdx.x == 0) out[0] = total;
 }
 
 int noalloc_fail(int status, const char* msg)
@@ -76,6 +82,9 @@ extern "C" int spect_poisson_ll_noalloc(const float* y, const float* p, float s,
                                         float* grad_proj, void* stream)
 {
     if (!y || !p || !ll_dev) return noalloc_fail(SPECT_EINVAL, "y, p and ll must be device pointers");
+    const auto aligned16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+    if (!aligned16(y) || !aligned16(p) || (grad_proj && !aligned16(grad_proj)))
+        return noalloc_fail(SPECT_EINVAL, "y, p and grad must be 16-byte aligned");
     if (!(s == s) || s - s != 0.f) return noalloc_fail(SPECT_EINVAL, "s must be finite");
     if (count > kLlMaxCount) {
         char msg[160];
@@ -112,7 +121,7 @@ extern "C" int spect_poisson_ll_noalloc(const float* y, const float* p, float s,
     if (n_blocks > 0) ll_partial_kernel<<<n_blocks, kLlThreads, 0, st>>>(y, p, s, count, partials, grad_proj);
     e = cudaGetLastError();
     if (e == cudaSuccess) {
-        ll_total_kernel<<<1, 32, 0, st>>>(partials, n_blocks, ll_dev);
+        ll_total_kernel<<<1, kLlThreads, 0, st>>>(partials, n_blocks, ll_dev);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return noalloc_fail(SPECT_ECUDA, cudaGetErrorString(e));

@@ -385,15 +385,6 @@ __device__ __forceinline__ void load_atten_plane(uint32_t buf, const float* plan
     }
 }
 
-// A timed-out wait: one thread records it; every thread learns of it at
-// the barrier (so all leave together).
-__device__ __forceinline__ bool sync_ok(bool ok, int* err)
-{
-    const int bad = __syncthreads_or(!ok);
-    if (bad && threadIdx.x == 0 && err) atomicExch(err, SPECT_ETIMEDOUT);
-    return !bad;
-}
-
 template <int IPT>
 __global__ void __launch_bounds__(kFwdThreads, 1) forward_kernel(ForwardArgs a)
 {

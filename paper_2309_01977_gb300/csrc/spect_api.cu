@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "async_copy.cuh"
 #include "internal.h"
 
 using namespace spect;
@@ -1080,6 +1081,19 @@ int spect_plan_check(spect_plan* plan)
         cudaMemset(plan->d_err, 0, sizeof(int));
         return fail(err, "a kernel of this plan gave up a bounded wait (%s)", spect_status_str(err));
     }
+    return SPECT_OK;
+}
+
+int spect_plan_selftest_timeout(spect_plan* plan, long long limit_cycles, void* stream)
+{
+    if (int rc = check_plan(plan)) return rc;
+    if (limit_cycles < 1 || limit_cycles > kWaitCycles)
+        return fail(SPECT_EINVAL, "limit_cycles must be in [1, %lld]", (long long)kWaitCycles);
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = timed(plan, "wait_selftest", st, 1, [&] { return launch_wait_selftest(limit_cycles, plan->d_err, st); });
+    if (e != cudaSuccess) return cuda_fail(e, "self-test kernel launch");
     return SPECT_OK;
 }
 

@@ -47,7 +47,7 @@ EXPORTED = [
     "spect_status_str", "spect_last_error", "spect_version",
     "spect_profile_enable", "spect_profile_read", "spect_kernel_launches",
     "spect_poisson_ll_noalloc", "spect_plan_check", "spect_plan_set_mu", "spect_osem_run_dev",
-    "spect_map_run", "spect_prior_grad", "spect_multi_osem_run",
+    "spect_map_run", "spect_prior_grad", "spect_multi_osem_run", "spect_plan_selftest_timeout",
     "spect_serve_create", "spect_serve_submit", "spect_serve_poll", "spect_serve_wait",
     "spect_serve_cancel", "spect_serve_stats_get", "spect_serve_destroy",
 ]
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.spect_plan_destroy.argtypes = [vp]
         lib.spect_plan_query.argtypes = [vp, ctypes.POINTER(_PlanInfo)]
         lib.spect_plan_check.argtypes = [vp]
+        lib.spect_plan_selftest_timeout.argtypes = [vp, ctypes.c_longlong, vp]
         lib.spect_subset_size.argtypes = [vp, i]
         lib.spect_subset_angles.argtypes = [vp, i, ctypes.POINTER(ctypes.c_int)]
         lib.spect_forward.argtypes = [vp, vp, vp, i, i, vp]
@@ -232,6 +233,13 @@ def spect_plan_destroy(plan: int) -> None:
 def spect_plan_check(plan: int) -> None:
     """Raise if a kernel of the plan gave up a bounded wait (synchronises)."""
     _check(load().spect_plan_check(plan))
+
+
+def spect_plan_selftest_timeout(plan: int, limit_cycles: int, stream=None) -> None:
+    """Run the bounded-wait failure path once: a kernel waits on a barrier that
+    nothing arrives on for limit_cycles SM cycles and records SPECT_ETIMEDOUT
+    in the plan's status word (read it with spect_plan_check)."""
+    _check(load().spect_plan_selftest_timeout(plan, int(limit_cycles), _stream(stream)))
 
 
 def spect_plan_query(plan: int) -> dict:

@@ -10,6 +10,21 @@ def rel_l2(a, b) -> float:
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
 
 
+def max_abs_rel(a, b) -> float:
+    """max |a - b| over max |b|: an error localised in one tile or strip is
+    not diluted by the rest of the array, as it is in the relative L2."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def assert_close(got, ref, tol, what=""):
+    """Relative L2 within tol, and every element within 10 tol of max |ref|."""
+    e2, einf = rel_l2(got, ref), max_abs_rel(got, ref)
+    assert e2 <= tol, (what, "rel L2", e2)
+    assert einf <= 10 * tol, (what, "max abs / max |ref|", einf)
+
+
 def f32(a) -> np.ndarray:
     """Round to float32 and back, so that the oracle sees exactly the GPU's inputs."""
     return np.asarray(a, dtype=np.float32).astype(np.float64)

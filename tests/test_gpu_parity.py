@@ -1,7 +1,9 @@
 """GPU parity of libspect against the FP64 oracle (through the C ABI).
 
 Tolerances:
-  - projections and back projections: relative L2 <= 1e-5 (FP32 path);
+  - projections, back projections and sensitivities: relative L2 <= 1e-5
+    (FP32 path), and every element within 1e-4 of the largest reference
+    value (so that an error confined to one tile or strip shows);
   - adjointness <Hx, y> = <x, H^T y> in FP32: <= 1e-6 relative;
   - OSEM images: relative L2 <= 2e-5 after the full 2 x 8 and 4 x 8 runs
     (rounding of ~1e-7 per step compounds over the subiterations; the
@@ -17,7 +19,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import f32, oracle_geom, phantom_inputs, rel_l2
+from helpers import assert_close, f32, oracle_geom, phantom_inputs, rel_l2
 
 torch = pytest.importorskip("torch")
 
@@ -71,7 +73,7 @@ def test_forward_parity(spect_lib, oracle_mod, cuda, name):
         assert sel == (list(range(g.n_angles)) if subset < 0 else oracle_mod.subset_angles(g.n_angles, g.n_subsets, subset))
         p = plan.forward(_t(f, cuda), subset).cpu().numpy()
         ref = oracle_mod.forward(f, og, sel)
-        assert rel_l2(p, ref) <= TOL, (name, subset, rel_l2(p, ref))
+        assert_close(p, ref, TOL, (name, subset))
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -83,7 +85,7 @@ def test_back_parity(spect_lib, oracle_mod, cuda, name):
         q = f32(rng.uniform(0.0, 2.0, size=(len(sel), g.n, g.nz)))
         b = plan.back(_t(q, cuda), subset).cpu().numpy()
         ref = oracle_mod.back(q, og, sel)
-        assert rel_l2(b, ref) <= TOL, (name, subset, rel_l2(b, ref))
+        assert_close(b, ref, TOL, (name, subset))
 
 
 @pytest.mark.parametrize("name", ["ragged40x36", "osem64", "explicit_angles"])
@@ -107,10 +109,10 @@ def test_sensitivity_parity(spect_lib, oracle_mod, cuda, name):
         sel = oracle_mod.subset_angles(g.n_angles, g.n_subsets, m)
         s = plan.sensitivity(m).cpu().numpy()
         ref = oracle_mod.back(np.ones((len(sel), g.n, g.nz)), og, sel)
-        assert rel_l2(s, ref) <= TOL
+        assert_close(s, ref, TOL, (name, m))
     s_all = plan.sensitivity(-1).cpu().numpy()
     ref = oracle_mod.back(np.ones((g.n_angles, g.n, g.nz)), og)
-    assert rel_l2(s_all, ref) <= TOL
+    assert_close(s_all, ref, TOL, (name, "all"))
 
 
 def _osem_case(spect, oracle, dev, n, n_angles, iters, M, counts, seed):
@@ -137,8 +139,7 @@ def test_osem_parity_and_conservation(spect_lib, oracle_mod, cuda, n, n_angles, 
     total = iters * M
     diag = plan.osem(yd, s, x, 0, total, diag=True).cpu().numpy()
     ref, ref_diag = oracle_mod.osem(y, s, og, M, 0, total)
-    err = rel_l2(x.cpu().numpy(), ref)
-    assert err <= 2e-5, err
+    assert_close(x.cpu().numpy(), ref, 2e-5, "osem image")
     np.testing.assert_allclose(diag, ref_diag, rtol=2e-5)
     # conservation on the GPU: sum over S_m of H_m x_new equals sum y * p / (p + s)
     x2 = torch.ones((n, n, n), device=cuda)
@@ -185,10 +186,10 @@ def test_z_tiled_planes_192(spect_lib, oracle_mod, cuda):
     og = oracle_geom(oracle_mod, g, mu)
     sel = plan.subset_angles(3)
     p = plan.forward(_t(f, cuda), 3).cpu().numpy()
-    assert rel_l2(p, oracle_mod.forward(f, og, sel)) <= TOL
+    assert_close(p, oracle_mod.forward(f, og, sel), TOL, "forward 192")
     q = f32(np.random.Generator(np.random.PCG64(9)).uniform(size=(len(sel), 192, 192)))
     b = plan.back(_t(q, cuda), 3).cpu().numpy()
-    assert rel_l2(b, oracle_mod.back(q, og, sel)) <= TOL
+    assert_close(b, oracle_mod.back(q, og, sel), TOL, "back 192")
 
 
 def test_poisson_ll_and_gradient(spect_lib, oracle_mod, cuda):

@@ -28,8 +28,10 @@ def _inputs(count, seed, dev):
 def test_noalloc_matches_plan_entry_point_twice(spect_lib, cuda):
     g = spect_lib.Geometry(n=16, nz=16, n_angles=4, attenuation=False)
     plan = spect_lib.Plan(g)
-    # two calls in a row with different sizes and data
-    for count, seed, s in [(1_000_003, 1, 0.25), (262_144, 2, 0.1)]:
+    # calls in a row with different sizes and data: fewer blocks than the
+    # call before (stale partials beyond the count must be ignored), then
+    # more blocks again
+    for count, seed, s in [(1_000_003, 1, 0.25), (262_144, 2, 0.1), (3_000_001, 3, 0.5)]:
         y, p = _inputs(count, seed, cuda)
         ll_ref = torch.zeros(1, device=cuda, dtype=torch.float64)
         gr_ref = torch.empty_like(p)
@@ -56,3 +58,27 @@ def test_noalloc_rejects_counts_beyond_its_scratch(spect_lib, cuda):
     rc = lib.spect_poisson_ll_noalloc(y.data_ptr(), y.data_ptr(), 0.0, too_many, ll.data_ptr(), None, None)
     assert rc == spect_lib.SPECT_EINVAL
     assert b"exceeds" in lib.spect_last_error()
+
+
+def test_noalloc_empty_count_gives_zero(spect_lib, cuda):
+    """count 0: no partial block runs, the total of nothing is 0 (whatever an
+    earlier call left in the scratch)."""
+    y, p = _inputs(100_000, 4, cuda)
+    ll = torch.zeros(1, device=cuda, dtype=torch.float64)
+    spect_lib.spect_poisson_ll_noalloc(y, p, 0.25, ll, None)
+    ll0 = torch.full((1,), float("nan"), device=cuda, dtype=torch.float64)
+    lib = spect_lib.load()
+    rc = lib.spect_poisson_ll_noalloc(y.data_ptr(), p.data_ptr(), 0.25, 0, ll0.data_ptr(), None,
+                                      torch.cuda.current_stream().cuda_stream)
+    assert rc == spect_lib.SPECT_OK
+    torch.cuda.synchronize()
+    assert ll0.item() == 0.0
+
+
+def test_noalloc_rejects_misaligned_buffers(spect_lib, cuda):
+    lib = spect_lib.load()
+    y, p = _inputs(1000, 5, cuda)
+    ll = torch.zeros(1, device=cuda, dtype=torch.float64)
+    rc = lib.spect_poisson_ll_noalloc(y.data_ptr() + 4, p.data_ptr(), 0.25, 100, ll.data_ptr(), None, None)
+    assert rc == spect_lib.SPECT_EINVAL
+    assert b"aligned" in lib.spect_last_error()
