@@ -79,6 +79,15 @@ def _load():
             lib.or_prior_grad.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
             lib.or_set_orbit.restype = None
             lib.or_set_orbit.argtypes = [_dp, ctypes.c_int]
+            lib.or_set_trans.restype = None
+            lib.or_set_trans.argtypes = [_dp, ctypes.c_int]
+            lib.or_set_fov.restype = None
+            lib.or_set_fov.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            lib.or_rotate_shift.restype = None
+            lib.or_rotate_shift.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
+            lib.or_rotate_adjoint_shift.restype = None
+            lib.or_rotate_adjoint_shift.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                    _dp]
             lib.or_map.restype = None
             lib.or_map.argtypes = ([_dp, ctypes.c_double] + geom_args + [ctypes.c_int] * 5 +
                                    [ctypes.c_double] * 4 + [_dp])
@@ -111,6 +120,10 @@ class Geom:
     nsigma: truncation radius R_i = ceil(nsigma * sigma_i);
     det_offsets: optional per-angle detector offsets (a non-circular orbit):
     d_i(a) = n - i - 0.5 + det_offsets[a] replaces det_offset for angle a.
+    trans: optional per-angle shifts (voxels) of the rotated frame along the
+    detector's transaxial axis (T_trans, non-central projections).
+    fov: optional per-angle projection-space weights [n_angles][n][nz]
+    (T_fov, the field-of-view mask).
     """
 
     n: int
@@ -125,13 +138,25 @@ class Geom:
     nsigma: float = 3.0
     det_offset: float = 0.0
     det_offsets: Optional[Sequence[float]] = None
+    trans: Optional[Sequence[float]] = None
+    fov: Optional[np.ndarray] = None
 
     def _args(self):
-        # the orbit travels through the oracle's module state, set for every call
+        # the orbit, T_trans and T_fov travel through the oracle's module
+        # state, set for every call
         orb = None if self.det_offsets is None else _f64(self.det_offsets)
         if orb is not None:
             assert orb.size == self.n_angles
         _load().or_set_orbit(_ptr(orb), int(self.n_angles))
+        tr = None if self.trans is None else _f64(self.trans)
+        if tr is not None:
+            assert tr.size == self.n_angles
+        _load().or_set_trans(_ptr(tr), int(self.n_angles))
+        fv = None if self.fov is None else _f64(self.fov)
+        if fv is not None:
+            assert fv.shape == (self.n_angles, self.n, self.nz)
+        _load().or_set_fov(_ptr(fv), int(self.n_angles), int(self.n), int(self.nz))
+        self._keep_state = (orb, tr, fv)
         ang = None if self.angles is None else _f64(self.angles)
         mu = None if self.mu is None else _f64(self.mu).reshape(self.n, self.n, self.nz)
         self._keep = (ang, mu)  # keep the buffers alive for the call
@@ -167,19 +192,27 @@ def psf_taps(n, sigma0=0.5, slope=0.03, nsigma=3.0, det_offset=0.0):
     return sig, rad, taps
 
 
-def rotate(f, theta: float) -> np.ndarray:
+def rotate(f, theta: float, shift: float = 0.0) -> np.ndarray:
+    """T_trans T_rot: bilinear rotation by theta, the rotated frame shifted by
+    `shift` voxels along the detector's transaxial axis."""
     f = _f64(f)
     n, _, nz = f.shape
     out = np.empty_like(f)
-    _load().or_rotate(_ptr(f), n, nz, float(theta), _ptr(out))
+    if shift == 0.0:
+        _load().or_rotate(_ptr(f), n, nz, float(theta), _ptr(out))
+    else:
+        _load().or_rotate_shift(_ptr(f), n, nz, float(theta), float(shift), _ptr(out))
     return out
 
 
-def rotate_adjoint(v, theta: float) -> np.ndarray:
+def rotate_adjoint(v, theta: float, shift: float = 0.0) -> np.ndarray:
     v = _f64(v)
     n, _, nz = v.shape
     out = np.empty_like(v)
-    _load().or_rotate_adjoint(_ptr(v), n, nz, float(theta), _ptr(out))
+    if shift == 0.0:
+        _load().or_rotate_adjoint(_ptr(v), n, nz, float(theta), _ptr(out))
+    else:
+        _load().or_rotate_adjoint_shift(_ptr(v), n, nz, float(theta), float(shift), _ptr(out))
     return out
 
 

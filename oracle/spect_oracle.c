@@ -10,8 +10,11 @@
  * (SPECT_SM): H = sum_n v_n (x) ( T_fov P_x T_cdr T_att T_trans T_rot ).
  * Per angle n the object is rotated (T_rot), weighted by attenuation (T_att),
  * blurred plane by plane with a depth-dependent collimator-detector response
- * (T_cdr) and summed along +x (P_x).  T_trans and T_fov are identities here
- * (the paper gives no geometry for them).  The back projector is the literal
+ * (T_cdr) and summed along +x (P_x).  T_trans (non-central projections) is a
+ * per-angle shift of the rotated frame along the detector's transaxial axis,
+ * and T_fov a per-angle weight (mask) on the projection bins; both are
+ * optional module state (or_set_trans, or_set_fov) and identities when unset
+ * (the paper names them without giving their geometry).  The back projector is the literal
  * transpose of each step (the paper: back projection is H^T).  OSEM follows
  * Table 1 (OSEM row: preconditioner f / H_m^T 1, no prior) applied to the
  * Poisson gradient of Table 1 (H^T(g/(Hf+s)) - H^T 1), i.e. the classical
@@ -23,6 +26,15 @@
  *   - rotation centre c = (n-1)/2; rotated sample (i,j) reads f at
  *       u = c + cos(t)(i-c) - sin(t)(j-c),  v = c + sin(t)(i-c) + cos(t)(j-c)
  *     with bilinear weights and zero fill for taps outside the grid.
+ *   - T_trans of angle n: the rotated frame shifted by s_n voxels along +j
+ *     (the projection of the rotation axis lands s_n bins from the detector
+ *     centre): sample (i,j) reads the rotated object at (i, j - s_n), i.e.
+ *     j - c becomes j - s_n - c above, in one bilinear interpolation.  The
+ *     attenuation map goes through the same T_trans T_rot.
+ *   - T_fov of angle n: projection bin (j,k) multiplied by m_n[j][k] (1 in the
+ *     field of view, 0 outside, or any weight); the back projector applies
+ *     the same factor to its input (a diagonal operator is its own
+ *     transpose).
  *   - default angles theta_n = 2*pi*n / n_angles.
  *   - attenuation: detector on the +x side; with tau = voxel_cm * (R_n mu),
  *       A[i] = exp( -( sum_{i'>i} tau[i'] + tau[i]/2 ) )   (mid-voxel rule).
@@ -154,16 +166,18 @@ static void blur_plane(const double* in, double* out, double* tmp, int n, int nz
 
 /* ---------------------------------------------------------------- T_rot */
 
-/* Bilinear rotation (T_rot, Eq. 1): out[i][j][k] = f(u(i,j), v(i,j), k). */
-void or_rotate(const double* f, int n, int nz, double theta, double* out)
+/* Bilinear rotation and translation (T_trans T_rot, Eq. 1):
+ * out[i][j][k] = f(u(i,j), v(i,j), k) with j - c replaced by j - shift - c. */
+void or_rotate_shift(const double* f, int n, int nz, double theta, double shift, double* out)
 {
     double c = 0.5 * (double)(n - 1);
     double ct = cos(theta), st = sin(theta);
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) {
-            double u = c + ct * ((double)i - c) - st * ((double)j - c);
-            double v = c + st * ((double)i - c) + ct * ((double)j - c);
+            double dj = (double)j - shift - c;
+            double u = c + ct * ((double)i - c) - st * dj;
+            double v = c + st * ((double)i - c) + ct * dj;
             double fu = floor(u), fv = floor(v);
             int x0 = (int)fu, y0 = (int)fv;
             double a = u - fu, b = v - fv;
@@ -180,10 +194,16 @@ void or_rotate(const double* f, int n, int nz, double theta, double* out)
         }
 }
 
-/* Literal transpose of or_rotate: every weight of sample (i,j) is scattered
- * back to the tap it read.  out is overwritten.  Parallel over z only, so the
- * order of the scatter is the same for every thread count. */
-void or_rotate_adjoint(const double* in, int n, int nz, double theta, double* out)
+/* Bilinear rotation (T_rot, Eq. 1): out[i][j][k] = f(u(i,j), v(i,j), k). */
+void or_rotate(const double* f, int n, int nz, double theta, double* out)
+{
+    or_rotate_shift(f, n, nz, theta, 0.0, out);
+}
+
+/* Literal transpose of or_rotate_shift: every weight of sample (i,j) is
+ * scattered back to the tap it read.  out is overwritten.  Parallel over z
+ * only, so the order of the scatter is the same for every thread count. */
+void or_rotate_adjoint_shift(const double* in, int n, int nz, double theta, double shift, double* out)
 {
     double c = 0.5 * (double)(n - 1);
     double ct = cos(theta), st = sin(theta);
@@ -192,8 +212,9 @@ void or_rotate_adjoint(const double* in, int n, int nz, double theta, double* ou
     for (int k = 0; k < nz; ++k)
         for (int i = 0; i < n; ++i)
             for (int j = 0; j < n; ++j) {
-                double u = c + ct * ((double)i - c) - st * ((double)j - c);
-                double v = c + st * ((double)i - c) + ct * ((double)j - c);
+                double dj = (double)j - shift - c;
+                double u = c + ct * ((double)i - c) - st * dj;
+                double v = c + st * ((double)i - c) + ct * dj;
                 double fu = floor(u), fv = floor(v);
                 int x0 = (int)fu, y0 = (int)fv;
                 double a = u - fu, b = v - fv;
@@ -208,16 +229,21 @@ void or_rotate_adjoint(const double* in, int n, int nz, double theta, double* ou
             }
 }
 
+void or_rotate_adjoint(const double* in, int n, int nz, double theta, double* out)
+{
+    or_rotate_adjoint_shift(in, n, nz, theta, 0.0, out);
+}
+
 /* ---------------------------------------------------------------- T_att */
 
-/* Attenuation weights of angle theta in the rotated frame (T_att, Eq. 1):
- * A[i][j][k] = exp(-(sum_{i'>i} tau[i'][j][k] + tau[i][j][k]/2)),
- * tau = voxel_cm * (R_theta mu).  mu in 1/cm. */
-void or_attenuation(const double* mu, int n, int nz, double theta, double voxel_cm, double* A)
+/* Attenuation weights of angle theta in the rotated (and shifted) frame
+ * (T_att, Eq. 1): A[i][j][k] = exp(-(sum_{i'>i} tau[i'][j][k] + tau[i][j][k]/2)),
+ * tau = voxel_cm * (T_trans T_rot mu).  mu in 1/cm. */
+void or_attenuation_shift(const double* mu, int n, int nz, double theta, double shift, double voxel_cm, double* A)
 {
     size_t vol = (size_t)n * n * nz;
     double* m = (double*)malloc(sizeof(double) * vol);
-    or_rotate(mu, n, nz, theta, m);
+    or_rotate_shift(mu, n, nz, theta, shift, m);
 #pragma omp parallel for schedule(static)
     for (int j = 0; j < n; ++j)
         for (int k = 0; k < nz; ++k) {
@@ -229,6 +255,11 @@ void or_attenuation(const double* mu, int n, int nz, double theta, double voxel_
             }
         }
     free(m);
+}
+
+void or_attenuation(const double* mu, int n, int nz, double theta, double voxel_cm, double* A)
+{
+    or_attenuation_shift(mu, n, nz, theta, 0.0, voxel_cm, A);
 }
 
 /* ---------------------------------------------------------------- H, H^T */
@@ -249,6 +280,47 @@ void or_set_orbit(const double* det_offsets, int n_angles)
         memcpy(g_orbit, det_offsets, sizeof(double) * (size_t)n_angles);
         g_orbit_n = n_angles;
     }
+}
+
+/* T_trans: per-angle shift of the rotated frame along +j (voxels), or none.
+ * T_fov: per-angle projection-space weights [n_angles][n][nz], or none.
+ * Test infrastructure state, set by or_set_trans / or_set_fov. */
+static double* g_trans = NULL;
+static int g_trans_n = 0;
+static double* g_fov = NULL;
+static size_t g_fov_len = 0;
+
+void or_set_trans(const double* shifts, int n_angles)
+{
+    free(g_trans);
+    g_trans = NULL;
+    g_trans_n = 0;
+    if (shifts && n_angles > 0) {
+        g_trans = (double*)malloc(sizeof(double) * (size_t)n_angles);
+        memcpy(g_trans, shifts, sizeof(double) * (size_t)n_angles);
+        g_trans_n = n_angles;
+    }
+}
+
+void or_set_fov(const double* mask, int n_angles, int n, int nz)
+{
+    free(g_fov);
+    g_fov = NULL;
+    g_fov_len = 0;
+    if (mask && n_angles > 0) {
+        g_fov_len = (size_t)n_angles * n * nz;
+        g_fov = (double*)malloc(sizeof(double) * g_fov_len);
+        memcpy(g_fov, mask, sizeof(double) * g_fov_len);
+    }
+}
+
+static double trans_of(int angle) { return (g_trans && angle < g_trans_n) ? g_trans[angle] : 0.0; }
+
+/* T_fov weights of one angle ([n][nz]) or NULL. */
+static const double* fov_of(int angle, size_t plane)
+{
+    if (!g_fov || (size_t)(angle + 1) * plane > g_fov_len) return NULL;
+    return g_fov + (size_t)angle * plane;
 }
 
 typedef struct {
@@ -280,10 +352,11 @@ static void forward_one(const or_geom* g, const double* f, int angle, double* pr
         taps = own_taps;
         radius = own_rad;
     }
-    or_rotate(f, n, nz, theta, rot);                       /* T_rot */
+    const double shift = trans_of(angle);
+    or_rotate_shift(f, n, nz, theta, shift, rot);          /* T_trans T_rot */
     if (g->mu) {                                           /* T_att */
         double* A = (double*)malloc(sizeof(double) * vol);
-        or_attenuation(g->mu, n, nz, theta, g->voxel_cm, A);
+        or_attenuation_shift(g->mu, n, nz, theta, shift, g->voxel_cm, A);
         for (size_t q = 0; q < vol; ++q) rot[q] *= A[q];
         free(A);
     }
@@ -301,6 +374,9 @@ static void forward_one(const or_geom* g, const double* f, int angle, double* pr
     for (size_t q = 0; q < plane; ++q) proj[q] = 0.0;     /* P_x: sum along +x */
     for (int i = 0; i < n; ++i)
         for (size_t q = 0; q < plane; ++q) proj[q] += blurred[(size_t)i * plane + q];
+    const double* fov = fov_of(angle, plane);              /* T_fov */
+    if (fov)
+        for (size_t q = 0; q < plane; ++q) proj[q] *= fov[q];
     free(rot);
     free(blurred);
     free(own_taps);
@@ -308,14 +384,20 @@ static void forward_one(const or_geom* g, const double* f, int angle, double* pr
 }
 
 /* Per-angle back projection H_n^T q, ADDED into out: the transpose of each
- * step of forward_one in reverse order (broadcast over depth, blur (the
- * zero-padded symmetric Gaussian is self-adjoint), attenuate, rotate^T). */
-static void back_one(const or_geom* g, const double* q, int angle, double* out,
+ * step of forward_one in reverse order (the T_fov weights, broadcast over
+ * depth, blur (the zero-padded symmetric Gaussian is self-adjoint),
+ * attenuate, (T_trans T_rot)^T). */
+static void back_one(const or_geom* g, const double* q_in, int angle, double* out,
                      const double* taps, const int* radius, int rmax)
 {
     int n = g->n, nz = g->nz;
     size_t vol = (size_t)n * n * nz, plane = (size_t)n * nz;
     double theta = angle_of(angle, g->n_angles, g->angles);
+    const double shift = trans_of(angle);
+    const double* fov = fov_of(angle, plane);
+    double* qm = (double*)malloc(sizeof(double) * plane);
+    for (size_t p = 0; p < plane; ++p) qm[p] = fov ? fov[p] * q_in[p] : q_in[p];
+    const double* q = qm;
     double* b = (double*)malloc(sizeof(double) * vol);
     double* r = (double*)malloc(sizeof(double) * vol);
     double* own_taps = NULL;
@@ -341,12 +423,13 @@ static void back_one(const or_geom* g, const double* q, int angle, double* out,
     }
     if (g->mu) {
         double* A = (double*)malloc(sizeof(double) * vol);
-        or_attenuation(g->mu, n, nz, theta, g->voxel_cm, A);
+        or_attenuation_shift(g->mu, n, nz, theta, shift, g->voxel_cm, A);
         for (size_t p = 0; p < vol; ++p) b[p] *= A[p];
         free(A);
     }
-    or_rotate_adjoint(b, n, nz, theta, r);
+    or_rotate_adjoint_shift(b, n, nz, theta, shift, r);
     for (size_t p = 0; p < vol; ++p) out[p] += r[p];
+    free(qm);
     free(b);
     free(r);
     free(own_taps);

@@ -503,3 +503,59 @@ def test_rotation_keeps_a_constant_field_inside_the_grid(oracle_mod):
         outside = (u < -1) | (u > n) | (v < -1) | (v > n)
         assert np.all(out[outside] == 0.0)
         assert inside.sum() > n * n // 2
+
+
+# ---------------------------------------------------------------- T_trans and T_fov (Eq. 1)
+
+@pytest.mark.parametrize("theta, shift", [(0.3, 0.7), (1.1, -2.3), (2.5, 1.0), (4.0, -0.45), (5.9, 3.2)])
+def test_shifted_rotation_matches_scipy_affine(oracle_mod, theta, shift):
+    f = _rng(81).uniform(size=(13, 13, 5))
+    np.testing.assert_allclose(oracle_mod.rotate(f, theta, shift), brute.rotate_lib(f, theta, shift),
+                               rtol=0, atol=1e-13)
+
+
+def test_shifted_rotation_adjoint_dot(oracle_mod):
+    rng = _rng(82)
+    x = rng.normal(size=(11, 11, 3))
+    y = rng.normal(size=(11, 11, 3))
+    for theta, shift in ((0.7, 1.3), (2.0, -0.6), (3.3, 2.0)):
+        lhs = np.vdot(oracle_mod.rotate(x, theta, shift), y)
+        rhs = np.vdot(x, oracle_mod.rotate_adjoint(y, theta, shift))
+        assert abs(lhs - rhs) <= 1e-13 * (abs(lhs) + 1)
+
+
+def test_integer_shift_translates_the_projection(oracle_mod):
+    """theta = 0, no blur, no attenuation: a shift of 2 voxels moves every
+    projection bin by exactly 2 along j (zero where nothing arrives)."""
+    n, nz = 12, 4
+    f = _rng(83).uniform(size=(n, n, nz))
+    g0 = oracle_mod.Geom(n=n, nz=nz, n_angles=1, angles=[0.0], mu=None, use_psf=False)
+    g2 = oracle_mod.Geom(n=n, nz=nz, n_angles=1, angles=[0.0], mu=None, use_psf=False, trans=[2.0])
+    p0 = oracle_mod.forward(f, g0)[0]
+    p2 = oracle_mod.forward(f, g2)[0]
+    np.testing.assert_allclose(p2[2:], p0[:-2], rtol=1e-14, atol=0)
+    assert np.all(p2[:2] == 0.0)
+
+
+def test_brute_force_dense_h_with_trans_and_fov(oracle_mod):
+    """Per-angle shifts (T_trans) and projection-space weights (T_fov): the
+    oracle's H and H^T equal the library-built dense H at 8^3, 8 angles."""
+    n = nz = 8
+    rng = _rng(84)
+    mu = rng.uniform(0.0, 0.4, size=(n, n, nz))
+    angles = [2 * math.pi * a / 8 + 0.05 for a in range(8)]
+    shifts = list(rng.uniform(-2.0, 2.0, size=8))
+    fov = (rng.uniform(size=(8, n, nz)) > 0.25) * rng.uniform(0.5, 1.0, size=(8, n, nz))
+    kw = dict(voxel_cm=0.48, use_psf=True, sigma0=0.6, slope=0.15, nsigma=3.0)
+    H = brute.dense_h(n, nz, angles, mu, trans=shifts, fov=fov, **kw)
+    g = oracle_mod.Geom(n=n, nz=nz, n_angles=8, angles=angles, mu=mu, trans=shifts, fov=fov, **kw)
+    x = rng.uniform(size=(n, n, nz))
+    y = rng.uniform(size=(8, n, nz))
+    ref_hx = H @ x.ravel()
+    ref_hty = H.T @ y.ravel()
+    assert np.abs(oracle_mod.forward(x, g).ravel() - ref_hx).max() <= 1e-12 * np.abs(ref_hx).max()
+    assert np.abs(oracle_mod.back(y, g).ravel() - ref_hty).max() <= 1e-12 * np.abs(ref_hty).max()
+    # with both switched off the operator is the central, unmasked one
+    g0 = oracle_mod.Geom(n=n, nz=nz, n_angles=8, angles=angles, mu=mu, trans=[0.0] * 8, fov=np.ones((8, n, nz)), **kw)
+    g1 = oracle_mod.Geom(n=n, nz=nz, n_angles=8, angles=angles, mu=mu, **kw)
+    np.testing.assert_array_equal(oracle_mod.forward(x, g0), oracle_mod.forward(x, g1))
