@@ -4,9 +4,11 @@
  *
  * Method: PyTomography (arXiv 2309.01977).
  *   - Sec. 2.1.1, Eq. (1): H = sum_n v_n (x) (T_fov P_x T_cdr T_att T_trans T_rot);
- *     per projection angle n the volume is rotated (bilinear), weighted by
- *     attenuation, blurred plane by plane by a depth-dependent Gaussian and
- *     summed along the depth axis +x.  T_trans and T_fov are identities.
+ *     per projection angle n the volume is rotated (bilinear) and optionally
+ *     shifted along the detector axis (T_trans, non-central projections),
+ *     weighted by attenuation, blurred plane by plane by a depth-dependent
+ *     Gaussian, summed along the depth axis +x and optionally weighted by a
+ *     field-of-view mask in projection space (T_fov).
  *   - Sec. 2.1.1: forward projection is H f, back projection is H^T g.
  *   - Table 1: Poisson gradient H^T(g/(Hf+s)) - H^T 1 and the OSEM
  *     preconditioner f / (H_m^T 1), which give the update
@@ -17,7 +19,8 @@
  *
  * Conventions (the paper leaves them open; the library fixes them):
  *   volume   f[x][y][z], z fastest, nx == ny == n, float32, contiguous;
- *   rotation about c = (n-1)/2; angle theta_a = 2*pi*a/n_angles unless given;
+ *   rotation about c = (n-1)/2; angle theta_a = 2*pi*a/n_angles unless given
+ *            (its quarter turns with the exact cos, sin of 0 and +-1);
  *            rotated voxel (i, j) samples f at
  *              u = c + cos(t)(i-c) - sin(t)(j-c),  v = c + sin(t)(i-c) + cos(t)(j-c)
  *            bilinearly, zero outside the grid; i is depth, j the detector bin;
@@ -31,9 +34,21 @@
  *
  * Ownership: the caller owns every buffer it passes.  Device buffers are
  * float32, contiguous and 16-byte aligned, else SPECT_EINVAL.  A plan owns
- * its tables, attenuation cache, sensitivities and scratch.  Calls on one
- * plan share that scratch: issue them in one stream (or order them with
- * events); calls on different plans are independent.
+ * its tables, attenuation cache, sensitivities and scratch.
+ *
+ * Concurrency: after creation a plan's tables, attenuation cache and
+ * sensitivities are only read (spect_plan_set_mu is the exception: it
+ * rewrites them, so no other call on the plan may run at the same time).
+ * The plan keeps one set of scratch buffers per stream: the creation
+ * stream's at creation, another stream's at the first call on it (or at
+ * spect_plan_reserve_stream), so calls queued on different streams never
+ * share scratch and may run concurrently on the device; calls on one
+ * stream are ordered by the stream.  Calls from several host threads take
+ * the plan's lock while they queue their work.  A stream under graph
+ * capture cannot allocate: reserve its scratch before capturing (the
+ * creation stream has it already); a captured graph uses the scratch of
+ * the stream it was captured on, so replay it on that stream.  Calls on
+ * different plans are independent.
  *
  * Errors: every call returns SPECT_OK (0) or a negative status; nothing
  * aborts or throws across the ABI.  spect_last_error() gives a thread-local
@@ -88,6 +103,17 @@ typedef struct spect_geom {
                                  detector offset of each angle in voxels (replaces
                                  det_offset; each angle gets its own PSF table, T_cdr of
                                  Eq. 1 with d_i = n - i - 0.5 + det_offsets[a]) */
+    const float* det_shifts;  /* host array [n_angles] or NULL: T_trans of Eq. 1 (non-central
+                                 projections), the shift s_a in voxels of angle a's rotated
+                                 frame along the detector axis y (|s_a| <= 4 n): rotated
+                                 voxel (i, j) samples where the central geometry puts
+                                 (i, j - s_a), one bilinear interpolation (j - c becomes
+                                 j - s_a - c below); the attenuation map is shifted alike */
+    const float* fov_mask;    /* host array [n_angles][ny][nz] or NULL: T_fov of Eq. 1, a
+                                 weight (finite, >= 0; 1 inside the field of view, 0
+                                 outside) on every projection bin of every angle; the back
+                                 projection applies it to its input.  Copied at plan
+                                 creation. */
 } spect_geom;
 
 typedef struct spect_plan spect_plan;
@@ -122,6 +148,16 @@ int spect_plan_query(const spect_plan* plan, spect_plan_info* info);
 /* Wait for the device and report whether any kernel of this plan gave up a
  * bounded wait (SPECT_ETIMEDOUT; the flag is then cleared).  Synchronous. */
 int spect_plan_check(spect_plan* plan);
+
+/* Create this plan's scratch for `stream` now (a cudaMalloc; about one
+ * volume per angle of the largest subset, at least 16 volumes, plus the
+ * depth-chunk partials), so that later calls on the stream, including ones
+ * inside a graph capture, allocate nothing.  No-op when it exists. */
+int spect_plan_reserve_stream(spect_plan* plan, void* stream);
+
+/* Wait for `stream`, then free this plan's scratch for it (a later call on
+ * the stream creates it again).  No-op when the stream has none. */
+int spect_plan_release_stream(spect_plan* plan, void* stream);
 
 /* Self-test of failure detection.  Every wait of the projector kernels on
  * an asynchronous copy is bounded (about 4e9 SM cycles, ~2 s); when a wait

@@ -35,7 +35,8 @@
  *     field of view, 0 outside, or any weight); the back projector applies
  *     the same factor to its input (a diagonal operator is its own
  *     transpose).
- *   - default angles theta_n = 2*pi*n / n_angles.
+ *   - default angles theta_n = 2*pi*n / n_angles, with the exact cos and sin
+ *     (0, +-1) at quarter turns.
  *   - attenuation: detector on the +x side; with tau = voxel_cm * (R_n mu),
  *       A[i] = exp( -( sum_{i'>i} tau[i'] + tau[i]/2 ) )   (mid-voxel rule).
  *   - PSF: d_i = n - i - 0.5 + det_offset (voxels), or with a non-circular
@@ -72,11 +73,29 @@
 
 /* ---------------------------------------------------------------- angles */
 
-/* Projection angle theta_n (radians).  Default: uniform over 360 degrees. */
-static double angle_of(int n, int n_angles, const double* angles)
+/* cos and sin of projection angle theta_n: the given angle (radians), or by
+ * default theta_n = 2 pi n / n_angles, whose quarter turns (4 n a multiple
+ * of n_angles) have the exact values 0 and +-1 (the FP64 library values of
+ * cos(pi/2) and sin(pi) carry residues of ~1e-16, which would leak
+ * rounding-level bilinear weights into voxels the exact rotation does not
+ * reach). */
+static void angle_cs(int n, int n_angles, const double* angles, double* ct, double* st)
 {
-    if (angles) return angles[n];
-    return 2.0 * M_PI * (double)n / (double)n_angles;
+    if (angles) {
+        *ct = cos(angles[n]);
+        *st = sin(angles[n]);
+        return;
+    }
+    if ((4L * n) % n_angles == 0) {
+        static const double qc[4] = {1.0, 0.0, -1.0, 0.0}, qs[4] = {0.0, 1.0, 0.0, -1.0};
+        const int q = (int)((4L * n / n_angles) % 4);
+        *ct = qc[q];
+        *st = qs[q];
+        return;
+    }
+    const double theta = 2.0 * M_PI * (double)n / (double)n_angles;
+    *ct = cos(theta);
+    *st = sin(theta);
 }
 
 int or_n_threads(void)
@@ -168,10 +187,9 @@ static void blur_plane(const double* in, double* out, double* tmp, int n, int nz
 
 /* Bilinear rotation and translation (T_trans T_rot, Eq. 1):
  * out[i][j][k] = f(u(i,j), v(i,j), k) with j - c replaced by j - shift - c. */
-void or_rotate_shift(const double* f, int n, int nz, double theta, double shift, double* out)
+static void rotate_cs(const double* f, int n, int nz, double ct, double st, double shift, double* out)
 {
     double c = 0.5 * (double)(n - 1);
-    double ct = cos(theta), st = sin(theta);
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) {
@@ -194,6 +212,11 @@ void or_rotate_shift(const double* f, int n, int nz, double theta, double shift,
         }
 }
 
+void or_rotate_shift(const double* f, int n, int nz, double theta, double shift, double* out)
+{
+    rotate_cs(f, n, nz, cos(theta), sin(theta), shift, out);
+}
+
 /* Bilinear rotation (T_rot, Eq. 1): out[i][j][k] = f(u(i,j), v(i,j), k). */
 void or_rotate(const double* f, int n, int nz, double theta, double* out)
 {
@@ -203,10 +226,9 @@ void or_rotate(const double* f, int n, int nz, double theta, double* out)
 /* Literal transpose of or_rotate_shift: every weight of sample (i,j) is
  * scattered back to the tap it read.  out is overwritten.  Parallel over z
  * only, so the order of the scatter is the same for every thread count. */
-void or_rotate_adjoint_shift(const double* in, int n, int nz, double theta, double shift, double* out)
+static void rotate_adjoint_cs(const double* in, int n, int nz, double ct, double st, double shift, double* out)
 {
     double c = 0.5 * (double)(n - 1);
-    double ct = cos(theta), st = sin(theta);
     memset(out, 0, sizeof(double) * (size_t)n * n * nz);
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < nz; ++k)
@@ -229,6 +251,11 @@ void or_rotate_adjoint_shift(const double* in, int n, int nz, double theta, doub
             }
 }
 
+void or_rotate_adjoint_shift(const double* in, int n, int nz, double theta, double shift, double* out)
+{
+    rotate_adjoint_cs(in, n, nz, cos(theta), sin(theta), shift, out);
+}
+
 void or_rotate_adjoint(const double* in, int n, int nz, double theta, double* out)
 {
     or_rotate_adjoint_shift(in, n, nz, theta, 0.0, out);
@@ -239,11 +266,12 @@ void or_rotate_adjoint(const double* in, int n, int nz, double theta, double* ou
 /* Attenuation weights of angle theta in the rotated (and shifted) frame
  * (T_att, Eq. 1): A[i][j][k] = exp(-(sum_{i'>i} tau[i'][j][k] + tau[i][j][k]/2)),
  * tau = voxel_cm * (T_trans T_rot mu).  mu in 1/cm. */
-void or_attenuation_shift(const double* mu, int n, int nz, double theta, double shift, double voxel_cm, double* A)
+static void attenuation_cs(const double* mu, int n, int nz, double ct, double st, double shift, double voxel_cm,
+                           double* A)
 {
     size_t vol = (size_t)n * n * nz;
     double* m = (double*)malloc(sizeof(double) * vol);
-    or_rotate_shift(mu, n, nz, theta, shift, m);
+    rotate_cs(mu, n, nz, ct, st, shift, m);
 #pragma omp parallel for schedule(static)
     for (int j = 0; j < n; ++j)
         for (int k = 0; k < nz; ++k) {
@@ -255,6 +283,11 @@ void or_attenuation_shift(const double* mu, int n, int nz, double theta, double 
             }
         }
     free(m);
+}
+
+void or_attenuation_shift(const double* mu, int n, int nz, double theta, double shift, double voxel_cm, double* A)
+{
+    attenuation_cs(mu, n, nz, cos(theta), sin(theta), shift, voxel_cm, A);
 }
 
 void or_attenuation(const double* mu, int n, int nz, double theta, double voxel_cm, double* A)
@@ -339,7 +372,8 @@ static void forward_one(const or_geom* g, const double* f, int angle, double* pr
 {
     int n = g->n, nz = g->nz;
     size_t vol = (size_t)n * n * nz, plane = (size_t)n * nz;
-    double theta = angle_of(angle, g->n_angles, g->angles);
+    double ct, st;
+    angle_cs(angle, g->n_angles, g->angles, &ct, &st);
     double* rot = (double*)malloc(sizeof(double) * vol);
     double* blurred = (double*)malloc(sizeof(double) * vol);
     double* own_taps = NULL;
@@ -353,10 +387,10 @@ static void forward_one(const or_geom* g, const double* f, int angle, double* pr
         radius = own_rad;
     }
     const double shift = trans_of(angle);
-    or_rotate_shift(f, n, nz, theta, shift, rot);          /* T_trans T_rot */
+    rotate_cs(f, n, nz, ct, st, shift, rot);               /* T_trans T_rot */
     if (g->mu) {                                           /* T_att */
         double* A = (double*)malloc(sizeof(double) * vol);
-        or_attenuation_shift(g->mu, n, nz, theta, shift, g->voxel_cm, A);
+        attenuation_cs(g->mu, n, nz, ct, st, shift, g->voxel_cm, A);
         for (size_t q = 0; q < vol; ++q) rot[q] *= A[q];
         free(A);
     }
@@ -392,7 +426,8 @@ static void back_one(const or_geom* g, const double* q_in, int angle, double* ou
 {
     int n = g->n, nz = g->nz;
     size_t vol = (size_t)n * n * nz, plane = (size_t)n * nz;
-    double theta = angle_of(angle, g->n_angles, g->angles);
+    double ct, st;
+    angle_cs(angle, g->n_angles, g->angles, &ct, &st);
     const double shift = trans_of(angle);
     const double* fov = fov_of(angle, plane);
     double* qm = (double*)malloc(sizeof(double) * plane);
@@ -423,11 +458,11 @@ static void back_one(const or_geom* g, const double* q_in, int angle, double* ou
     }
     if (g->mu) {
         double* A = (double*)malloc(sizeof(double) * vol);
-        or_attenuation_shift(g->mu, n, nz, theta, shift, g->voxel_cm, A);
+        attenuation_cs(g->mu, n, nz, ct, st, shift, g->voxel_cm, A);
         for (size_t p = 0; p < vol; ++p) b[p] *= A[p];
         free(A);
     }
-    or_rotate_adjoint_shift(b, n, nz, theta, shift, r);
+    rotate_adjoint_cs(b, n, nz, ct, st, shift, r);
     for (size_t p = 0; p < vol; ++p) out[p] += r[p];
     free(qm);
     free(b);

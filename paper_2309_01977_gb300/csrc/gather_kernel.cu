@@ -3,7 +3,7 @@
 //
 // For angle a and voxel column q = (x, y), the rotated-grid samples p whose
 // bilinear footprint covers q lie in the box of half-width |cos|+|sin|
-// around c + R(-theta)(q - c).  The plan stores, per (angle, column), up to
+// around R(-theta)(q - c) + (c, cj) (cj: the angle's shifted detector centre).  The plan stores, per (angle, column), up to
 // kMaxCand (offset of p's row in a rotated-frame volume, weight) pairs, the
 // weight recomputed with the forward's own arithmetic so that it equals the
 // forward weight bit for bit.  A convex region of area 4 and perimeter 8
@@ -16,17 +16,17 @@
 
 namespace spect {
 
-__global__ void gather_table_kernel(const float2* __restrict__ cs_tab, int n, int nz, int2* __restrict__ tab)
+__global__ void gather_table_kernel(const float4* __restrict__ cs_tab, int n, int nz, int2* __restrict__ tab)
 {
     const int angle = blockIdx.y;
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= n * n) return;
     const int x = col / n, y = col - x * n;
     const float c = 0.5f * (float)(n - 1);
-    const float2 cs = cs_tab[angle];
+    const float4 cs = cs_tab[angle];
     const float dx = (float)x - c, dy = (float)y - c;
     const float pi = c + cs.x * dx + cs.y * dy;
-    const float pj = c - cs.y * dx + cs.x * dy;
+    const float pj = cs.z - cs.y * dx + cs.x * dy;
     const float ext = fabsf(cs.x) + fabsf(cs.y) + 1e-3f;
     const int ia = max(0, (int)ceilf(pi - ext)), ib = min(n - 1, (int)floorf(pi + ext));
     const int ja = max(0, (int)ceilf(pj - ext)), jb = min(n - 1, (int)floorf(pj + ext));
@@ -35,7 +35,7 @@ __global__ void gather_table_kernel(const float2* __restrict__ cs_tab, int n, in
     for (int i = ia; i <= ib; ++i)
         for (int j = ja; j <= jb; ++j) {
             float u, v;
-            sample_point(cs.x, cs.y, c, i, j, u, v);
+            sample_point(cs.x, cs.y, c, cs.z, i, j, u, v);
             const float fu = floorf(u), fv = floorf(v);
             const int xa = (int)fu, ya = (int)fv;
             const float ax = u - fu, by = v - fv;
@@ -49,7 +49,7 @@ __global__ void gather_table_kernel(const float2* __restrict__ cs_tab, int n, in
     for (; count < kMaxCand; ++count) out[count] = make_int2(0, 0);
 }
 
-cudaError_t launch_gather_tables(const float2* cs, int n, int nz, int n_angles, int2* tab, cudaStream_t st)
+cudaError_t launch_gather_tables(const float4* cs, int n, int nz, int n_angles, int2* tab, cudaStream_t st)
 {
     dim3 grid((n * n + 127) / 128, n_angles);
     gather_table_kernel<<<grid, 128, 0, st>>>(cs, n, nz, tab);

@@ -29,7 +29,7 @@ namespace spect {
 // ---------------------------------------------------------------- tables
 
 // One CTA per (tile, angle), one thread per column of the tile.
-__global__ void gather_tiled_table_kernel(const float2* __restrict__ cs_tab, int n, int nz, int T, int tiles_x,
+__global__ void gather_tiled_table_kernel(const float4* __restrict__ cs_tab, int n, int nz, int T, int tiles_x,
                                           int2* __restrict__ tab, int* __restrict__ desc, int* __restrict__ rows_max,
                                           int* __restrict__ err)
 {
@@ -55,17 +55,17 @@ __global__ void gather_tiled_table_kernel(const float2* __restrict__ cs_tab, int
     int count = 0;
     if (live) {
         const float c = 0.5f * (float)(n - 1);
-        const float2 cs = cs_tab[angle];
+        const float4 cs = cs_tab[angle];
         const float dx = (float)x - c, dy = (float)y - c;
         const float pi = c + cs.x * dx + cs.y * dy;
-        const float pj = c - cs.y * dx + cs.x * dy;
+        const float pj = cs.z - cs.y * dx + cs.x * dy;
         const float ext = fabsf(cs.x) + fabsf(cs.y) + 1e-3f;
         const int ia = max(0, (int)ceilf(pi - ext)), ib = min(n - 1, (int)floorf(pi + ext));
         const int ja = max(0, (int)ceilf(pj - ext)), jb = min(n - 1, (int)floorf(pj + ext));
         for (int i = ia; i <= ib; ++i)
             for (int j = ja; j <= jb; ++j) {
                 float u, v;
-                sample_point(cs.x, cs.y, c, i, j, u, v);
+                sample_point(cs.x, cs.y, c, cs.z, i, j, u, v);
                 const float fu = floorf(u), fv = floorf(v);
                 const int xa = (int)fu, ya = (int)fv;
                 const float ax = u - fu, by = v - fv;
@@ -121,7 +121,7 @@ __global__ void gather_tiled_table_kernel(const float2* __restrict__ cs_tab, int
     }
 }
 
-cudaError_t launch_gather_tiled_tables(const float2* cs, int n, int nz, int n_angles, int T, int2* tab, int* desc,
+cudaError_t launch_gather_tiled_tables(const float4* cs, int n, int nz, int n_angles, int T, int2* tab, int* desc,
                                        int* rows_max, int* err, cudaStream_t st)
 {
     const int tiles_x = (n + T - 1) / T;

@@ -6,15 +6,17 @@
 
 namespace spect {
 
-// Sample point of rotated voxel (i, j) for angle (ct, st) = (cos, sin):
-//   u = c + ct (i - c) - st (j - c),   v = c + st (i - c) + ct (j - c).
+// Sample point of rotated voxel (i, j) for angle (ct, st) = (cos, sin) and
+// the angle's centre cj = c + s of the shifted detector axis (T_trans of
+// Eq. 1; cj = c without a shift):
+//   u = c + ct (i - c) - st (j - cj),   v = c + st (i - c) + ct (j - cj).
 // Every kernel that needs the point of the same (angle, i, j) calls this
 // function, so the forward bilinear weights and the gathered transpose
 // weights are bitwise equal.
-__device__ __forceinline__ void sample_point(float ct, float st, float c, int i, int j, float& u, float& v)
+__device__ __forceinline__ void sample_point(float ct, float st, float c, float cj, int i, int j, float& u, float& v)
 {
     const float di = (float)i - c;
-    const float dj = (float)j - c;
+    const float dj = (float)j - cj;
     u = fmaf(ct, di, fmaf(-st, dj, c));
     v = fmaf(st, di, fmaf(ct, dj, c));
 }

@@ -6,6 +6,8 @@
 #include <stdint.h>
 
 #include <map>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -55,7 +57,7 @@ struct PlaneTiling {
 struct ForwardArgs {
     const float* x;        // [batch][n][n][nz]
     const float* atten;    // [n_angles][n][n][nz] or nullptr
-    const float2* cs;      // [n_angles] (cos, sin)
+    const float4* cs;      // [n_angles] (cos, sin, cj = c + T_trans shift, 0)
     const float* taps;     // [n][kTapW] centred at kMaxR
     const int* rad;        // [n]
     const int* work;       // [n+1] prefix sums of the per-plane work estimate
@@ -84,12 +86,14 @@ struct ReduceArgs {
     float s;
     float scale;           // forward-model scale a (multi-photopeak): r = a y / (a p + s); 1 otherwise
     const float* s_ptr;    // when not NULL, s is read from this device word
+    const float* fov;      // [n_angles][plane] T_fov weights applied to p, or nullptr
     double* diag_blocks;   // [gridDim.x][3] or nullptr: sums of (p+s), y, y*p/(p+s)
 };
 
 struct BlurBackArgs {
     const float* proj;     // first projection of the group, or nullptr for all-ones projections
     size_t proj_bstride;   // elements between batch entries of proj
+    const float* fov;      // [n_angles][n][nz] T_fov weights applied to proj, or nullptr
     const float* atten;    // [n_angles][n][n][nz] or nullptr
     const float* taps;
     const int* rad;
@@ -156,7 +160,7 @@ struct GatherTiledArgs {
 struct ForwardBf16Args {
     const float* x;
     const float* atten;
-    const float2* cs;
+    const float4* cs;
     const uint16_t* ttab;
     size_t ttab_stride;    // elements between the angles' Toeplitz tile sets (0: one set)
     const int* sel;
@@ -170,6 +174,7 @@ struct ForwardBf16Args {
 struct BlurBackBf16Args {
     const float* proj;
     size_t proj_bstride;
+    const float* fov;      // T_fov weights applied to proj, or nullptr
     const float* atten;
     const uint16_t* ttab;
     size_t ttab_stride;    // elements between the angles' Toeplitz tile sets (0: one set)
@@ -190,8 +195,8 @@ PlaneTiling plane_tiling(int n, int nz, int rmax, size_t cap, size_t limit);
 cudaError_t launch_forward(const ForwardArgs& a, int grid_x, cudaStream_t st);
 cudaError_t launch_blur_back(const BlurBackArgs& a, int grid_x, cudaStream_t st);
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t st);
-cudaError_t launch_gather_tables(const float2* cs, int n, int nz, int n_angles, int2* tab, cudaStream_t st);
-cudaError_t launch_gather_tiled_tables(const float2* cs, int n, int nz, int n_angles, int T, int2* tab, int* desc,
+cudaError_t launch_gather_tables(const float4* cs, int n, int nz, int n_angles, int2* tab, cudaStream_t st);
+cudaError_t launch_gather_tiled_tables(const float4* cs, int n, int nz, int n_angles, int T, int2* tab, int* desc,
                                        int* rows_max, int* err, cudaStream_t st);
 cudaError_t launch_gather_tiled(const GatherTiledArgs& a, cudaStream_t st);
 size_t gather_tiled_smem(int rows_cap, int zs, int T, int stages);
@@ -203,7 +208,7 @@ template <int IPT> int forward_occupancy_ipt(int threads, size_t smem);
 template <int IPT> cudaError_t blur_back_launch_ipt(const BlurBackArgs& a, int grid_x, cudaStream_t st);
 
 // misc kernels
-cudaError_t launch_attenuation(const float* mu, const float2* cs, int n, int nz, int n_angles,
+cudaError_t launch_attenuation(const float* mu, const float4* cs, int n, int nz, int n_angles,
                                float voxel_cm, int f64, float* atten, cudaStream_t st);
 cudaError_t launch_diag_finalize(const double* part, int n_part, double* out3, cudaStream_t st);
 cudaError_t launch_forward_reduce(const ReduceArgs& a, int blocks, cudaStream_t st);
@@ -225,6 +230,20 @@ void spect_internal_set_error(const char* msg);
 // Adds kernels launched outside spect_api.cu to spect_kernel_launches().
 void spect_internal_count_launches(unsigned long long kernels);
 
+// Scratch of the calls queued on one stream of a plan: calls on different
+// streams never share it, so they may run concurrently.
+struct spect_plan_scratch {
+    cudaStream_t stream = nullptr;
+    float* partials = nullptr;    // forward depth-chunk partials [partial_planes][n][nz]
+    float* bvol = nullptr;        // back-projection rotated-frame volumes [bvol_cap][vol]
+    float* ratio = nullptr;       // [max_subset][n][nz]
+    float* bp = nullptr;          // one volume: back projection of large subsets, other peaks
+    double* diag_part = nullptr;  // [kReduceBlocks][3]
+    double* ll_part = nullptr;    // poisson block partials [1024]
+    float* grad = nullptr;        // MAP: prior gradient (allocated by the first MAP call on the stream)
+    float* msens = nullptr;       // multi-photopeak: weighted subset sensitivity (first call)
+};
+
 struct spect_plan {
     spect_geom geom{};
     int n = 0, nz = 0, na = 0, M = 1;
@@ -239,34 +258,34 @@ struct spect_plan {
     int fwd_occ = 1;         // resident forward CTAs per SM
 
     // device memory
-    float2* d_cs = nullptr;
+    float4* d_cs = nullptr;                   // [na] (cos, sin, cj = c + T_trans shift, 0)
+    float* d_fov = nullptr;                   // [na][n][nz] T_fov weights, or none
     float* d_taps = nullptr;
     int* d_rad = nullptr;
     int* d_sel_all = nullptr;                 // [na] = 0..na-1
     std::vector<int*> d_sel;                  // per subset
     float* d_atten = nullptr;                 // [na][vol]
     float* d_sens = nullptr;                  // [M][vol]
-    float* d_partials = nullptr;              // forward depth-chunk partials
-    size_t partial_planes = 0;
+    size_t partial_planes = 0;                // capacity of a scratch's depth-chunk partials, planes
     int2* d_gtab = nullptr;                   // adjoint-rotation gather tables: [na][n*n][kMaxCand], or
                                               // tiled [na][gt_tiles][gt_T^2][kMaxCand]
     int* d_gdesc = nullptr;                   // tiled gather footprints [na][gt_tiles][kFpDescInts]
-    float* d_grad = nullptr;                  // MAP: prior gradient (allocated by the first MAP call)
-    float* d_msens = nullptr;                 // multi-photopeak: weighted subset sensitivity (first call)
     float* d_sens_all = nullptr;              // BSREM: H^T 1 over all angles (first BSREM call)
     bool sens_all_ok = false;                 // d_sens_all matches the current attenuation map
+    cudaEvent_t sens_all_ready = nullptr;     // recorded after d_sens_all was computed
+    cudaStream_t sens_all_stream = nullptr;   // the stream it was computed on
     int* d_gwork = nullptr;                   // tiled gather: largest footprint (rows)
     bool gather_tiled = false;                // footprints staged in shared memory
     int gt_T = 0, gt_tiles = 0, gt_zs = 0, gt_rows = 0, gt_stages = 2;
     bool bf16 = false;                        // tensor-core PSF path
     uint16_t* d_ttab = nullptr;               // [n][2][128*128] BF16 Toeplitz tiles (hi, lo)
     int* d_err = nullptr;                     // kernel status word (bounded waits)
-    float* d_bvol = nullptr;                  // back-projection rotated-frame volumes
-    size_t bvol_cap = 0;                      // capacity in volumes
-    float* d_ratio = nullptr;                 // [max_subset][n][nz]
-    float* d_bp = nullptr;                    // one volume: back projection of large subsets
-    double* d_diag_part = nullptr;            // [kReduceBlocks][3]
-    double* d_ll_part = nullptr;              // poisson block partials
+    size_t bvol_cap = 0;                      // capacity of a scratch's rotated-frame volumes
+    // per-stream scratch (the creation stream's first), and the lock every
+    // call holds while it reads or changes host-side plan state and queues
+    // its work
+    std::vector<std::unique_ptr<spect_plan_scratch>> scratch;
+    std::mutex mtx;
     size_t device_bytes = 0;
     size_t atten_bytes = 0;
     std::vector<void*> allocations;

@@ -43,7 +43,7 @@ struct RaySum {
 };
 }  // namespace
 
-__global__ void __launch_bounds__(256) attenuation_kernel(const float* __restrict__ mu, const float2* __restrict__ cs_tab,
+__global__ void __launch_bounds__(256) attenuation_kernel(const float* __restrict__ mu, const float4* __restrict__ cs_tab,
                                                           int n, int nz, float voxel_cm, int f64,
                                                           float* __restrict__ atten)
 {
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) attenuation_kernel(const float* __restric
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * zq) return;
     const int j = idx / zq, k = 4 * (idx - j * zq);
-    const float2 cs = cs_tab[angle];
+    const float4 cs = cs_tab[angle];
     const float c = 0.5f * (float)(n - 1);
     RaySum r[4];
     float4* out = reinterpret_cast<float4*>(atten + ((size_t)angle * n * n + j) * nz + k);
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) attenuation_kernel(const float* __restric
             const int i = i0 - s;
             if (i < 0) break;
             float u, v;
-            sample_point(cs.x, cs.y, c, i, j, u, v);
+            sample_point(cs.x, cs.y, c, cs.z, i, j, u, v);
             const float fu = floorf(u), fv = floorf(v);
             const int x0 = (int)fu, y0 = (int)fv;
             const float ax = u - fu, by = v - fv;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) attenuation_kernel(const float* __restric
     }
 }
 
-cudaError_t launch_attenuation(const float* mu, const float2* cs, int n, int nz, int n_angles, float voxel_cm, int f64,
+cudaError_t launch_attenuation(const float* mu, const float4* cs, int n, int nz, int n_angles, float voxel_cm, int f64,
                                float* atten, cudaStream_t st)
 {
     const int threads = 256;
@@ -123,8 +123,9 @@ cudaError_t launch_diag_finalize(const double* part, int n_part, double* out3, c
     return cudaGetLastError();
 }
 
-// Sum of the depth-chunk partial projections (chunk order, deterministic)
-// and, with y, the OSEM ratio r = y / (p + s) (0 where p + s == 0) and the
+// Sum of the depth-chunk partial projections (chunk order, deterministic),
+// times the T_fov weights of the angle when the plan has them, and, with y,
+// the OSEM ratio r = y / (p + s) (0 where p + s == 0) and the
 // FP64 count sums of (p + s), y and y * p / (p + s) per block.
 // The FP64 count sums run only when requested (kDiag): FP64 throughput on
 // GB300 is a small fraction of FP32.
@@ -159,6 +160,11 @@ __global__ void __launch_bounds__(256) forward_reduce_kernel(ReduceArgs a)
                     p.w += v[u].w;
                 }
             }
+        }
+        if (a.fov) {  // T_fov of the item's angle
+            const float4 m = __ldg(reinterpret_cast<const float4*>(a.fov) +
+                                   (size_t)a.sel[item % a.n_sel] * plane4 + off4);
+            p = make_float4(p.x * m.x, p.y * m.y, p.z * m.z, p.w * m.w);
         }
         float4 o = p;
         if (a.y) {

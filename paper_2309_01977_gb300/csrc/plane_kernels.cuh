@@ -267,11 +267,11 @@ struct TapRow {
     float w[4];
 };
 
-__device__ __forceinline__ void tap_rows(TapRow* rows, int n, int nz, int i, float2 cs, float c)
+__device__ __forceinline__ void tap_rows(TapRow* rows, int n, int nz, int i, float4 cs, float c)
 {
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         float u, v;
-        sample_point(cs.x, cs.y, c, i, j, u, v);
+        sample_point(cs.x, cs.y, c, cs.z, i, j, u, v);
         const float fu = floorf(u), fv = floorf(v);
         const int x0 = (int)fu, y0 = (int)fv;
         const float ax = u - fu, by = v - fv;
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) forward_kernel(ForwardArgs a)
     const int* rad_g = a.rad + (size_t)angle * a.rad_stride;
     const int* work_g = a.work + (size_t)angle * a.rad_stride;
     const int* bounds_g = a.bounds ? a.bounds + (size_t)angle * a.rad_stride : nullptr;
-    const float2 cs = a.cs[angle];
+    const float4 cs = a.cs[angle];
     const float c = 0.5f * (float)(n - 1);
     const int kt0 = tile * t.ktile;
     const int KT = min(t.ktile, nz - kt0);
@@ -613,8 +613,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1) blur_back_kernel(BlurBackArgs 
     const uint32_t bar = smem_u32(sm + t.off_bar_b);
 
     // The projection window of this angle (all ones without a projection),
-    // zero outside the detector.
+    // times the angle's T_fov weights when the plan has them, zero outside
+    // the detector.
     const float* pr = a.proj ? a.proj + (size_t)b * a.proj_bstride + (size_t)sidx * n * nz : nullptr;
+    const float* fv = a.fov ? a.fov + (size_t)angle * n * nz : nullptr;
     zero_pads(P, Q, t, nz, kw0);
     {
         // one quad (two rows, two columns) per item; four items of a thread
@@ -631,8 +633,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1) blur_back_kernel(BlurBackArgs 
                 for (int h = 0; h < 2; ++h) {
                     const int j = 2 * jp + h;
                     v[u][h] = make_float2(0.f, 0.f);
-                    if (it < items && j < n)
+                    if (it < items && j < n) {
                         v[u][h] = pr ? __ldg(reinterpret_cast<const float2*>(pr + (size_t)j * nz + k)) : make_float2(1.f, 1.f);
+                        if (fv) {
+                            const float2 m = __ldg(reinterpret_cast<const float2*>(fv + (size_t)j * nz + k));
+                            v[u][h] = make_float2(v[u][h].x * m.x, v[u][h].y * m.y);
+                        }
+                    }
                 }
             }
 #pragma unroll

@@ -254,11 +254,11 @@ struct TcTapRow {
     float w[4];
 };
 
-__device__ __forceinline__ void tc_tap_rows(TcTapRow* rows, int n, int nz, int i, float2 cs, float c)
+__device__ __forceinline__ void tc_tap_rows(TcTapRow* rows, int n, int nz, int i, float4 cs, float c)
 {
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         float u, v;
-        sample_point(cs.x, cs.y, c, i, j, u, v);
+        sample_point(cs.x, cs.y, c, cs.z, i, j, u, v);
         const float fu = floorf(u), fv = floorf(v);
         const int x0 = (int)fu, y0 = (int)fv;
         const float ax = u - fu, by = v - fv;
@@ -357,15 +357,23 @@ __device__ __forceinline__ void tc_prefetch_plane(const float* plane, int n, int
     for (int j = threadIdx.x; j < n; j += blockDim.x) prefetch_l2(plane + (size_t)j * nz, (uint32_t)nz * 4u);
 }
 
-// B1[j][k] = proj[j][k] (all ones when proj is NULL) for k < nz, as BF16 hi
-// and lo parts; lanes along k as above.
-__device__ __forceinline__ void tc_stage_proj(uint32_t b1, uint32_t b1_lo, const float* __restrict__ pr, int n, int nz)
+// B1[j][k] = proj[j][k] (all ones when proj is NULL) times the T_fov weight
+// fv[j][k] (when not NULL) for k < nz, as BF16 hi and lo parts; lanes along
+// k as above.
+__device__ __forceinline__ void tc_stage_proj(uint32_t b1, uint32_t b1_lo, const float* __restrict__ pr,
+                                              const float* __restrict__ fv, int n, int nz)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int k = 4 * lane;
     for (int j = warp; j < n; j += nw) {
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (k < nz) v = pr ? __ldg(reinterpret_cast<const float4*>(pr + (size_t)j * nz + k)) : make_float4(1.f, 1.f, 1.f, 1.f);
+        if (k < nz) {
+            v = pr ? __ldg(reinterpret_cast<const float4*>(pr + (size_t)j * nz + k)) : make_float4(1.f, 1.f, 1.f, 1.f);
+            if (fv) {
+                const float4 m = __ldg(reinterpret_cast<const float4*>(fv + (size_t)j * nz + k));
+                v = make_float4(v.x * m.x, v.y * m.y, v.z * m.z, v.w * m.w);
+            }
+        }
         put4(b1, b1_lo, j, k, n, v);
     }
 }
@@ -383,7 +391,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
     const int chunk = blockIdx.x, sidx = blockIdx.y, b = blockIdx.z;
     const int angle = a.sel[sidx];
     const uint16_t* ttab = a.ttab + (size_t)angle * a.ttab_stride;  // this angle's tiles
-    const float2 cs = a.cs[angle];
+    const float4 cs = a.cs[angle];
     const float c = 0.5f * (float)(n - 1);
     const uint32_t ncols = a.tmem_cols;
     TcState st;
@@ -499,7 +507,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
     if (i < n && a.atten) tc_prefetch_plane(a.atten + ((size_t)angle * n + i) * n * nz, n, nz);
     if (i < n && threadIdx.x == 0)
         tma_load_1d(st.s.tap, ttab + (size_t)i * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
-    tc_stage_proj(st.s.b1, st.s.b1_lo, pr, n, nz);
+    tc_stage_proj(st.s.b1, st.s.b1_lo, pr, a.fov ? a.fov + (size_t)angle * n * nz : nullptr, n, nz);
     fence_async_smem();
     if (i < n) {
         ok = all_ok(mbar_wait(st.s.bar_t, ph_t), a.err);

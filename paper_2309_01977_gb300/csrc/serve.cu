@@ -87,6 +87,8 @@ struct Request {
     spect_geom geom{};
     std::vector<double> angles;
     std::vector<float> offsets;  // non-circular orbit, or empty
+    std::vector<float> shifts;   // T_trans per angle, or empty
+    std::vector<float> fov;      // T_fov weights, or empty
     float s = 0.f;
     int n_iters = 0;
     uint64_t tag = 0;
@@ -105,7 +107,7 @@ struct Request {
 struct Slot {
     spect_geom geom{};
     std::vector<double> angles;
-    std::vector<float> offsets;
+    std::vector<float> offsets, shifts, fov;
     spect_plan* plan = nullptr;
     float* d_mu = nullptr;
     float* d_y = nullptr;
@@ -120,12 +122,13 @@ struct Slot {
     Request* req = nullptr;
 };
 
-bool same_geometry(const spect_geom& a, const std::vector<double>& aa, const std::vector<float>& ao,
-                   const spect_geom& b, const std::vector<double>& ba, const std::vector<float>& bo)
+bool same_geometry(const Slot& sl, const Request& r)
 {
+    const spect_geom &a = sl.geom, &b = r.geom;
     return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.voxel_cm == b.voxel_cm && a.n_angles == b.n_angles &&
            a.psf_sigma0 == b.psf_sigma0 && a.psf_slope == b.psf_slope && a.psf_nsigma == b.psf_nsigma &&
-           a.det_offset == b.det_offset && a.n_subsets == b.n_subsets && a.flags == b.flags && aa == ba && ao == bo;
+           a.det_offset == b.det_offset && a.n_subsets == b.n_subsets && a.flags == b.flags &&
+           sl.angles == r.angles && sl.offsets == r.offsets && sl.shifts == r.shifts && sl.fov == r.fov;
 }
 
 }  // namespace
@@ -171,6 +174,7 @@ size_t request_bytes(const spect_geom& g, int num_sms)
     const size_t tables = g.det_offsets ? na : 1;                        // PSF tables (orbit)
     if (g.flags & SPECT_FLAG_PSF_BF16) b += tables * n * 2 * 128 * 128 * 2;  // Toeplitz tiles
     b += tables * (n * 41 * 4 + spect::psf_int_stride((int)n) * 4);             // taps, radii, work, chunk bounds
+    if (g.fov_mask) b += na * plane * 4;                                 // T_fov weights
     b += 3 * vol * 4 + na * plane * 4;                                   // mu, x, y
     b += 1 << 20;                                                        // tables, small scratch
     return b;
@@ -198,6 +202,8 @@ int create_slot(spect_server* sv, Request* r, cudaStream_t st, Slot** out)
     sl->geom = r->geom;
     sl->angles = r->angles;
     sl->offsets = r->offsets;
+    sl->shifts = r->shifts;
+    sl->fov = r->fov;
     sl->vol = r->vol;
     sl->proj = r->proj;
     sl->bytes = r->bytes;
@@ -217,6 +223,8 @@ int create_slot(spect_server* sv, Request* r, cudaStream_t st, Slot** out)
     spect_geom g = sl->geom;
     g.angles_rad = sl->angles.empty() ? nullptr : sl->angles.data();
     g.det_offsets = sl->offsets.empty() ? nullptr : sl->offsets.data();
+    g.det_shifts = sl->shifts.empty() ? nullptr : sl->shifts.data();
+    g.fov_mask = sl->fov.empty() ? nullptr : sl->fov.data();
     int rc = spect_plan_create(&g, (g.flags & SPECT_FLAG_ATTEN) ? sl->d_mu : nullptr, st, &sl->plan);
     if (rc) {
         destroy_slot(sl);
@@ -311,7 +319,7 @@ void scheduler(spect_server* sv)
             }
             Slot* sl = nullptr;
             for (Slot* c : sv->slots)
-                if (!c->busy && same_geometry(c->geom, c->angles, c->offsets, r->geom, r->angles, r->offsets)) {
+                if (!c->busy && same_geometry(*c, *r)) {
                     sl = c;
                     break;
                 }
@@ -457,8 +465,12 @@ int spect_serve_submit(spect_server* sv, const spect_request* req, uint64_t* id)
     r->geom = g;
     r->geom.angles_rad = nullptr;
     r->geom.det_offsets = nullptr;
+    r->geom.det_shifts = nullptr;
+    r->geom.fov_mask = nullptr;
     if (g.angles_rad) r->angles.assign(g.angles_rad, g.angles_rad + g.n_angles);
     if (g.det_offsets) r->offsets.assign(g.det_offsets, g.det_offsets + g.n_angles);
+    if (g.det_shifts) r->shifts.assign(g.det_shifts, g.det_shifts + g.n_angles);
+    if (g.fov_mask) r->fov.assign(g.fov_mask, g.fov_mask + (size_t)g.n_angles * g.ny * g.nz);
     r->s = req->s;
     r->n_iters = req->n_iters;
     r->tag = req->tag;

@@ -174,6 +174,7 @@ void free_plan(spect_plan* p)
         cudaEventDestroy(r.stop);
     }
     for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+    if (p->sens_all_ready) cudaEventDestroy(p->sens_all_ready);
     for (void* a : p->allocations) cudaFree(a);
     delete p;
 }
@@ -279,15 +280,16 @@ int chunk_target(const spect_plan* p, long items)
 // depends on the subset size only (never on the batch), so a volume
 // projects to bitwise the same values alone or in a batch.  diag_blocks
 // (ratio mode only) receives per-block FP64 sums; *n_diag their count.
-int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, int n_sel, int batch, const float* y,
-                float s, double* diag_blocks, int* n_diag, cudaStream_t st, const float* s_ptr = nullptr,
-                float scale = 1.f)
+int run_forward(spect_plan* p, spect_plan_scratch& sc, const float* x, float* out, const int* sel_dev, int n_sel,
+                int batch, const float* y, float s, double* diag_blocks, int* n_diag, cudaStream_t st,
+                const float* s_ptr = nullptr, float scale = 1.f)
 {
     const PlaneTiling& t = p->tiling;
     // never more chunks than the partial buffer holds for one batch entry
     const int chunks = (int)std::min<size_t>(chunk_target(p, (long)n_sel * (p->bf16 ? 1 : t.ntiles)),
                                              std::max<size_t>(1, p->partial_planes / (size_t)n_sel));
-    const bool use_partials = chunks > 1 || y != nullptr;
+    // the reduction pass also applies T_fov
+    const bool use_partials = chunks > 1 || y != nullptr || p->d_fov != nullptr;
     const size_t vol = vol_elems(p), plane = plane_elems(p);
     int bper = batch;
     if (use_partials)
@@ -311,7 +313,7 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
             a.chunks = chunks;
             a.tmem_cols = bf16_tmem_cols(p->n);
             a.out = out + (size_t)b0 * n_sel * plane;
-            a.partials = use_partials ? p->d_partials : nullptr;
+            a.partials = use_partials ? sc.partials : nullptr;
             a.err = p->d_err;
             e = timed(p, "forward_bf16", st, 1, [&] { return launch_forward_bf16(a, st); });
         } else {
@@ -333,14 +335,14 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
             a.chunks = chunks;
             a.t = t;
             a.out = out + (size_t)b0 * n_sel * plane;
-            a.partials = use_partials ? p->d_partials : nullptr;
+            a.partials = use_partials ? sc.partials : nullptr;
             a.err = p->d_err;
             e = timed(p, "forward", st, 1, [&] { return launch_forward(a, chunks * t.ntiles, st); });
         }
         if (e != cudaSuccess) return cuda_fail(e, "forward kernel launch");
         if (!use_partials) continue;
         ReduceArgs r{};
-        r.partials = p->d_partials;
+        r.partials = sc.partials;
         r.chunks = chunks;
         r.items = nb * n_sel;
         r.n_sel = n_sel;
@@ -351,6 +353,7 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
         r.s = s;
         r.scale = scale;
         r.s_ptr = s_ptr;
+        r.fov = p->d_fov;
         r.diag_blocks = (y && diag_blocks) ? diag_blocks : nullptr;
         const size_t total4 = (size_t)r.items * plane / 4;
         const int blocks = (int)std::max<size_t>(1, std::min<size_t>(kReduceBlocks, (total4 + 255) / 256));
@@ -363,8 +366,8 @@ int run_forward(spect_plan* p, const float* x, float* out, const int* sel_dev, i
 
 // x_out (per batch entry) = sum over sel of H_a^T proj_a, optionally fused with
 // the OSEM update x_out <- x_out * bp / sens (then batch must be 1).
-int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev, int n_sel, int batch,
-             const UpdateSpec* upd, cudaStream_t st, bool accumulate = false)
+int run_back(spect_plan* p, spect_plan_scratch& sc, const float* proj, float* x_out, const int* sel_dev, int n_sel,
+             int batch, const UpdateSpec* upd, cudaStream_t st, bool accumulate = false)
 {
     const size_t vol = vol_elems(p), plane = plane_elems(p);
     const int gmax = (int)std::min<size_t>(16, p->bvol_cap);
@@ -375,7 +378,7 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
     const int G = std::min(gmax, n_sel);
     const int bper = std::max(1, std::min(batch, (int)(p->bvol_cap / G)));
     for (int b0 = 0; b0 < batch; b0 += bper) {
-        float* out_b = (upd && !fused) ? p->d_bp : x_out + (size_t)b0 * vol;
+        float* out_b = (upd && !fused) ? sc.bp : x_out + (size_t)b0 * vol;
         const int nb = std::min(bper, batch - b0);
         for (int g0 = 0; g0 < n_sel; g0 += G) {
             const int ng = std::min(G, n_sel - g0);
@@ -384,6 +387,7 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
                 BlurBackBf16Args bb{};
                 bb.proj = proj ? proj + ((size_t)b0 * n_sel + g0) * plane : nullptr;
                 bb.proj_bstride = (size_t)n_sel * plane;
+                bb.fov = p->d_fov;
                 bb.atten = p->d_atten;
                 bb.ttab = p->d_ttab;
                 bb.ttab_stride = p->psf_tables > 1 ? (size_t)p->n * 2 * kTcTile : 0;
@@ -394,13 +398,14 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
                 bb.batch = nb;
                 bb.chunks = chunk_target(p, (long)nb * ng);
                 bb.tmem_cols = bf16_tmem_cols(p->n);
-                bb.bvol = p->d_bvol;
+                bb.bvol = sc.bvol;
                 bb.err = p->d_err;
                 e = timed(p, "blur_back_bf16", st, 1, [&] { return launch_blur_back_bf16(bb, st); });
             } else {
                 BlurBackArgs bb{};
                 bb.proj = proj ? proj + ((size_t)b0 * n_sel + g0) * plane : nullptr;
                 bb.proj_bstride = (size_t)n_sel * plane;
+                bb.fov = p->d_fov;
                 bb.atten = p->d_atten;
                 bb.taps = p->d_taps;
                 bb.rad = p->d_rad;
@@ -416,14 +421,14 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
                 bb.t = p->tiling;
                 const int chunks = chunk_target(p, (long)nb * ng * p->tiling.ntiles);
                 bb.chunks = chunks;
-                bb.bvol = p->d_bvol;
+                bb.bvol = sc.bvol;
                 bb.err = p->d_err;
                 e = timed(p, "blur_back", st, 1, [&] { return launch_blur_back(bb, chunks * p->tiling.ntiles, st); });
             }
             if (e != cudaSuccess) return cuda_fail(e, "blur_back kernel launch");
             if (p->gather_tiled) {
                 GatherTiledArgs gt{};
-                gt.bvol = p->d_bvol;
+                gt.bvol = sc.bvol;
                 gt.tab = p->d_gtab;
                 gt.desc = p->d_gdesc;
                 gt.sel = sel_dev + g0;
@@ -445,7 +450,7 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
                 continue;
             }
             GatherArgs ga{};
-            ga.bvol = p->d_bvol;
+            ga.bvol = sc.bvol;
             ga.tab = p->d_gtab;
             ga.sel = sel_dev + g0;
             ga.n = p->n;
@@ -464,7 +469,7 @@ int run_back(spect_plan* p, const float* proj, float* x_out, const int* sel_dev,
             if (e != cudaSuccess) return cuda_fail(e, "gather kernel launch");
         }
         if (upd && !fused) {
-            cudaError_t e = timed(p, "update", st, 1, [&] { return launch_update(x_out + (size_t)b0 * vol, p->d_bp, *upd, vol, st); });
+            cudaError_t e = timed(p, "update", st, 1, [&] { return launch_update(x_out + (size_t)b0 * vol, sc.bp, *upd, vol, st); });
             if (e != cudaSuccess) return cuda_fail(e, "update kernel launch");
         }
     }
@@ -475,6 +480,54 @@ int check_plan(const spect_plan* p)
 {
     if (!p) return fail(SPECT_EINVAL, "plan is NULL");
     return SPECT_OK;
+}
+
+// The scratch of the calls on stream st, created (cudaMalloc) by the first
+// call on st.  The caller holds p->mtx and has made the plan's device
+// current.  A stream under capture cannot allocate: its scratch has to
+// exist before the capture begins.
+int scratch_for(spect_plan* p, cudaStream_t st, spect_plan_scratch** out)
+{
+    *out = nullptr;
+    for (auto& s : p->scratch)
+        if (s->stream == st) {
+            *out = s.get();
+            return SPECT_OK;
+        }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusNone;
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(SPECT_ESTATE, "the stream is being captured and this plan has no scratch for it yet: call "
+                                  "spect_plan_reserve_stream (or any call on the stream) before the capture");
+    std::unique_ptr<spect_plan_scratch> s(new (std::nothrow) spect_plan_scratch());
+    if (!s) return fail(SPECT_ENOMEM, "host allocation failed");
+    s->stream = st;
+    const size_t vol = vol_elems(p), plane = plane_elems(p);
+    int rc;
+    if ((rc = dev_alloc(p, &s->partials, p->partial_planes * plane)) ||
+        (rc = dev_alloc(p, &s->bvol, p->bvol_cap * vol)) ||
+        (rc = dev_alloc(p, &s->ratio, (size_t)p->max_subset * plane)) ||
+        (rc = dev_alloc(p, &s->bp, vol)) ||
+        (rc = dev_alloc(p, &s->diag_part, (size_t)kReduceBlocks * 3)) ||
+        (rc = dev_alloc(p, &s->ll_part, 1024)))
+        return rc;  // what was allocated stays on the plan's list and is freed with it
+    *out = s.get();
+    p->scratch.push_back(std::move(s));
+    return SPECT_OK;
+}
+
+// Free one device allocation of the plan (a released stream's scratch).
+void dev_free(spect_plan* p, void* ptr, size_t bytes)
+{
+    if (!ptr) return;
+    auto it = std::find(p->allocations.begin(), p->allocations.end(), ptr);
+    if (it == p->allocations.end()) return;
+    p->allocations.erase(it);
+    p->device_bytes -= bytes;
+    cudaFree(ptr);
 }
 
 int subset_of(const spect_plan* p, int subset, const int** sel_dev, int* n_sel)
@@ -500,24 +553,27 @@ int osem_core(spect_plan* plan, const float* y, float s, const float* s_dev, flo
     DeviceGuard guard(plan->device);
     if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lock(plan->mtx);
+    spect_plan_scratch* sc;
+    if (int rc = scratch_for(plan, st, &sc)) return rc;
     const size_t vol = vol_elems(plan);
     for (int t = first_subiter; t < first_subiter + n_subiters; ++t) {
         const int m = t % plan->M;
         const int ns = (int)plan->subsets[m].size();
         int n_diag = 0;
-        int rc = run_forward(plan, x_inout, plan->d_ratio, plan->d_sel[m], ns, 1, y, s,
-                             diag_dev ? plan->d_diag_part : nullptr, &n_diag, st, s_dev);
+        int rc = run_forward(plan, *sc, x_inout, sc->ratio, plan->d_sel[m], ns, 1, y, s,
+                             diag_dev ? sc->diag_part : nullptr, &n_diag, st, s_dev);
         if (rc) return rc;
         if (diag_dev) {
             cudaError_t e = timed(plan, "diag", st, 1, [&] {
-                return launch_diag_finalize(plan->d_diag_part, n_diag, diag_dev + 3 * (size_t)(t - first_subiter), st);
+                return launch_diag_finalize(sc->diag_part, n_diag, diag_dev + 3 * (size_t)(t - first_subiter), st);
             });
             if (e != cudaSuccess) return cuda_fail(e, "diag kernel launch");
         }
         UpdateSpec u{};
         u.mode = kUpdOsem;
         u.sens = plan->d_sens + (size_t)m * vol;
-        rc = run_back(plan, plan->d_ratio, x_inout, plan->d_sel[m], ns, 1, &u, st);
+        rc = run_back(plan, *sc, sc->ratio, x_inout, plan->d_sel[m], ns, 1, &u, st);
         if (rc) return rc;
     }
     return SPECT_OK;
@@ -544,20 +600,35 @@ int map_core(spect_plan* plan, const float* y, float s, float* x_inout, int firs
     DeviceGuard guard(plan->device);
     if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t vol = vol_elems(plan);
+    std::lock_guard<std::mutex> lock(plan->mtx);
+    spect_plan_scratch* sc;
     int rc;
-    if (!plan->d_grad && ((rc = dev_alloc(plan, &plan->d_grad, vol)))) return rc;
+    if ((rc = scratch_for(plan, st, &sc))) return rc;
+    const size_t vol = vol_elems(plan);
+    if (!sc->grad && ((rc = dev_alloc(plan, &sc->grad, vol)))) return rc;
     if (mp->algorithm == SPECT_ALG_BSREM && !plan->sens_all_ok) {
+        // H^T 1 over all angles, once per attenuation map, on this stream;
+        // calls on other streams wait for it through an event
         if (!plan->d_sens_all && ((rc = dev_alloc(plan, &plan->d_sens_all, vol)))) return rc;
-        rc = run_back(plan, nullptr, plan->d_sens_all, plan->d_sel_all, plan->na, 1, nullptr, st);
+        if (!plan->sens_all_ready) {
+            cudaError_t e = cudaEventCreateWithFlags(&plan->sens_all_ready, cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(e, "create event");
+        }
+        rc = run_back(plan, *sc, nullptr, plan->d_sens_all, plan->d_sel_all, plan->na, 1, nullptr, st);
         if (rc) return rc;
+        cudaError_t e = cudaEventRecord(plan->sens_all_ready, st);
+        if (e != cudaSuccess) return cuda_fail(e, "record event");
+        plan->sens_all_stream = st;
         plan->sens_all_ok = true;
+    } else if (mp->algorithm == SPECT_ALG_BSREM && plan->sens_all_stream != st) {
+        cudaError_t e = cudaStreamWaitEvent(st, plan->sens_all_ready, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "wait for H^T 1");
     }
     const float c = 1.f / (float)plan->M;
     for (int t = first_subiter; t < first_subiter + n_subiters; ++t) {
         const int m = t % plan->M;
         const int ns = (int)plan->subsets[m].size();
-        rc = run_forward(plan, x_inout, plan->d_ratio, plan->d_sel[m], ns, 1, y, s, nullptr, nullptr, st);
+        rc = run_forward(plan, *sc, x_inout, sc->ratio, plan->d_sel[m], ns, 1, y, s, nullptr, nullptr, st);
         if (rc) return rc;
         UpdateSpec u{};
         u.mode = mp->algorithm == SPECT_ALG_OSMAPOSL ? kUpdOsl : kUpdBsrem;
@@ -565,16 +636,16 @@ int map_core(spect_plan* plan, const float* y, float s, float* x_inout, int firs
         u.beta_n = mp->beta * c;
         if (mp->prior != SPECT_PRIOR_NONE) {
             cudaError_t e = timed(plan, "prior_grad", st, 1, [&] {
-                return launch_prior_grad(x_inout, plan->d_grad, plan->n, plan->nz, mp->prior, mp->delta, mp->gamma, st);
+                return launch_prior_grad(x_inout, sc->grad, plan->n, plan->nz, mp->prior, mp->delta, mp->gamma, st);
             });
             if (e != cudaSuccess) return cuda_fail(e, "prior gradient kernel");
-            u.grad = plan->d_grad;
+            u.grad = sc->grad;
         }
         if (u.mode == kUpdBsrem) {
             u.sens_all = plan->d_sens_all;
             u.step = mp->alpha0 / (1.f + (float)(t / plan->M)) / c;
         }
-        rc = run_back(plan, plan->d_ratio, x_inout, plan->d_sel[m], ns, 1, &u, st);
+        rc = run_back(plan, *sc, sc->ratio, x_inout, plan->d_sel[m], ns, 1, &u, st);
         if (rc) return rc;
     }
     return SPECT_OK;
@@ -609,28 +680,41 @@ int multi_core(spect_plan* const* plans, const float* scales, int P, const float
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t vol = vol_elems(p0);
     int rc;
-    if (!p0->d_msens && ((rc = dev_alloc(p0, &p0->d_msens, vol)))) return rc;
+    // each peak's scratch of this stream; the plans are locked one at a time
+    // (never two together), around the host work of each step
+    spect_plan_scratch* sc[kMaxPeaks];
+    for (int n = 0; n < P; ++n) {
+        std::lock_guard<std::mutex> lock(plans[n]->mtx);
+        if ((rc = scratch_for(plans[n], st, &sc[n]))) return rc;
+        if (n == 0 && !sc[0]->msens && ((rc = dev_alloc(p0, &sc[0]->msens, vol)))) return rc;
+    }
     for (int t = first; t < first + count; ++t) {
         const int m = t % p0->M;
         const int ns = (int)p0->subsets[m].size();
         const float* sens[kMaxPeaks];
         for (int n = 0; n < P; ++n) {
-            rc = run_forward(plans[n], x, plans[n]->d_ratio, plans[n]->d_sel[m], ns, 1, y[n], s[n], nullptr, nullptr,
+            std::lock_guard<std::mutex> lock(plans[n]->mtx);
+            rc = run_forward(plans[n], *sc[n], x, sc[n]->ratio, plans[n]->d_sel[m], ns, 1, y[n], s[n], nullptr, nullptr,
                              st, nullptr, scales[n]);
             if (rc) return rc;
             sens[n] = plans[n]->d_sens + (size_t)m * vol;
         }
-        cudaError_t e = timed(p0, "sens_sum", st, 1, [&] { return launch_wsum(p0->d_msens, sens, scales, P, vol, st); });
-        if (e != cudaSuccess) return cuda_fail(e, "weighted sum kernel");
+        {
+            std::lock_guard<std::mutex> lock(p0->mtx);
+            cudaError_t e = timed(p0, "sens_sum", st, 1, [&] { return launch_wsum(sc[0]->msens, sens, scales, P, vol, st); });
+            if (e != cudaSuccess) return cuda_fail(e, "weighted sum kernel");
+        }
         for (int n = 0; n + 1 < P; ++n) {
-            rc = run_back(plans[n], plans[n]->d_ratio, p0->d_bp, plans[n]->d_sel[m], ns, 1, nullptr, st, n > 0);
+            std::lock_guard<std::mutex> lock(plans[n]->mtx);
+            rc = run_back(plans[n], *sc[n], sc[n]->ratio, sc[0]->bp, plans[n]->d_sel[m], ns, 1, nullptr, st, n > 0);
             if (rc) return rc;
         }
         UpdateSpec u{};
         u.mode = kUpdOsem;
-        u.sens = p0->d_msens;
-        u.bp_add = P > 1 ? p0->d_bp : nullptr;
-        rc = run_back(plans[P - 1], plans[P - 1]->d_ratio, x, plans[P - 1]->d_sel[m], ns, 1, &u, st);
+        u.sens = sc[0]->msens;
+        u.bp_add = P > 1 ? sc[0]->bp : nullptr;
+        std::lock_guard<std::mutex> lock(plans[P - 1]->mtx);
+        rc = run_back(plans[P - 1], *sc[P - 1], sc[P - 1]->ratio, x, plans[P - 1]->d_sel[m], ns, 1, &u, st);
         if (rc) return rc;
     }
     return SPECT_OK;
@@ -638,7 +722,7 @@ int multi_core(spect_plan* const* plans, const float* scales, int P, const float
 
 // Attenuation cache A_a (T_att) from mu and the per-subset sensitivities
 // H_m^T 1 (compute_normalization_factor); queued on st.
-int refresh_mu(spect_plan* p, const float* mu_dev, cudaStream_t st)
+int refresh_mu(spect_plan* p, spect_plan_scratch& sc, const float* mu_dev, cudaStream_t st)
 {
     const size_t vol = vol_elems(p);
     if (p->d_atten) {
@@ -649,8 +733,8 @@ int refresh_mu(spect_plan* p, const float* mu_dev, cudaStream_t st)
         if (e != cudaSuccess) return cuda_fail(e, "attenuation kernel");
     }
     for (int m = 0; m < p->M; ++m) {
-        const int rc = run_back(p, nullptr, p->d_sens + (size_t)m * vol, p->d_sel[m], (int)p->subsets[m].size(), 1,
-                                nullptr, st);
+        const int rc = run_back(p, sc, nullptr, p->d_sens + (size_t)m * vol, p->d_sel[m], (int)p->subsets[m].size(),
+                                1, nullptr, st);
         if (rc) return rc;
     }
     return SPECT_OK;
@@ -723,6 +807,8 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     p->geom = g;
     p->geom.angles_rad = nullptr;
     p->geom.det_offsets = nullptr;
+    p->geom.det_shifts = nullptr;
+    p->geom.fov_mask = nullptr;
     p->n = g.nx;
     p->nz = g.nz;
     p->na = g.n_angles;
@@ -736,14 +822,35 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
         return cuda_fail(e, "cudaDeviceGetAttribute");
     }
 
-    // angles and their FP32 cos/sin (computed in FP64)
+    // angles: FP32 cos, sin (computed in FP64; exact 0 and +-1 at the
+    // quarter turns of the default angles 2 pi a / n_angles, where the FP64
+    // library values carry ~1e-16 residues) and the centre of the angle's
+    // detector axis, c + the T_trans shift
     p->angles.resize(p->na);
-    std::vector<float2> cs(p->na);
+    std::vector<float4> cs(p->na);
     for (int a = 0; a < p->na; ++a) {
         const double th = g.angles_rad ? g.angles_rad[a] : 2.0 * M_PI * (double)a / (double)p->na;
         if (!std::isfinite(th)) { free_plan(p); return fail(SPECT_EINVAL, "angle %d is not finite", a); }
+        const double sh = g.det_shifts ? (double)g.det_shifts[a] : 0.0;
+        if (!std::isfinite(sh) || std::fabs(sh) > 4.0 * p->n)
+            { free_plan(p); return fail(SPECT_EINVAL, "detector shift %d is not finite or beyond 4 n", a); }
         p->angles[a] = th;
-        cs[a] = make_float2((float)std::cos(th), (float)std::sin(th));
+        double ct = std::cos(th), st = std::sin(th);
+        if (!g.angles_rad && (4L * a) % p->na == 0) {
+            static const double qc[4] = {1.0, 0.0, -1.0, 0.0}, qs[4] = {0.0, 1.0, 0.0, -1.0};
+            const int q = (int)((4L * a / p->na) % 4);
+            ct = qc[q];
+            st = qs[q];
+        }
+        cs[a] = make_float4((float)ct, (float)st, (float)(0.5 * (double)(p->n - 1) + sh), 0.f);
+    }
+    if (g.fov_mask) {
+        const size_t cnt = (size_t)p->na * p->n * p->nz;
+        for (size_t q = 0; q < cnt; ++q)
+            if (!std::isfinite(g.fov_mask[q]) || g.fov_mask[q] < 0.f) {
+                free_plan(p);
+                return fail(SPECT_EINVAL, "fov_mask[%zu] is not a finite value >= 0", q);
+            }
     }
     // PSF tables: one per angle for a non-circular orbit, else one
     std::vector<float> taps;
@@ -782,13 +889,7 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
         (rc = dev_alloc(p, &p->d_rad, (size_t)p->psf_tables * psf_int_stride(p->n))) ||
         (rc = dev_alloc(p, &p->d_sel_all, (size_t)p->na)) ||
         (rc = dev_alloc(p, &p->d_sens, (size_t)p->M * vol)) ||
-        (rc = dev_alloc(p, &p->d_partials, p->partial_planes * plane)) ||
         (rc = dev_alloc(p, &p->d_gwork, 1)) ||
-        (rc = dev_alloc(p, &p->d_bvol, p->bvol_cap * vol)) ||
-        (rc = dev_alloc(p, &p->d_ratio, (size_t)p->max_subset * plane)) ||
-        (rc = dev_alloc(p, &p->d_bp, vol)) ||
-        (rc = dev_alloc(p, &p->d_diag_part, (size_t)kReduceBlocks * 3)) ||
-        (rc = dev_alloc(p, &p->d_ll_part, 1024)) ||
         (rc = dev_alloc(p, &p->d_err, 1))) {
         free_plan(p);
         return rc;
@@ -818,7 +919,12 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
             build_toeplitz_bf16(g, p->n, g.det_offsets ? (double)g.det_offsets[a] : (double)g.det_offset, ttab);
         if ((rc = dev_alloc(p, &p->d_ttab, ttab.size()))) { free_plan(p); return rc; }
     }
-    SPECT_CK(cudaMemcpyAsync(p->d_cs, cs.data(), cs.size() * sizeof(float2), cudaMemcpyHostToDevice, st), "copy angles");
+    SPECT_CK(cudaMemcpyAsync(p->d_cs, cs.data(), cs.size() * sizeof(float4), cudaMemcpyHostToDevice, st), "copy angles");
+    if (g.fov_mask) {
+        if ((rc = dev_alloc(p, &p->d_fov, (size_t)p->na * plane))) { cudaStreamSynchronize(st); free_plan(p); return rc; }
+        SPECT_CK(cudaMemcpyAsync(p->d_fov, g.fov_mask, (size_t)p->na * plane * sizeof(float), cudaMemcpyHostToDevice, st),
+                 "copy field-of-view weights");
+    }
     SPECT_CK(cudaMemsetAsync(p->d_err, 0, sizeof(int), st), "clear status");
     if (p->bf16)
         SPECT_CK(cudaMemcpyAsync(p->d_ttab, ttab.data(), ttab.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st),
@@ -896,7 +1002,10 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     for (int m = 0; m < p->M; ++m)
         SPECT_CK(cudaMemcpyAsync(p->d_sel[m], p->subsets[m].data(), p->subsets[m].size() * sizeof(int),
                                  cudaMemcpyHostToDevice, st), "copy subsets");
-    rc = refresh_mu(p, mu_dev, st);
+    // the creation stream's scratch, then A_a and the sensitivities
+    spect_plan_scratch* sc = nullptr;
+    rc = scratch_for(p, st, &sc);
+    if (!rc) rc = refresh_mu(p, *sc, mu_dev, st);
     if (rc) { cudaStreamSynchronize(st); free_plan(p); return rc; }
     SPECT_CK(cudaStreamSynchronize(st), "plan creation");
     SPECT_CK(cudaGetLastError(), "plan creation");
@@ -964,7 +1073,11 @@ int spect_forward(spect_plan* plan, const float* x, float* proj, int subset, int
     if (int rc = subset_of(plan, subset, &sel, &ns)) return rc;
     DeviceGuard guard(plan->device);
     if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
-    return run_forward(plan, x, proj, sel, ns, batch, nullptr, 0.f, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lock(plan->mtx);
+    spect_plan_scratch* sc;
+    if (int rc = scratch_for(plan, st, &sc)) return rc;
+    return run_forward(plan, *sc, x, proj, sel, ns, batch, nullptr, 0.f, nullptr, nullptr, st);
 }
 
 int spect_back(spect_plan* plan, const float* proj, float* x_out, int subset, int batch, void* stream)
@@ -978,7 +1091,11 @@ int spect_back(spect_plan* plan, const float* proj, float* x_out, int subset, in
     if (int rc = subset_of(plan, subset, &sel, &ns)) return rc;
     DeviceGuard guard(plan->device);
     if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
-    return run_back(plan, proj, x_out, sel, ns, batch, nullptr, static_cast<cudaStream_t>(stream));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lock(plan->mtx);
+    spect_plan_scratch* sc;
+    if (int rc = scratch_for(plan, st, &sc)) return rc;
+    return run_back(plan, *sc, proj, x_out, sel, ns, batch, nullptr, st);
 }
 
 int spect_sensitivity(spect_plan* plan, int subset, float* out, void* stream)
@@ -998,7 +1115,10 @@ int spect_sensitivity(spect_plan* plan, int subset, float* out, void* stream)
         if (e != cudaSuccess) return cuda_fail(e, "copy sensitivity");
         return SPECT_OK;
     }
-    return run_back(plan, nullptr, out, sel, ns, 1, nullptr, st);
+    std::lock_guard<std::mutex> lock(plan->mtx);
+    spect_plan_scratch* sc;
+    if (int rc = scratch_for(plan, st, &sc)) return rc;
+    return run_back(plan, *sc, nullptr, out, sel, ns, 1, nullptr, st);
 }
 
 int spect_osem_run(spect_plan* plan, const float* y, float s, float* x_inout, int first_subiter, int n_subiters,
@@ -1022,8 +1142,12 @@ int spect_plan_set_mu(spect_plan* plan, const float* mu_dev, void* stream)
         return fail(SPECT_EINVAL, "the plan models attenuation: mu must be a 16-byte aligned device pointer");
     DeviceGuard guard(plan->device);
     if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lock(plan->mtx);
+    spect_plan_scratch* sc;
+    if (int rc = scratch_for(plan, st, &sc)) return rc;
     plan->sens_all_ok = false;  // BSREM's H^T 1 follows the attenuation map
-    return refresh_mu(plan, mu_dev, static_cast<cudaStream_t>(stream));
+    return refresh_mu(plan, *sc, mu_dev, st);
 }
 
 int spect_map_run(spect_plan* plan, const float* y, float s, float* x_inout, int first_subiter, int n_subiters,
@@ -1063,17 +1187,58 @@ int spect_poisson_ll(spect_plan* plan, const float* y, const float* p, float s, 
     if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
     const int blocks = (int)std::max<size_t>(1, std::min<size_t>(1024, (count + 255) / 256));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lock(plan->mtx);
+    spect_plan_scratch* sc;
+    if (int rc = scratch_for(plan, st, &sc)) return rc;
     cudaError_t e = timed(plan, "poisson_ll", st, 2, [&] {
-        return launch_poisson_ll(y, p, s, count, plan->d_ll_part, blocks, ll_dev, grad_proj, st);
+        return launch_poisson_ll(y, p, s, count, sc->ll_part, blocks, ll_dev, grad_proj, st);
     });
     if (e != cudaSuccess) return cuda_fail(e, "poisson kernel launch");
     return SPECT_OK;
+}
+
+int spect_plan_reserve_stream(spect_plan* plan, void* stream)
+{
+    if (int rc = check_plan(plan)) return rc;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
+    std::lock_guard<std::mutex> lock(plan->mtx);
+    spect_plan_scratch* sc;
+    return scratch_for(plan, static_cast<cudaStream_t>(stream), &sc);
+}
+
+int spect_plan_release_stream(spect_plan* plan, void* stream)
+{
+    if (int rc = check_plan(plan)) return rc;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lock(plan->mtx);
+    for (size_t k = 0; k < plan->scratch.size(); ++k) {
+        spect_plan_scratch* s = plan->scratch[k].get();
+        if (s->stream != st) continue;
+        cudaError_t e = cudaStreamSynchronize(st);  // its last use has finished
+        if (e != cudaSuccess) return cuda_fail(e, "synchronize the released stream");
+        const size_t vol = vol_elems(plan), plane = plane_elems(plan);
+        dev_free(plan, s->partials, plan->partial_planes * plane * sizeof(float));
+        dev_free(plan, s->bvol, plan->bvol_cap * vol * sizeof(float));
+        dev_free(plan, s->ratio, (size_t)plan->max_subset * plane * sizeof(float));
+        dev_free(plan, s->bp, vol * sizeof(float));
+        dev_free(plan, s->diag_part, (size_t)kReduceBlocks * 3 * sizeof(double));
+        dev_free(plan, s->ll_part, 1024 * sizeof(double));
+        dev_free(plan, s->grad, vol * sizeof(float));
+        dev_free(plan, s->msens, vol * sizeof(float));
+        plan->scratch.erase(plan->scratch.begin() + (long)k);
+        return SPECT_OK;
+    }
+    return SPECT_OK;  // the stream had no scratch
 }
 
 int spect_plan_check(spect_plan* plan)
 {
     if (int rc = check_plan(plan)) return rc;
     DeviceGuard guard(plan->device);
+    std::lock_guard<std::mutex> lock(plan->mtx);
     int err = 0;
     cudaError_t e = cudaMemcpy(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "read kernel status");
@@ -1092,6 +1257,7 @@ int spect_plan_selftest_timeout(spect_plan* plan, long long limit_cycles, void* 
     DeviceGuard guard(plan->device);
     if (!guard.ok) return fail(SPECT_ECUDA, "cannot select the plan's device");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lock(plan->mtx);
     cudaError_t e = timed(plan, "wait_selftest", st, 1, [&] { return launch_wait_selftest(limit_cycles, plan->d_err, st); });
     if (e != cudaSuccess) return cuda_fail(e, "self-test kernel launch");
     return SPECT_OK;
@@ -1100,6 +1266,7 @@ int spect_plan_selftest_timeout(spect_plan* plan, long long limit_cycles, void* 
 int spect_profile_enable(spect_plan* plan, int on)
 {
     if (int rc = check_plan(plan)) return rc;
+    std::lock_guard<std::mutex> lock(plan->mtx);
     plan->prof = on != 0;
     return SPECT_OK;
 }
@@ -1109,6 +1276,7 @@ int spect_profile_read(spect_plan* plan, spect_kernel_time* out, int max_entries
     if (int rc = check_plan(plan)) return rc;
     if (max_entries < 0 || (max_entries > 0 && !out)) return fail(SPECT_EINVAL, "bad output array");
     DeviceGuard guard(plan->device);
+    std::lock_guard<std::mutex> lock(plan->mtx);
     for (auto& r : plan->pending) {
         cudaError_t e = cudaEventSynchronize(r.stop);
         float ms = 0.f;

@@ -48,6 +48,7 @@ EXPORTED = [
     "spect_profile_enable", "spect_profile_read", "spect_kernel_launches",
     "spect_poisson_ll_noalloc", "spect_plan_check", "spect_plan_set_mu", "spect_osem_run_dev",
     "spect_map_run", "spect_prior_grad", "spect_multi_osem_run", "spect_plan_selftest_timeout",
+    "spect_plan_reserve_stream", "spect_plan_release_stream",
     "spect_serve_create", "spect_serve_submit", "spect_serve_poll", "spect_serve_wait",
     "spect_serve_cancel", "spect_serve_stats_get", "spect_serve_destroy",
 ]
@@ -75,6 +76,8 @@ class _Geom(ctypes.Structure):
         ("n_subsets", ctypes.c_int),
         ("flags", ctypes.c_uint),
         ("det_offsets", ctypes.POINTER(ctypes.c_float)),
+        ("det_shifts", ctypes.POINTER(ctypes.c_float)),
+        ("fov_mask", ctypes.POINTER(ctypes.c_float)),
     ]
 
 
@@ -111,6 +114,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.spect_plan_query.argtypes = [vp, ctypes.POINTER(_PlanInfo)]
         lib.spect_plan_check.argtypes = [vp]
         lib.spect_plan_selftest_timeout.argtypes = [vp, ctypes.c_longlong, vp]
+        lib.spect_plan_reserve_stream.argtypes = [vp, vp]
+        lib.spect_plan_release_stream.argtypes = [vp, vp]
         lib.spect_subset_size.argtypes = [vp, i]
         lib.spect_subset_angles.argtypes = [vp, i, ctypes.POINTER(ctypes.c_int)]
         lib.spect_forward.argtypes = [vp, vp, vp, i, i, vp]
@@ -187,6 +192,8 @@ class Geometry:
     psf_bf16: bool = False
     angles_rad: Optional[Sequence[float]] = None
     det_offsets: Optional[Sequence[float]] = None  # per-angle detector offsets (non-circular orbit)
+    det_shifts: Optional[Sequence[float]] = None   # per-angle shifts along the detector axis (T_trans)
+    fov_mask: Optional[object] = None              # [n_angles][n][nz] projection weights (T_fov)
 
     def to_c(self):
         g = _Geom()
@@ -205,6 +212,19 @@ class Geometry:
             arr = (ctypes.c_float * len(self.det_offsets))(*[float(v) for v in self.det_offsets])
             keep.append(arr)
             g.det_offsets = ctypes.cast(arr, ctypes.POINTER(ctypes.c_float))
+        if self.det_shifts is not None:
+            if len(self.det_shifts) != self.n_angles:
+                raise SpectError(SPECT_EINVAL, "det_shifts needs one value per angle")
+            arr = (ctypes.c_float * len(self.det_shifts))(*[float(v) for v in self.det_shifts])
+            keep.append(arr)
+            g.det_shifts = ctypes.cast(arr, ctypes.POINTER(ctypes.c_float))
+        if self.fov_mask is not None:
+            import numpy as np
+            m = np.ascontiguousarray(np.asarray(self.fov_mask, dtype=np.float32))
+            if m.shape != (self.n_angles, self.n, self.nz):
+                raise SpectError(SPECT_EINVAL, "fov_mask must be [n_angles][n][nz]")
+            keep.append(m)
+            g.fov_mask = m.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         g.psf_sigma0 = float(self.psf_sigma0)
         g.psf_slope = float(self.psf_slope)
         g.psf_nsigma = float(self.psf_nsigma)
@@ -240,6 +260,16 @@ def spect_plan_selftest_timeout(plan: int, limit_cycles: int, stream=None) -> No
     nothing arrives on for limit_cycles SM cycles and records SPECT_ETIMEDOUT
     in the plan's status word (read it with spect_plan_check)."""
     _check(load().spect_plan_selftest_timeout(plan, int(limit_cycles), _stream(stream)))
+
+
+def spect_plan_reserve_stream(plan: int, stream=None) -> None:
+    """Create the plan's scratch for `stream` now (before a graph capture on it)."""
+    _check(load().spect_plan_reserve_stream(plan, _stream(stream)))
+
+
+def spect_plan_release_stream(plan: int, stream=None) -> None:
+    """Wait for `stream` and free the plan's scratch for it."""
+    _check(load().spect_plan_release_stream(plan, _stream(stream)))
 
 
 def spect_plan_query(plan: int) -> dict:

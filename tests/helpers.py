@@ -37,9 +37,30 @@ def oracle_geom(oracle, g, mu64):
                        use_psf=g.psf, sigma0=float(np.float32(g.psf_sigma0)),
                        slope=float(np.float32(g.psf_slope)), nsigma=float(np.float32(g.psf_nsigma)),
                        det_offset=float(np.float32(g.det_offset)),
-                       det_offsets=None if g.det_offsets is None else [float(np.float32(v)) for v in g.det_offsets])
+                       det_offsets=None if g.det_offsets is None else [float(np.float32(v)) for v in g.det_offsets],
+                       trans=None if g.det_shifts is None else [float(np.float32(v)) for v in g.det_shifts],
+                       fov=None if g.fov_mask is None else f32(g.fov_mask))
 
 
 def phantom_inputs(n, nz, seed):
     f, mu = phantom.make_phantom(n, nz, seed)
     return f32(f), f32(mu)
+
+
+def one_hot_projection(oracle, og, voxel, rmax):
+    """H e_v of the oracle for the unit volume at `voxel` = (i, j, k), from the
+    z slab the voxel's blur reaches: rotation and attenuation act on every z
+    plane alone and the PSF spreads at most rmax bins along z, so the
+    projection of e_v is zero outside [k - rmax, k + rmax] and, inside, equals
+    the projection of the slab [k - rmax - 1, k + rmax + 2) cut from the
+    volume and the mu map (edges of the real volume stay where they are).
+    Returns the full [n_angles][n][nz] array."""
+    import dataclasses
+    i, j, k = voxel
+    zlo, zhi = max(0, k - rmax - 1), min(og.nz, k + rmax + 2)
+    e = np.zeros((og.n, og.n, zhi - zlo))
+    e[i, j, k - zlo] = 1.0
+    og_c = dataclasses.replace(og, nz=zhi - zlo, mu=None if og.mu is None else np.asarray(og.mu)[:, :, zlo:zhi])
+    c = np.zeros((og.n_angles, og.n, og.nz))
+    c[:, :, zlo:zhi] = oracle.forward(e, og_c)
+    return c

@@ -30,10 +30,19 @@ def _t(a, dev):
     (128, 128, 120, 8, 0, 2),
     (64, 40, 12, 3, -1, 7),   # axial size below 128 and not a multiple of 16
     (64, 64, 16, 4, -1, 8),   # non-circular orbit (per-angle Toeplitz tiles)
+    (64, 48, 16, 4, -1, 9),   # non-central projections (T_trans) and a field-of-view mask (T_fov)
 ])
 def test_bf16_projection_parity(spect_lib, oracle_mod, cuda, n, nz, na, M, subset, seed):
     offs = [3.0 + 2.0 * math.cos(2 * 2 * math.pi * a / na) for a in range(na)] if seed == 8 else None
-    g = spect_lib.Geometry(n=n, nz=nz, n_angles=na, n_subsets=M, psf_bf16=True, atten_f64=True, det_offsets=offs)
+    kw = {}
+    if seed == 9:
+        rng = np.random.Generator(np.random.PCG64(9))
+        kw["det_shifts"] = [float(v) for v in rng.uniform(-4.0, 4.0, size=na)]
+        mask = np.zeros((na, n, nz), dtype=np.float32)
+        mask[:, 6:58, 4:44] = 1.0
+        kw["fov_mask"] = mask
+    g = spect_lib.Geometry(n=n, nz=nz, n_angles=na, n_subsets=M, psf_bf16=True, atten_f64=True, det_offsets=offs,
+                           **kw)
     f, mu = phantom_inputs(n, nz, seed)
     plan = spect_lib.Plan(g, _t(mu, cuda))
     og = oracle_geom(oracle_mod, g, mu)

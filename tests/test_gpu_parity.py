@@ -11,8 +11,10 @@ Tolerances:
   - FP64 count sums: conservation holds to FP32 rounding of H x (1e-6).
 Sizes span several blur strips and plane tiles with ragged tails (n and nz
 not multiples of 16), a 132^2 x 44 geometry whose back projection takes the
-tiled gather with partial tiles, a non-circular orbit (per-angle PSF tables), the 64^3 and 128^3 workloads in full, and a
-192^3 geometry whose planes are split into z tiles.
+tiled gather with partial tiles, a non-circular orbit (per-angle PSF tables),
+non-central projections (T_trans) with a field-of-view mask (T_fov), the
+64^3 and 128^3 workloads in full, and a 192^3 geometry whose planes are
+split into z tiles.
 """
 import math
 
@@ -32,8 +34,44 @@ def _t(a, dev):
     return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float32))).to(dev)
 
 
+def _fov_mask(n_angles, n, nz, seed):
+    """T_fov test weights: per angle a field of view of random width along y
+    and z (1 inside, 0 outside), with a few partial weights at its edge."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    m = np.zeros((n_angles, n, nz), dtype=np.float32)
+    for a in range(n_angles):
+        j0, j1 = sorted(rng.integers(0, n, size=2))
+        k0, k1 = sorted(rng.integers(0, nz, size=2))
+        m[a, j0:j1 + 2, k0:k1 + 2] = 1.0
+        m[a, j0, k0:k1 + 2] = 0.5
+    return m
+
+
+def _band_mask(n_angles, n, nz, shifts, half):
+    """A detector field of view: bins within `half` of the angle's shifted
+    detector centre along y and inside two bins of the axial edges."""
+    m = np.zeros((n_angles, n, nz), dtype=np.float32)
+    c = 0.5 * (n - 1)
+    j = np.arange(n)
+    for a in range(n_angles):
+        m[a][np.abs(j - c - shifts[a]) <= half, 2:nz - 2] = 1.0
+    return m
+
+
+def _shifts(n_angles, amp, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [float(v) for v in rng.uniform(-amp, amp, size=n_angles)]
+
+
 CASES = {
     # name: (geometry kwargs, phantom seed)
+    # non-central projections (T_trans, sub-voxel shifts per angle) and a
+    # field-of-view mask (T_fov), per-column gather
+    "trans_fov40x36": (dict(n=40, nz=36, n_angles=12, n_subsets=3, psf_slope=0.1, det_shifts=_shifts(12, 3.5, 41),
+                            fov_mask=_fov_mask(12, 40, 36, 42)), 20),
+    # the same on the tiled gather (partial tiles) with an orbit
+    "trans_tiled132x44": (dict(n=132, nz=44, n_angles=9, n_subsets=3, det_shifts=_shifts(9, 6.0, 43),
+                               det_offsets=[1.0 + 0.5 * a for a in range(9)]), 21),
     "ragged40x36": (dict(n=40, nz=36, n_angles=12, n_subsets=3, psf_slope=0.1), 11),
     "osem64": (dict(n=64, nz=64, n_angles=64, n_subsets=8), 1),
     "noatt_nopsf": (dict(n=48, nz=20, n_angles=7, n_subsets=2, attenuation=False, psf=False), 12),
@@ -102,7 +140,7 @@ def test_adjoint_dot_product(spect_lib, oracle_mod, cuda, name):
     assert abs(lhs - rhs) <= 1e-6 * scale
 
 
-@pytest.mark.parametrize("name", ["ragged40x36", "osem64", "noatt_nopsf"])
+@pytest.mark.parametrize("name", ["ragged40x36", "osem64", "noatt_nopsf", "trans_fov40x36"])
 def test_sensitivity_parity(spect_lib, oracle_mod, cuda, name):
     g, f, mu, plan, og = _setup(spect_lib, oracle_mod, cuda, name)
     for m in range(g.n_subsets):
@@ -235,3 +273,39 @@ def test_plan_reuse_with_new_mu_and_device_scatter(spect_lib, oracle_mod, cuda):
     p2.osem(y, 0.25, a, 0, 5)
     spect_lib.spect_osem_run_dev(p1.handle, y, torch.full((1,), 0.25, device=cuda), b, 0, 5)
     assert torch.equal(a, b)
+
+
+def test_osem_with_trans_and_fov(spect_lib, oracle_mod, cuda):
+    """OSEM through T_trans and T_fov: the masked forward feeds the ratio and
+    the count sums, the back projection weights the ratio again.  The field
+    of view is a detector band that follows each angle's shifted centre (the
+    random per-angle masks of the projector cases leave voxels seen only
+    through PSF tails at a mask edge, where FP32 rounding of the tiny
+    bilinear weights, not the method, decides the OSEM ratio)."""
+    from paper_2309_01977_gb300 import phantom
+    n, na, M = 48, 24, 4
+    shifts = _shifts(na, 2.5, 44)
+    g = spect_lib.Geometry(n=n, nz=n, n_angles=na, n_subsets=M, det_shifts=shifts,
+                           fov_mask=_band_mask(na, n, n, shifts, 18.0))
+    f_raw, mu = phantom_inputs(n, n, 22)
+    og = oracle_geom(oracle_mod, g, mu)
+    hf = oracle_mod.forward(f_raw, og)
+    _, y, s, _ = phantom.make_counts(f_raw, hf, 2e6, 0.05, 22)
+    s = float(np.float32(s))
+    plan = spect_lib.Plan(g, _t(mu, cuda))
+    x = torch.ones((n, n, n), device=cuda)
+    diag = plan.osem(_t(y, cuda), s, x, 0, 2 * M, diag=True).cpu().numpy()
+    ref, ref_diag = oracle_mod.osem(y, s, og, M, 0, 2 * M)
+    assert_close(x.cpu().numpy(), ref, 2e-5, "osem trans+fov")
+    np.testing.assert_allclose(diag, ref_diag, rtol=2e-5)
+
+
+def test_trans_fov_reject_bad_values(spect_lib, cuda):
+    bad_mask = np.ones((4, 16, 16), dtype=np.float32)
+    bad_mask[1, 2, 3] = -1.0
+    for kw in (dict(det_shifts=[0.0, float("nan"), 0.0, 0.0]), dict(det_shifts=[0.0, 100.0, 0.0, 0.0]),
+               dict(fov_mask=bad_mask)):
+        g = spect_lib.Geometry(n=16, nz=16, n_angles=4, attenuation=False, **kw)
+        with pytest.raises(spect_lib.SpectError) as e:
+            spect_lib.Plan(g)
+        assert e.value.status == spect_lib.SPECT_EINVAL

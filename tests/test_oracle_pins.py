@@ -559,3 +559,39 @@ def test_brute_force_dense_h_with_trans_and_fov(oracle_mod):
     g0 = oracle_mod.Geom(n=n, nz=nz, n_angles=8, angles=angles, mu=mu, trans=[0.0] * 8, fov=np.ones((8, n, nz)), **kw)
     g1 = oracle_mod.Geom(n=n, nz=nz, n_angles=8, angles=angles, mu=mu, **kw)
     np.testing.assert_array_equal(oracle_mod.forward(x, g0), oracle_mod.forward(x, g1))
+
+
+def test_one_hot_projection_from_a_z_slab_equals_the_full_one(oracle_mod):
+    """The GPU gradient test at 192^3 takes H e_v from the z slab the voxel's
+    blur reaches (tests/helpers.py); at 16 x 16 x 40 it equals the oracle's
+    projection of the whole one-hot volume, near both axial edges and inside."""
+    from helpers import one_hot_projection
+    n, nz = 16, 40
+    rng = _rng(91)
+    mu = rng.uniform(0.0, 0.3, size=(n, n, nz))
+    g = oracle_mod.Geom(n=n, nz=nz, n_angles=6, mu=mu, use_psf=True, sigma0=0.5, slope=0.2)
+    rmax = oracle_mod.psf_rmax(n, 0.5, 0.2, 3.0)
+    for v in [(3, 7, 0), (8, 2, 20), (12, 12, 39), (5, 9, rmax + 1)]:
+        e = np.zeros((n, n, nz))
+        e[v] = 1.0
+        full = oracle_mod.forward(e, g)
+        np.testing.assert_allclose(one_hot_projection(oracle_mod, g, v, rmax), full, rtol=1e-13, atol=1e-16)
+
+
+def test_uniform_quarter_turns_are_exact_permutations(oracle_mod):
+    """theta = 2 pi a / 4: cos and sin are exactly 0 and +-1, so without blur
+    and attenuation each projection is the sum over depth of an exact index
+    permutation of the volume (bitwise, summed in the same order), with no
+    rounding-level weight leaking into neighbouring voxels."""
+    n, nz = 10, 3
+    f = _rng(92).uniform(size=(n, n, nz))
+    g = oracle_mod.Geom(n=n, nz=nz, n_angles=4, mu=None, use_psf=False)
+    p = oracle_mod.forward(f, g)
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    perms = [(i, j), (n - 1 - j, i), (n - 1 - i, n - 1 - j), (j, n - 1 - i)]  # (u, v) of rotated voxel (i, j)
+    for a, (u, v) in enumerate(perms):
+        rot = f[u, v, :]
+        expect = np.zeros((n, nz))
+        for d in range(n):
+            expect += rot[d]
+        np.testing.assert_array_equal(p[a], expect)
