@@ -16,7 +16,15 @@ Extra objects on the JSON line:
   roofline     the dominant kernel's algorithmic bytes per launch over its
                CUDA-event duration (a second, profiled pass of the same
                steps), against the measured HBM copy bandwidth;
-  cpu_baseline the FP64 CPU oracle on a bounded sample of the workload;
+  cpu_baseline the FP64 CPU oracle on the whole 4 x 8 reconstruction of the
+               workload (32 subiterations from the same y);
+  accuracy_vs_fp64  relative L2 errors against that FP64 oracle of the
+               reconstructed image and of the projections H f_true, for the
+               FP32 form and the BF16-PSF form;
+  bf16         the BF16-PSF form (tensor-core PSF GEMMs, FP64 attenuation
+               sums) on the same workload and data, device and end to end;
+  plan_time    plan creation (wall time) and the device time of the
+               attenuation cache and subset sensitivities, per form;
   clocks       nvidia-smi SM clocks and throttle reasons sampled during the
                timed region.
 
@@ -64,6 +72,7 @@ def parse_args():
     ap.add_argument("--no-orbit", action="store_true", help="skip the non-circular orbit OSEM leg")
     ap.add_argument("--no-pet", action="store_true", help="skip the listmode PET leg")
     ap.add_argument("--no-autograd", action="store_true", help="skip the batch-of-4 192^3 gradient leg")
+    ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-PSF leg")
     ap.add_argument("--pet-only", action="store_true",
                     help="run only the listmode PET leg (one GPU) and print it as one JSON line")
     ap.add_argument("--pet-prompts", type=int, default=None, help="prompts of the PET leg (default 30 M)")
@@ -227,28 +236,40 @@ def algorithmic_bytes(kernel: str, wl, n_sel: int) -> float:
     return 0.0
 
 
-def cpu_baseline(wl, y, s, mu64, seconds: float, steps=None):
-    """Time the FP64 oracle's OSEM on the host cores: whole subiterations until
-    `seconds` have passed (or exactly `steps` of them)."""
+def oracle_geom(wl, mu64):
     import oracle
-    og = oracle.Geom(n=wl.n, nz=wl.nz, n_angles=wl.n_angles, mu=mu64, voxel_cm=float(np.float32(wl.voxel_cm)),
-                     sigma0=float(np.float32(wl.sigma0)), slope=float(np.float32(wl.slope)),
-                     nsigma=float(np.float32(wl.nsigma)))
+    return oracle.Geom(n=wl.n, nz=wl.nz, n_angles=wl.n_angles, mu=mu64, voxel_cm=float(np.float32(wl.voxel_cm)),
+                       sigma0=float(np.float32(wl.sigma0)), slope=float(np.float32(wl.slope)),
+                       nsigma=float(np.float32(wl.nsigma)))
+
+
+def cpu_baseline(wl, y, s, mu64, seconds: float, steps=None, full=False):
+    """Time the FP64 oracle's OSEM on the host cores: whole subiterations until
+    `seconds` have passed (or exactly `steps` of them; with full=True the
+    whole n_iters x n_subsets reconstruction).  Returns the record and the
+    oracle's image."""
+    import oracle
+    og = oracle_geom(wl, mu64)
     f = np.ones((wl.n, wl.n, wl.nz))
     done = 0
+    total = wl.n_iters * wl.n_subsets
     t0 = time.perf_counter()
     while True:
         f, _ = oracle.osem(y, s, og, wl.n_subsets, done, 1, f)
         done += 1
         el = time.perf_counter() - t0
-        if steps is not None:
+        if full:
+            if done >= total:
+                break
+        elif steps is not None:
             if done >= steps:
                 break
         elif el >= seconds:
             break
+    what = ("the whole %dx%d OSEM (%d subiterations)" % (wl.n_iters, wl.n_subsets, done) if full and done == total
+            else "first %d subiteration(s) of the %dx%d OSEM" % (done, wl.n_iters, wl.n_subsets))
     out = {"value": done / el, "unit": UNIT, "cores": oracle.n_threads(), "kind": "oracle",
-           "sample": "first %d subiteration(s) of the %dx%d OSEM on %s (FP64, %.1f s)" % (
-               done, wl.n_iters, wl.n_subsets, wl.name, el)}
+           "sample": "%s on %s (FP64, %.1f s)" % (what, wl.name, el)}
     if steps is None:
         # the same oracle on one thread: one subiteration
         threads = oracle.n_threads()
@@ -259,6 +280,29 @@ def cpu_baseline(wl, y, s, mu64, seconds: float, steps=None):
             out["one_thread_value"] = 1.0 / (time.perf_counter() - t1)
         finally:
             oracle.set_threads(threads)
+    return out, f
+
+
+def rel_l2(a, b) -> float:
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def accuracy_vs_fp64(wl, mu64, f_true, ref_image, images: dict, projections: dict) -> dict:
+    """Relative L2 errors of the GPU forms against the FP64 oracle: the
+    4 x 8 OSEM image (against the oracle's image from the same y) and the
+    projections H f_true of all angles (against the oracle's)."""
+    import oracle
+    t0 = time.perf_counter()
+    ref_proj = oracle.forward(f_true.astype(np.float64), oracle_geom(wl, mu64))
+    out = {"reference": "FP64 CPU oracle: the 4x8 OSEM image from the same y, and H f_true over all angles",
+           "oracle_projection_s": round(time.perf_counter() - t0, 2)}
+    for k, img in images.items():
+        out["%s_image_rel_l2" % k] = rel_l2(img, ref_image)
+    for k, prj in projections.items():
+        out["%s_proj_rel_l2" % k] = rel_l2(prj, ref_proj)
+    out["bars"] = {"fp32": "projections 1e-5, image 2e-5", "bf16": "1e-3"}
     return out
 
 
@@ -520,8 +564,10 @@ def run_pet_leg(torch, dev, timed, max_over_ranks, world, k, cpu_seconds: float,
         # (with time of flight the erf weights also keep the issue slots busy)
         if prof_l2:
             leg["roofline"] = {"bound": "l2", "kernel": em_name, "frac": prof_l2["lts_throughput_frac"],
-                               "issue_active_frac": prof_l2["issue_active_frac"],
-                               "source": "ncu of the same kernel at 3 M prompts (profiles/pet_lm_em_petlm204.md)"}
+                               "issue_active_frac": prof_l2["issue_active_frac"], "measured_in_run": False,
+                               "source": "stored: ncu of the same kernel at 3 M prompts, read from "
+                                         "profiles/l2_petlm204.json (profiles/pet_lm_em_petlm204.md); "
+                                         "stale if the kernel has changed since"}
     if with_cpu:
         leg["cpu_baseline"] = pet_cpu_baseline(wl, act, mu, lors, mult, s, sens, cpu_seconds, tof_bin)
     plan.close()
@@ -611,6 +657,88 @@ def run_autograd_leg(spect, torch, dev, timed, max_over_ranks, world, k):
             "step": "Poisson log-likelihood of the batch and its gradient through torch.autograd",
             "gradients_per_s": replica_throughput(world, k, batch, ms), "ms_per_step": ms / k,
             "kernel_avg_us": {kk: round(1e3 * v[1] / v[0], 1) for kk, v in prof.items()}}
+
+
+def plan_time(spect, torch, dev, g, mu_dev) -> dict:
+    """Plan-time costs (outside every timed step): a fresh plan's creation
+    (wall time: tables, gather tables, the attenuation cache A_a of every
+    angle, the subset sensitivities H_m^T 1, and the synchronisation), and
+    the device time of rebuilding A_a and H_m^T 1 from a mu map
+    (spect_plan_set_mu, CUDA events per kernel)."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p = spect.Plan(g, mu_dev)
+    create_ms = (time.perf_counter() - t0) * 1e3
+    spect.spect_profile_enable(p.handle, True)
+    spect.spect_profile_read(p.handle, reset=True)
+    spect.spect_plan_set_mu(p.handle, mu_dev)
+    prof = spect.spect_profile_read(p.handle, reset=True)
+    p.close()
+    att = sum(v[1] for k, v in prof.items() if k == "attenuation")
+    sens = sum(v[1] for k, v in prof.items() if k != "attenuation")
+    return {"create_ms": round(create_ms, 2), "attenuation_cache_ms": round(att, 3),
+            "sensitivities_ms": round(sens, 3), "sensitivity_kernels": sorted(k for k in prof if k != "attenuation")}
+
+
+def run_bf16_leg(spect, torch, dev, wl, mu_dev, f_dev, y_dev, y_host, s, timed, max_over_ranks, world, k):
+    """The BF16-PSF form on the same workload and data: the PSF of every
+    depth plane as banded-Toeplitz BF16 tensor-core GEMMs (FP32 accumulate),
+    the attenuation prefix sums in FP64; the rest as in the FP32 form.  One
+    step = one full 4 x 8 OSEM reconstruction from f0 = 1."""
+    n_sub = wl.n_iters * wl.n_subsets
+    g = spect.Geometry(n=wl.n, nz=wl.nz, n_angles=wl.n_angles, n_subsets=wl.n_subsets, voxel_cm=wl.voxel_cm,
+                       psf_sigma0=wl.sigma0, psf_slope=wl.slope, psf_nsigma=wl.nsigma, psf_bf16=True,
+                       atten_f64=True)
+    pt = plan_time(spect, torch, dev, g, mu_dev)
+    plan = spect.Plan(g, mu_dev)
+    x = torch.empty((wl.n, wl.n, wl.nz), device=dev)
+    x_host = torch.empty((wl.n, wl.n, wl.nz), dtype=torch.float32).pin_memory()
+
+    def step():
+        x.fill_(1.0)
+        spect.spect_osem_run(plan.handle, y_dev, s, x, 0, n_sub)
+
+    def step_e2e():
+        y_dev.copy_(y_host, non_blocking=True)
+        x.fill_(1.0)
+        spect.spect_osem_run(plan.handle, y_dev, s, x, 0, n_sub)
+        x_host.copy_(x, non_blocking=True)
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(timed(step, k))
+    for _ in range(2):
+        step_e2e()
+    ms_e2e = max_over_ranks(timed(step_e2e, k))
+    spect.spect_profile_enable(plan.handle, True)
+    spect.spect_profile_read(plan.handle, reset=True)
+    timed(step, k)
+    prof = spect.spect_profile_read(plan.handle, reset=True)
+    spect.spect_profile_enable(plan.handle, False)
+    image = x.cpu().numpy()
+    proj = plan.forward(f_dev).cpu().numpy()
+    plan.check()
+    plan.close()
+    n_sel = -(-wl.n_angles // wl.n_subsets)
+    peaks = measured_peaks()
+    fwd = prof.get("forward_bf16")
+    roof = None
+    if fwd:
+        avg_s = fwd[1] / fwd[0] / 1e3
+        flops, _ = algorithmic_flops("forward_bf16", wl, n_sel)
+        nbytes = algorithmic_bytes("forward_bf16", wl, n_sel)
+        roof = {"kernel": "forward_bf16", "avg_launch_us": avg_s * 1e6,
+                "tensor_frac": flops / avg_s / 1e12 / peaks["bf16_tflops_sustained"],
+                "hbm_frac": nbytes / avg_s / 1e9 / peaks["hbm_gbs"],
+                "tensor_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
+                "peaks": "BF16 sustained %.0f TF/s, HBM %.0f GB/s (%s)" % (
+                    peaks["bf16_tflops_sustained"], peaks["hbm_gbs"], peaks["source"])}
+    leg = {"form": "BF16 banded-Toeplitz PSF on tcgen05 (FP32 accumulate), FP64 attenuation sums",
+           "subset_iters_per_s": replica_throughput(world, k, n_sub, ms), "ms_per_recon": ms / k,
+           "e2e_subset_iters_per_s": replica_throughput(world, k, n_sub, ms_e2e),
+           "kernel_avg_us": {kk: round(1e3 * v[1] / v[0], 2) for kk, v in prof.items()},
+           "roofline": roof, "plan_time": pt}
+    return leg, image, proj
 
 
 def run_libspect(args):
@@ -724,6 +852,10 @@ def run_libspect(args):
         roofline = {"bound": "tensor" if pipe == "tensor" else "alu", "achieved": flops / avg_s / 1e12,
                     "peak": fpeak, "unit": "TFLOP/s"}
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    image_main = x.cpu().numpy()  # the last profiled step's 4 x 8 reconstruction
+    f_dev = torch.from_numpy(f_raw).to(dev)
+    proj_main = hf.astype(np.float32)
+    plan_times = {"bf16" if bf16 else "fp32": plan_time(spect, torch, dev, g, torch.from_numpy(mu).to(dev))}
     roofline.update({
         "traffic": traffic, "kernel": name, "peak_source": peaks["source"] + (
             " (FP32: SMs x 128 lanes x 2 flop x max clock)" if roofline["bound"] == "alu" else
@@ -758,14 +890,26 @@ def run_libspect(args):
     if not args.no_orbit:
         legs["orbit"] = run_orbit_leg(spect, torch, dev, wl, g, f_raw, mu, x, timed, max_over_ranks, world,
                                       max(2, args.steps // 2))
+    images = {"bf16" if bf16 else "fp32": image_main}
+    projections = {"bf16" if bf16 else "fp32": proj_main}
+    if not bf16 and not args.no_bf16:
+        leg_b, img_b, proj_b = run_bf16_leg(spect, torch, dev, wl, torch.from_numpy(mu).to(dev), f_dev, y_dev,
+                                            y_host, s, timed, max_over_ranks, world, args.steps)
+        plan_times["bf16"] = leg_b.pop("plan_time")
+        legs["bf16"] = leg_b
+        images["bf16"], projections["bf16"] = img_b, proj_b
 
     serving = None
     if args.serve_requests > 0 and world == 1:
         serving = run_serving(spect, dev, args)
 
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl, y, s, mu.astype(np.float64), args.cpu_seconds)
+        # the oracle's whole 4 x 8 reconstruction from the same y: timed as the
+        # CPU baseline, and the FP64 reference of the accuracy figures
+        cpu, ref_image = cpu_baseline(wl, y, s, mu.astype(np.float64), args.cpu_seconds, full=True)
+        accuracy = accuracy_vs_fp64(wl, mu.astype(np.float64), f_raw, ref_image, images, projections)
 
     # listmode PET last: its event lists are the largest allocations of the run
     if not args.no_pet:
@@ -788,7 +932,7 @@ def run_libspect(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16 PSF, f32" if bf16 else "f32", "data": "synthetic",
             "config": cfg,
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": int(launches),
-            "clocks": clk, **legs, "serving": serving,
+            "clocks": clk, "accuracy_vs_fp64": accuracy, "plan_time": plan_times, **legs, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     plan.close()
