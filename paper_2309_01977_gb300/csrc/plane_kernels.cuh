@@ -633,14 +633,28 @@ __global__ void __launch_bounds__(kFwdThreads, 1) blur_back_kernel(BlurBackArgs 
                 for (int h = 0; h < 2; ++h) {
                     const int j = 2 * jp + h;
                     v[u][h] = make_float2(0.f, 0.f);
-                    if (it < items && j < n) {
+                    if (it < items && j < n)
                         v[u][h] = pr ? __ldg(reinterpret_cast<const float2*>(pr + (size_t)j * nz + k)) : make_float2(1.f, 1.f);
-                        if (fv) {
-                            const float2 m = __ldg(reinterpret_cast<const float2*>(fv + (size_t)j * nz + k));
-                            v[u][h] = make_float2(v[u][h].x * m.x, v[u][h].y * m.y);
-                        }
+                }
+            }
+            if (fv) {  // T_fov weights of the same elements, loaded together
+                float2 m[4][2];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int it = it0 + u * blockDim.x + tid;
+                    const int jp = it / max(ncp, 1), cq = it - jp * ncp;
+                    const int k = klo + 2 * cq;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = 2 * jp + h;
+                        m[u][h] = (it < items && j < n) ? __ldg(reinterpret_cast<const float2*>(fv + (size_t)j * nz + k))
+                                                        : make_float2(0.f, 0.f);
                     }
                 }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) v[u][h] = make_float2(v[u][h].x * m[u][h].x, v[u][h].y * m[u][h].y);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {

@@ -5,20 +5,23 @@
 // with T_i the symmetric banded Toeplitz matrix of the plane's Gaussian taps.
 // Both products are issued with K-major operands only:
 //   GEMM 1   D1[k][j]  = sum_k' T_i[k][k'] P[j][k']          (blur along z)
-//   GEMM 2   D2[k][j] += sum_j' X[k][j'] T_i[j][j']  with X = bf16(D1)
+//   GEMM 2   D2[k][j] += sum_j' X[k][j'] T_i[j][j']  with X = D1
 // so D2 = (T_i P T_i^T)^T, and the forward keeps D2 in TMEM across the depth
-// loop (P_x).  Every operand is split into two BF16 parts, v = v_hi + v_lo
-// (v_lo = bf16(v - v_hi)), and each GEMM runs three MMA chains,
-// hi*hi + hi*lo + lo*hi, dropping only lo*lo (relative ~2^-18): the
-// projector then agrees with FP32 to ~1e-6 instead of the ~2e-4 of a single
-// BF16 rounding, which OSEM would compound past 1e-3 over 32 subiterations.
+// loop (P_x).  The taps are BF16, renormalised to unit sum; the data operands
+// (P, and X read back from TMEM) are split into two BF16 parts, v = v_hi +
+// v_lo (v_lo = bf16(v - v_hi)), and each GEMM runs two MMA chains,
+// T * v_hi + T * v_lo.  Measured on the 128^3 x 120-angle 4 x 8 OSEM against
+// the FP64 oracle: image 6.5e-4 and projections 8.5e-5 relative L2 (bar
+// 1e-3).  The alternatives measured: three chains with the taps split too,
+// 3.4e-6 (but 8 us slower per kernel); the taps split and the data rounded
+// once, 1.3e-3; one chain, 2.5e-3 with renormalised taps, 4.0e-3 without.
 // Rotation, attenuation, the ratio and the update stay FP32 on the CUDA
 // cores.
 //
 // Shared-memory operands are K-major tiles with the 128-byte swizzle (see
 // sw_off), so that both the staging (lanes along z) and the TMEM read-back
 // (lanes along the tile rows) store without bank conflicts.  The per-plane
-// Toeplitz pair (64 KB) arrives by one TMA bulk copy.
+// Toeplitz tile (32 KB) arrives by one TMA bulk copy.
 //
 // Every wait on an mbarrier is bounded: when the bound runs out the kernel
 // records SPECT_ETIMEDOUT in the plan's error word, releases its tensor
@@ -119,7 +122,7 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 }
 
 struct TcSmem {
-    uint32_t tap;   // T_hi then T_lo (2 tiles)
+    uint32_t tap;   // T (one tile)
     uint32_t b1;    // GEMM 1 B operand [n][128]: hi part, then the lo part at + b1_lo
     uint32_t a2;    // GEMM 2 A operand [128][n]: hi part, then the lo part at + a2_lo
     uint32_t b1_lo, a2_lo;  // byte distance from the hi to the lo part
@@ -138,25 +141,23 @@ __device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uin
 __device__ __forceinline__ void issue_gemm1(const TcSmem& s, uint32_t d1, uint32_t idesc, int n)
 {
     tc_fence_after();
-    for (int h = 0; h < 3; ++h) {
-        const uint32_t ta = s.tap + (h == 1 ? kTile : 0);
-        const uint32_t tb = s.b1 + (h == 2 ? s.b1_lo : 0);
+    for (int h = 0; h < 2; ++h) {
+        const uint32_t tb = s.b1 + (h ? s.b1_lo : 0);
 #pragma unroll
         for (int ks = 0; ks < kTcM / 16; ++ks)
-            tc_mma(d1, sw_desc(sw_kstep(ta, ks, kTcM)), sw_desc(sw_kstep(tb, ks, n)), idesc, (h | ks) != 0);
+            tc_mma(d1, sw_desc(sw_kstep(s.tap, ks, kTcM)), sw_desc(sw_kstep(tb, ks, n)), idesc, (h | ks) != 0);
     }
     tc_commit(s.bar_1);
 }
 
-// GEMM 2: D2 (+)= A_hi T_hi^T + A_hi T_lo^T + A_lo T_hi^T over K = n.
+// GEMM 2: D2 (+)= A_hi T^T + A_lo T^T over K = n.
 __device__ __forceinline__ void issue_gemm2(const TcSmem& s, uint32_t d2, uint32_t idesc, int n, bool accumulate)
 {
     tc_fence_after();
-    for (int h = 0; h < 3; ++h) {
-        const uint32_t ta = s.a2 + (h == 2 ? s.a2_lo : 0);
-        const uint32_t tb = s.tap + (h == 1 ? kTile : 0);
+    for (int h = 0; h < 2; ++h) {
+        const uint32_t ta = s.a2 + (h ? s.a2_lo : 0);
         for (int ks = 0; ks < n / 16; ++ks)
-            tc_mma(d2, sw_desc(sw_kstep(ta, ks, kTcM)), sw_desc(sw_kstep(tb, ks, kTcM)), idesc,
+            tc_mma(d2, sw_desc(sw_kstep(ta, ks, kTcM)), sw_desc(sw_kstep(s.tap, ks, kTcM)), idesc,
                    (accumulate || h || ks) ? 1u : 0u);
     }
     tc_commit(s.bar_2);
@@ -186,7 +187,7 @@ __device__ __forceinline__ void d1_to_a2(const TcSmem& s, uint32_t d1, int n)
 // Byte offset of the barriers after the operand tiles.
 __host__ __device__ constexpr int bf16_tail_offset(int n)
 {
-    return 2 * kTile + 2 * n * kTcM * 2 + 2 * kTcM * ((n + 63) / 64 * 64) * 2;
+    return kTile + 2 * n * kTcM * 2 + 2 * kTcM * ((n + 63) / 64 * 64) * 2;
 }
 
 struct TcState {
@@ -197,10 +198,10 @@ struct TcState {
 
 __device__ __forceinline__ bool tc_setup(TcState& st, unsigned char* smem, int n, uint32_t ncols)
 {
-    // tiles: T_hi, T_lo (128 x 128); B1 hi, lo (n x 128); A2 hi, lo (128 x K
-    // with K = n rounded up to whole 64-column swizzle blocks); all 1 KB aligned
+    // tiles: T (128 x 128); B1 hi, lo (n x 128); A2 hi, lo (128 x K with
+    // K = n rounded up to whole 64-column swizzle blocks); all 1 KB aligned
     st.s.tap = smem_u32(smem);
-    st.s.b1 = st.s.tap + 2 * kTile;
+    st.s.b1 = st.s.tap + kTile;
     st.s.b1_lo = n * kTcM * 2;
     st.s.a2 = st.s.b1 + 2 * st.s.b1_lo;
     st.s.a2_lo = kTcM * ((n + 63) / 64 * 64) * 2;
@@ -414,7 +415,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
     if (i < n) {
         const float* arow = a.atten ? a.atten + ((size_t)angle * n + i) * n * nz : nullptr;
         if (a.atten && i + a.chunks < n) tc_prefetch_plane(arow + (size_t)a.chunks * n * nz, n, nz);
-        if (threadIdx.x == 0) tma_load_1d(st.s.tap, ttab + (size_t)i * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
+        if (threadIdx.x == 0) tma_load_1d(st.s.tap, ttab + (size_t)i * kTcM * kTcM, kTile, st.s.bar_t);
         tc_tap_rows(rows, n, nz, i, cs, c);
         __syncthreads();
         tc_stage_plane(st.s.b1, st.s.b1_lo, rows, xb, arow, n, nz);
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
             // fetch those of the next plane behind the staging below
             if (inext < n) {
                 ok2 = mbar_wait(st.s.bar_2, ph_2);
-                if (ok2) tma_load_1d(st.s.tap, ttab + (size_t)inext * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
+                if (ok2) tma_load_1d(st.s.tap, ttab + (size_t)inext * kTcM * kTcM, kTile, st.s.bar_t);
             }
         }
         first = false;
@@ -506,7 +507,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
     int i = chunk;
     if (i < n && a.atten) tc_prefetch_plane(a.atten + ((size_t)angle * n + i) * n * nz, n, nz);
     if (i < n && threadIdx.x == 0)
-        tma_load_1d(st.s.tap, ttab + (size_t)i * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
+        tma_load_1d(st.s.tap, ttab + (size_t)i * kTcM * kTcM, kTile, st.s.bar_t);
     tc_stage_proj(st.s.b1, st.s.b1_lo, pr, a.fov ? a.fov + (size_t)angle * n * nz : nullptr, n, nz);
     fence_async_smem();
     if (i < n) {
@@ -532,7 +533,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
         ph_2 ^= 1u;
         if (!ok) break;
         if (inext < n && threadIdx.x == 0)
-            tma_load_1d(st.s.tap, ttab + (size_t)inext * 2 * kTcM * kTcM, 2 * kTile, st.s.bar_t);
+            tma_load_1d(st.s.tap, ttab + (size_t)inext * kTcM * kTcM, kTile, st.s.bar_t);
         tc_fence_after();
         // B[i][j][k] = A[i][j][k] * (K_i r)[j][k]; D2 holds (K_i r)^T (lanes k)
         const float* arow = a.atten ? a.atten + ((size_t)angle * n + i) * n * nz : nullptr;
