@@ -42,7 +42,8 @@ namespace spect {
 
 namespace {
 
-constexpr int kTcThreads = 512;                 // 16 warps: 4 TMEM lane quadrants x 4 column parts
+constexpr int kWorkers = 16;                    // worker warps: 4 TMEM lane quadrants x 4 column parts
+constexpr int kTcThreads = 32 * (1 + kWorkers); // warp 0 issues copies and products, warps 1..16 work
 constexpr int kTcM = 128;                       // MMA M = axial size padded to 128
 constexpr int kTile = kTcM * kTcM * 2;          // one 128x128 BF16 tile, bytes
 
@@ -162,17 +163,23 @@ __device__ __forceinline__ void issue_gemm2(uint32_t a2, uint32_t lo, uint32_t t
     if (bar) tc_commit(bar);
 }
 
+// The worker warps w = 1..kWorkers split each TMEM accumulator: warp w may
+// only access TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31 (its lane quadrant),
+// and takes the 16-column chunks c with c / 16 = (w - 1) / 4 (mod 4), so
+// the 16 workers cover every (quadrant, chunk) once.
+__device__ __forceinline__ int tm_quad(int warp) { return warp & 3; }
+__device__ __forceinline__ int tm_col0(int warp) { return 16 * ((warp - 1) >> 2); }
+
 // D1 (TMEM, lanes k, columns j) -> BF16 hi/lo -> A operand of GEMM 2
-// (K-major [k][j], K = n; lo part `lo` bytes after the hi part).  Warp w
-// reads TMEM lanes 32*(w%4).. (its lane quadrant) and the 16-column chunks
-// c with c/16 = w/4 (mod 4).
+// (K-major [k][j], K = n; lo part `lo` bytes after the hi part); this
+// worker's lanes and chunks.
 __device__ __forceinline__ void d1_to_a2(uint32_t a2, uint32_t lo, uint32_t d1, int n)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = 32 * (warp & 3) + lane;
-    for (int c = 16 * (warp >> 2); c < n; c += 64) {
+    const int k = 32 * tm_quad(warp) + lane;
+    for (int c = tm_col0(warp); c < n; c += 64) {
         float v[16];
-        tc_ld16(d1 + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c, v);
+        tc_ld16(d1 + ((uint32_t)(32 * tm_quad(warp)) << 16) + (uint32_t)c, v);
         uint32_t h[8], l[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) split_bf16x2(v[2 * q], v[2 * q + 1], h[q], l[q]);
@@ -189,21 +196,26 @@ __device__ __forceinline__ void d1_to_a2(uint32_t a2, uint32_t lo, uint32_t d1, 
 // rounded up to whole 64-column swizzle blocks).
 __host__ __device__ constexpr uint32_t part_bytes(int n) { return (uint32_t)kTcM * ((n + 63) / 64 * 64) * 2u; }
 
-// Shared-memory layouts (every tile 1 KB aligned), then a 64-byte block of
-// up to six mbarriers and the TMEM address slot at byte 48:
-//   forward:  Toeplitz slots [2] | plane buffers [2] (hi, lo) | tap-row tables [2][n]
+// Shared-memory layouts (every tile 1 KB aligned), then a 128-byte block of
+// mbarriers with the TMEM address slot at byte 112:
+//   forward:  Toeplitz slots [2] | plane buffers [2] (hi, lo) | tap-row table [n]
 //   back:     Toeplitz slots [3] | B1 = projection (hi, lo) | A2 (hi, lo)
 constexpr int kFwdSlots = 2, kBackSlots = 3;
-constexpr uint32_t kBarBytes = 64;
+constexpr uint32_t kBarBytes = 128, kTmemSlot = 112;
 __host__ __device__ constexpr uint32_t fwd_rows_offset(int n) { return kFwdSlots * kTile + 4u * part_bytes(n); }
-__host__ __device__ constexpr uint32_t fwd_bar_offset(int n) { return fwd_rows_offset(n) + 64u * (uint32_t)n; }
+__host__ __device__ constexpr uint32_t fwd_bar_offset(int n) { return fwd_rows_offset(n) + 32u * (uint32_t)n; }
 __host__ __device__ constexpr uint32_t back_bar_offset(int n) { return kBackSlots * kTile + 4u * part_bytes(n); }
 
-// Thread 0's record of the Toeplitz-tile copies per slot (slot s completes
-// on the barrier at bars + 8 s): a copy is pending from its issue until
-// thread 0 has seen it land, and the parity bit of a slot is that of its
-// next completion.  After a timeout, drain() waits (bounded) for the copies
-// still in flight, so that none lands after the CTA has left.
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// The issuing thread's record of the Toeplitz-tile copies per slot (slot s
+// completes on the barrier at bars + 8 s): a copy is pending from its issue
+// until that thread has seen it land, and the parity bit of a slot is that
+// of its next completion.  After a timeout, drain() waits (bounded) for the
+// copies still in flight, so that none lands after the CTA has left.
 struct TileLoads {
     uint32_t pend = 0, par = 0;
     __device__ __forceinline__ void load(int s, uint32_t dst, const void* src, uint32_t bars)
@@ -227,23 +239,19 @@ struct TileLoads {
     }
 };
 
-// Thread 0, after a timeout: one more commit covers every product it has
-// issued; wait (bounded) until they are done before the TMEM is released.
+// The issuing thread, last: one more commit covers every product it has
+// issued; wait (bounded) until they are done, so that none is in flight
+// when the TMEM is released.
 __device__ __forceinline__ void tc_drain(uint32_t bar)
 {
     tc_commit(bar);
     mbar_wait(bar, 0);
 }
 
-// Initialise `count` barriers of one arrival at bars, bars + 8, ... (thread
-// 0), allocate `ncols` TMEM columns (warp 0) and return their base address.
-__device__ __forceinline__ uint32_t tc_begin(uint32_t bars, int count, uint32_t ncols)
+// Allocate `ncols` TMEM columns (warp 0) after thread 0 has initialised the
+// barriers, and return their base address to every thread.
+__device__ __forceinline__ uint32_t tc_alloc(uint32_t slot, uint32_t ncols)
 {
-    const uint32_t slot = bars + 48u;
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < count; ++q) mbar_init(bars + 8u * q, 1);
-        mbar_init_fence();
-    }
     if ((threadIdx.x >> 5) == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
                      : "memory");
@@ -267,43 +275,36 @@ __device__ __forceinline__ void tc_end(uint32_t tmem, uint32_t ncols)
     }
 }
 
-// Every thread reaches this with its own `ok`; on a timeout one thread
-// records the status and all threads leave together.
-__device__ __forceinline__ bool all_ok(bool ok, int* err)
+__device__ __forceinline__ void report_timeout(int* err)
 {
-    const int bad = __syncthreads_or(!ok);
-    if (bad && threadIdx.x == 0 && err) atomicExch(err, SPECT_ETIMEDOUT);
-    return !bad;
+    if (err) atomicExch(err, SPECT_ETIMEDOUT);
 }
 
-
-// Bilinear taps of rotated row j of plane i (as in the FP32 forward).
+// Bilinear taps of one rotated row (as in the FP32 forward).
 struct TcTapRow {
     int off[4];
     float w[4];
 };
 
-__device__ __forceinline__ void tc_tap_rows(TcTapRow* rows, int n, int nz, int i, float4 cs, float c)
+__device__ __forceinline__ TcTapRow tc_tap_row(int n, int nz, int i, int j, float4 cs, float c)
 {
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        float u, v;
-        sample_point(cs.x, cs.y, c, cs.z, i, j, u, v);
-        const float fu = floorf(u), fv = floorf(v);
-        const int x0 = (int)fu, y0 = (int)fv;
-        const float ax = u - fu, by = v - fv;
-        const bool vx0 = x0 >= 0 && x0 < n, vx1 = x0 + 1 >= 0 && x0 + 1 < n;
-        const bool vy0 = y0 >= 0 && y0 < n, vy1 = y0 + 1 >= 0 && y0 + 1 < n;
-        TcTapRow t;
-        t.w[0] = (vx0 && vy0) ? (1.f - ax) * (1.f - by) : 0.f;
-        t.w[1] = (vx1 && vy0) ? ax * (1.f - by) : 0.f;
-        t.w[2] = (vx0 && vy1) ? (1.f - ax) * by : 0.f;
-        t.w[3] = (vx1 && vy1) ? ax * by : 0.f;
-        t.off[0] = (vx0 && vy0) ? (x0 * n + y0) * nz : 0;
-        t.off[1] = (vx1 && vy0) ? ((x0 + 1) * n + y0) * nz : 0;
-        t.off[2] = (vx0 && vy1) ? (x0 * n + y0 + 1) * nz : 0;
-        t.off[3] = (vx1 && vy1) ? ((x0 + 1) * n + y0 + 1) * nz : 0;
-        rows[j] = t;
-    }
+    float u, v;
+    sample_point(cs.x, cs.y, c, cs.z, i, j, u, v);
+    const float fu = floorf(u), fv = floorf(v);
+    const int x0 = (int)fu, y0 = (int)fv;
+    const float ax = u - fu, by = v - fv;
+    const bool vx0 = x0 >= 0 && x0 < n, vx1 = x0 + 1 >= 0 && x0 + 1 < n;
+    const bool vy0 = y0 >= 0 && y0 < n, vy1 = y0 + 1 >= 0 && y0 + 1 < n;
+    TcTapRow t;
+    t.w[0] = (vx0 && vy0) ? (1.f - ax) * (1.f - by) : 0.f;
+    t.w[1] = (vx1 && vy0) ? ax * (1.f - by) : 0.f;
+    t.w[2] = (vx0 && vy1) ? (1.f - ax) * by : 0.f;
+    t.w[3] = (vx1 && vy1) ? ax * by : 0.f;
+    t.off[0] = (vx0 && vy0) ? (x0 * n + y0) * nz : 0;
+    t.off[1] = (vx1 && vy0) ? ((x0 + 1) * n + y0) * nz : 0;
+    t.off[2] = (vx0 && vy1) ? (x0 * n + y0 + 1) * nz : 0;
+    t.off[3] = (vx1 && vy1) ? ((x0 + 1) * n + y0 + 1) * nz : 0;
+    return t;
 }
 
 __device__ __forceinline__ void fma4(float4& acc, float w, const float4& v)
@@ -330,28 +331,41 @@ __device__ __forceinline__ void put4(uint32_t b1, uint32_t b1_lo, int j, int k, 
     st_shared_v2(o + b1_lo, l0, l1);
 }
 
-// B1[j][k] = A[j][k] * bilinear(f)[j][k] for k < nz, 0 for nz <= k < 128, as
-// BF16 hi and lo parts.  A warp stages whole rows, lane l covering k = 4l..4l+3
+// Worker wi (0 .. kWorkers-1) owns the rows j = wi + kWorkers r of every
+// plane.  Ask L2 to fetch its rows of an attenuation plane ahead of use.
+__device__ __forceinline__ void prefetch_rows(const float* plane, int n, int nz, int wi)
+{
+    const int lane = threadIdx.x & 31;
+    for (int j = wi + kWorkers * lane; j < n; j += kWorkers * 32) prefetch_l2(plane + (size_t)j * nz, (uint32_t)nz * 4u);
+}
+
+// B1[j][k] = A[j][k] * bilinear(f)[j][k] (plane i) for this worker's rows j,
+// k < nz, 0 for nz <= k < 128, as BF16 hi and lo parts.  Lanes compute the
+// rows' taps into the shared table first; then lane l covers k = 4l..4l+3
 // with 128-bit loads (one 512-byte row per load instruction), four rows at a
 // time so that twenty loads per lane are in flight together.  When wait_bar
 // is not 0 the buffer is still an operand of products in flight: the first
 // stores wait for phase parity wait_par of that barrier, behind the first
 // loads.  Returns false when that wait ran out.
-__device__ __forceinline__ bool tc_stage_plane(uint32_t b1, uint32_t b1_lo, const TcTapRow* rows,
-                                               const float* __restrict__ xb, const float* __restrict__ arow, int n,
-                                               int nz, uint32_t wait_bar, uint32_t wait_par)
+__device__ __forceinline__ bool stage_rows(uint32_t b1, uint32_t b1_lo, TcTapRow* rows, const float* __restrict__ xb,
+                                           const float* __restrict__ arow, int n, int nz, int i, float4 cs, float c,
+                                           int wi, uint32_t wait_bar, uint32_t wait_par)
 {
-    bool ok = true;
     constexpr int kRows = 4;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nr = (n - wi + kWorkers - 1) / kWorkers;  // rows of this worker
+    __syncwarp();  // this warp's reads of its table entries are done
+    if (lane < nr) rows[wi + kWorkers * lane] = tc_tap_row(n, nz, i, wi + kWorkers * lane, cs, c);
+    __syncwarp();
     const int k = 4 * lane;
     const bool in = k < nz;
-    for (int jb = warp; jb < n; jb += kRows * nw) {
+    bool ok = true;
+    for (int r0 = 0; r0 < nr; r0 += kRows) {
         float4 v[kRows];
         int jr[kRows];
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
-            jr[r] = jb + r * nw;
+            jr[r] = wi + kWorkers * (r0 + r);
             v[r] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         if (in) {
@@ -359,7 +373,7 @@ __device__ __forceinline__ bool tc_stage_plane(uint32_t b1, uint32_t b1_lo, cons
             TcTapRow t[kRows];
 #pragma unroll
             for (int r = 0; r < kRows; ++r) {
-                const int j = jr[r] < n ? jr[r] : jb;  // rows past n repeat a valid row; not stored
+                const int j = jr[r] < n ? jr[r] : wi;  // rows past n repeat a valid row; not stored
                 t[r] = rows[j];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) f[r][q] = __ldg(reinterpret_cast<const float4*>(xb + t[r].off[q] + k));
@@ -388,23 +402,14 @@ __device__ __forceinline__ bool tc_stage_plane(uint32_t b1, uint32_t b1_lo, cons
     return ok;
 }
 
-// Ask L2 to fetch one attenuation plane (n rows of nz floats; rows start on
-// 16-byte boundaries as nz % 8 == 0) ahead of its use; a hint that nothing
-// waits on.
-__device__ __forceinline__ void tc_prefetch_plane(const float* plane, int n, int nz)
-{
-    for (int j = threadIdx.x; j < n; j += blockDim.x) prefetch_l2(plane + (size_t)j * nz, (uint32_t)nz * 4u);
-}
-
 // B1[j][k] = proj[j][k] (all ones when proj is NULL) times the T_fov weight
-// fv[j][k] (when not NULL) for k < nz, as BF16 hi and lo parts; lanes along
-// k as above.
-__device__ __forceinline__ void tc_stage_proj(uint32_t b1, uint32_t b1_lo, const float* __restrict__ pr,
-                                              const float* __restrict__ fv, int n, int nz)
+// fv[j][k] (when not NULL) for this worker's rows j and k < nz, as BF16 hi
+// and lo parts; lanes along k as above.
+__device__ __forceinline__ void stage_proj_rows(uint32_t b1, uint32_t b1_lo, const float* __restrict__ pr,
+                                                const float* __restrict__ fv, int n, int nz, int wi)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int k = 4 * lane;
-    for (int j = warp; j < n; j += nw) {
+    const int k = 4 * (threadIdx.x & 31);
+    for (int j = wi; j < n; j += kWorkers) {
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (k < nz) {
             v = pr ? __ldg(reinterpret_cast<const float4*>(pr + (size_t)j * nz + k)) : make_float4(1.f, 1.f, 1.f, 1.f);
@@ -423,123 +428,136 @@ __device__ __forceinline__ void tc_stage_proj(uint32_t b1, uint32_t b1_lo, const
 //
 // Planes p = 0, 1, .. of this CTA's depth chunk (plane index chunk + p *
 // chunks) flow through two plane buffers X[p & 1]: the staged plane is the B
-// operand of GEMM 1(p); once GEMM 1(p) is done, D1 is written back over it
-// as the A operand of GEMM 2(p); once GEMM 2(p) is done, X[p & 1] takes the
-// staging of plane p + 2.  Per iteration p the CUDA cores stage plane p + 1
-// and hand D1(p) over, while the tensor cores run GEMM 2(p - 1) and
-// GEMM 1(p); one thread then issues GEMM 2(p) and GEMM 1(p + 1) back to
-// back.  The Toeplitz tile of plane p + 1 is copied into the slot of plane
-// p - 1 as soon as GEMM 2(p - 1) is done, a whole staging ahead of its use.
-// D2 accumulates the chunk's depth sum in TMEM (P_x).
+// operand of GEMM 1(p) into D1[p & 1]; once GEMM 1(p) is done, the workers
+// write D1 back over it as the A operand of GEMM 2(p), which accumulates the
+// chunk's depth sum in D2 (P_x); once GEMM 2(p) is done, X[p & 1] takes the
+// staging of plane p + 2.  Warp 0 (one thread) issues: GEMM 1(p) when the
+// workers have staged plane p, GEMM 2(p - 1) when they have handed D1(p - 1)
+// over, and the copy of plane p + 1's Toeplitz tile into the slot GEMM
+// 2(p - 1) has released.  The 16 worker warps meet the issuer on mbarriers
+// only, so a fast warp has its loads of the next plane in flight while the
+// others finish.
+//
+// Barriers (bars + 8 q): q = 0, 1 Toeplitz slots; 2, 3 GEMM 1 into D1[0],
+// D1[1]; 4 GEMM 2; 5 plane staged (every worker thread arrives); 6 D1 handed
+// over (every worker thread); 7 final drain.
 
 __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16Args a)
 {
     extern __shared__ __align__(1024) unsigned char tsm[];
-    const int n = a.n, nz = a.nz, tid = threadIdx.x;
+    const int n = a.n, nz = a.nz, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int chunk = blockIdx.x, sidx = blockIdx.y, b = blockIdx.z;
     const int angle = a.sel[sidx];
     const uint16_t* ttab = a.ttab + (size_t)angle * a.ttab_stride;  // this angle's tiles
     const float4 cs = a.cs[angle];
     const float c = 0.5f * (float)(n - 1);
     const uint32_t base = smem_u32(tsm), part = part_bytes(n);
-    const uint32_t bars = base + fwd_bar_offset(n);  // Toeplitz slots s at bars + 8 s
-    const uint32_t bar_1 = bars + 16, bar_2 = bars + 24, bar_d = bars + 32;
-    TcTapRow* rows = reinterpret_cast<TcTapRow*>(tsm + fwd_rows_offset(n));  // [2][n]
-    const uint32_t tmem = tc_begin(bars, 5, a.tmem_cols);
-    const uint32_t d1 = tmem, d2 = tmem + (uint32_t)n;
+    const uint32_t bars = base + fwd_bar_offset(n);
+    const uint32_t bar_t = bars, bar_1 = bars + 16, bar_2 = bars + 32, bar_s = bars + 40, bar_a = bars + 48,
+                   bar_d = bars + 56;
+    TcTapRow* rows = reinterpret_cast<TcTapRow*>(tsm + fwd_rows_offset(n));  // [n]
+    if (tid == 0) {
+        for (int q = 0; q < 8; ++q) mbar_init(bars + 8u * q, (q == 5 || q == 6) ? 32u * kWorkers : 1u);
+        mbar_init_fence();
+    }
+    const uint32_t tmem = tc_alloc(bars + kTmemSlot, a.tmem_cols);  // D1[0], D1[1], D2
+    const uint32_t d2 = tmem + 2u * (uint32_t)n;
     const uint32_t idesc = idesc_bf16(kTcM, n);
     const int np = chunk < n ? (n - 1 - chunk) / a.chunks + 1 : 0;
     const float* xb = a.x + (size_t)b * n * n * nz;
     const size_t item = (size_t)b * a.n_sel + sidx;
     float* dst = a.partials ? a.partials + (item * a.chunks + chunk) * (size_t)n * nz : a.out + item * (size_t)n * nz;
-    const int warp = tid >> 5, lane = tid & 31;
     auto plane = [&](int p) { return chunk + p * a.chunks; };
     auto tap = [&](int s) { return base + (uint32_t)s * kTile; };
     auto xbuf = [&](int s) { return base + kFwdSlots * kTile + (uint32_t)s * 2u * part; };
+    auto d1 = [&](int s) { return tmem + (uint32_t)s * (uint32_t)n; };
     auto tsrc = [&](int p) { return ttab + (size_t)plane(p) * kTcM * kTcM; };
     auto arow = [&](int p) -> const float* {
         return a.atten ? a.atten + ((size_t)angle * n + plane(p)) * n * nz : nullptr;
     };
-    TileLoads tl;
-    bool ok = true;
 
-    if (np > 0) {
-        if (tid == 0) {
-            tl.load(0, tap(0), tsrc(0), bars);
-            if (np > 1) tl.load(1, tap(1), tsrc(1), bars);
-        }
-        if (a.atten && np > 1) tc_prefetch_plane(arow(1), n, nz);
-        tc_tap_rows(rows, n, nz, plane(0), cs, c);
-        __syncthreads();
-        if (np > 1) tc_tap_rows(rows + n, n, nz, plane(1), cs, c);  // read after the next barrier
-        tc_stage_plane(xbuf(0), part, rows, xb, arow(0), n, nz, 0u, 0u);
-        fence_async_smem();
-        __syncthreads();
-        bool okt = true;
-        if (tid == 0) {
-            okt = tl.wait(0, bars);
-            if (okt) {
+    if (np == 0) {
+        // a chunk without planes (more chunks than planes): its sum is zero
+        for (int e = tid; e < n * nz; e += blockDim.x) dst[e] = 0.f;
+    } else if (warp == 0) {
+        if (lane == 0) {
+            TileLoads tl;
+            tl.load(0, tap(0), tsrc(0), bar_t);
+            if (np > 1) tl.load(1, tap(1), tsrc(1), bar_t);
+            bool ok = true;
+            for (int p = 0; p < np && ok; ++p) {
+                ok = mbar_wait(bar_s, (uint32_t)p & 1u) && tl.wait(p & 1, bar_t);
+                if (!ok) break;
                 tc_fence_after();
-                issue_gemm1(tap(0), xbuf(0), part, d1, idesc, n, bar_1);
+                issue_gemm1(tap(p & 1), xbuf(p & 1), part, d1(p & 1), idesc, n, bar_1 + 8u * (p & 1));
+                if (p > 0) {
+                    ok = mbar_wait(bar_a, (uint32_t)(p - 1) & 1u);
+                    if (!ok) break;
+                    tc_fence_after();
+                    issue_gemm2(xbuf((p - 1) & 1), part, tap((p - 1) & 1), d2, idesc, n, p > 1, bar_2);
+                    // GEMM 2(p-1) done: its Toeplitz slot takes plane p+1's tile
+                    ok = mbar_wait(bar_2, (uint32_t)(p - 1) & 1u);
+                    if (ok && p + 1 < np) tl.load((p + 1) & 1, tap((p + 1) & 1), tsrc(p + 1), bar_t);
+                }
             }
-        }
-        ok = all_ok(okt, a.err);
-    }
-    for (int p = 0; p < np && ok; ++p) {
-        const bool more = p + 1 < np;
-        bool okw = true;
-        if (more) {
-            if (p + 2 < np) {  // the table of plane p was read by its staging, before the last barrier
-                tc_tap_rows(rows + (p & 1) * n, n, nz, plane(p + 2), cs, c);
-                if (a.atten) tc_prefetch_plane(arow(p + 2), n, nz);
+            if (ok) {
+                ok = mbar_wait(bar_a, (uint32_t)(np - 1) & 1u);
+                if (ok) {
+                    tc_fence_after();
+                    issue_gemm2(xbuf((np - 1) & 1), part, tap((np - 1) & 1), d2, idesc, n, np > 1, bar_2);
+                }
             }
-            // X[(p+1)&1] last held the A operand of GEMM 2(p-1)
-            okw = tc_stage_plane(xbuf((p + 1) & 1), part, rows + ((p + 1) & 1) * n, xb, arow(p + 1), n, nz,
-                                 p > 0 ? bar_2 : 0u, (uint32_t)(p - 1) & 1u);
-            // GEMM 2(p-1) has also released the Toeplitz slot of plane p+1
-            if (tid == 0 && p > 0 && okw) tl.load((p + 1) & 1, tap((p + 1) & 1), tsrc(p + 1), bars);
-        } else if (p > 0) {
-            okw = mbar_wait(bar_2, (uint32_t)(p - 1) & 1u);  // keep the waits on bar_2 one phase apart
+            if (!ok) {
+                report_timeout(a.err);
+                tl.drain(bar_t, kFwdSlots);
+            }
+            tc_drain(bar_d);
         }
-        // GEMM 1(p) is done: D1 becomes the A operand of GEMM 2(p), over
-        // GEMM 1(p)'s B operand in X[p&1]
-        const bool ok1 = mbar_wait(bar_1, (uint32_t)p & 1u);
-        tc_fence_after();
-        if (ok1) d1_to_a2(xbuf(p & 1), part, d1, n);
+        __syncwarp();
+    } else {
+        const int wi = warp - 1;
+        if (a.atten && np > 1) prefetch_rows(arow(1), n, nz, wi);
+        bool ok = stage_rows(xbuf(0), part, rows, xb, arow(0), n, nz, plane(0), cs, c, wi, 0u, 0u);
         fence_async_smem();
-        tc_fence_before();
-        ok = all_ok(okw && ok1, a.err);
-        if (!ok) break;
-        if (tid == 0) {
+        mbar_arrive(bar_s);
+        for (int p = 0; p < np && ok; ++p) {
+            if (p + 1 < np) {
+                if (a.atten && p + 2 < np) prefetch_rows(arow(p + 2), n, nz, wi);
+                // X[(p+1)&1] last held the A operand of GEMM 2(p-1)
+                ok = stage_rows(xbuf((p + 1) & 1), part, rows, xb, arow(p + 1), n, nz, plane(p + 1), cs, c, wi,
+                                p > 0 ? bar_2 : 0u, (uint32_t)(p - 1) & 1u);
+                fence_async_smem();
+                mbar_arrive(bar_s);
+            } else if (p > 0) {
+                ok = mbar_wait(bar_2, (uint32_t)(p - 1) & 1u);  // keep this warp's waits on bar_2 in order
+            }
+            if (!ok) break;
+            // GEMM 1(p) is done: D1[p&1] becomes the A operand of GEMM 2(p),
+            // over GEMM 1(p)'s B operand in X[p&1]
+            ok = mbar_wait(bar_1 + 8u * (p & 1), (uint32_t)(p >> 1) & 1u);
+            if (!ok) break;
             tc_fence_after();
-            issue_gemm2(xbuf(p & 1), part, tap(p & 1), d2, idesc, n, p > 0, bar_2);
-            if (more && tl.wait((p + 1) & 1, bars))
-                issue_gemm1(tap((p + 1) & 1), xbuf((p + 1) & 1), part, d1, idesc, n, bar_1);
+            d1_to_a2(xbuf(p & 1), part, d1(p & 1), n);
+            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(bar_a);
         }
-        __syncwarp();  // warp 0 reconverges before its next warp-wide TMEM access
-    }
-    if (ok && np > 0) {
-        ok = all_ok(mbar_wait(bar_2, (uint32_t)(np - 1) & 1u), a.err);
+        if (ok) ok = mbar_wait(bar_2, (uint32_t)(np - 1) & 1u);  // the last GEMM 2
         if (ok) {
             // D2 = (sum over the chunk's planes)^T: lanes k, columns j
             tc_fence_after();
-            const int k = 32 * (warp & 3) + lane;
-            for (int cc = 16 * (warp >> 2); cc < n; cc += 64) {
+            const int k = 32 * tm_quad(warp) + lane;
+            for (int cc = tm_col0(warp); cc < n; cc += 64) {
                 float v[16];
-                tc_ld16(d2 + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)cc, v);
+                tc_ld16(d2 + ((uint32_t)(32 * tm_quad(warp)) << 16) + (uint32_t)cc, v);
                 if (k < nz) {
 #pragma unroll
                     for (int q = 0; q < 16; ++q) dst[(size_t)(cc + q) * nz + k] = v[q];
                 }
             }
+        } else if (lane == 0) {
+            report_timeout(a.err);
         }
-    } else if (ok) {
-        // a chunk without planes (more chunks than planes): its sum is zero
-        for (int e = tid; e < n * nz; e += blockDim.x) dst[e] = 0.f;
-    }
-    if (!ok && tid == 0) {
-        tl.drain(bars, kFwdSlots);
-        tc_drain(bar_d);
     }
     tc_end(tmem, a.tmem_cols);
 }
@@ -547,121 +565,150 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
 // ---------------------------------------------------------------- back blur
 //
 // The projection of the angle is the B operand of every plane's GEMM 1.
-// Per iteration p: GEMM 1(p) done (and with it GEMM 2(p - 1)) -> D1 to A2
-// -> one thread issues GEMM 2(p) into D2[p & 1] and GEMM 1(p + 1); the CUDA
-// cores meanwhile finish plane p - 1 from D2[(p - 1) & 1]: times A, stored
-// as B.  Three Toeplitz slots: the tile of plane p + 2 is copied into the
-// slot of plane p - 1 once GEMM 2(p - 1) is done.
+// Plane p: GEMM 1(p) into D1[p & 1]; the workers hand D1 over to A2; GEMM
+// 2(p) into D2[p & 1]; the workers finish the plane from D2: times A, stored
+// as B.  The issuer keeps GEMM 1 two planes ahead (D1 double buffered) and
+// issues GEMM 2(p) once A2 holds plane p and the workers have finished plane
+// p - 2 from the same D2 buffer.  Three Toeplitz slots: plane p + 3's tile
+// goes into plane p's slot once GEMM 2(p) is done.
+//
+// Barriers (bars + 8 q): q = 0..2 Toeplitz slots; 3, 4 GEMM 1 into D1[0],
+// D1[1]; 5, 6 GEMM 2 into D2[0], D2[1]; 7 projection staged (every worker
+// thread arrives); 8 A2 handed over (every worker thread); 9, 10 plane
+// finished from D2[0], D2[1] (every worker thread); 11 final drain.
 
 __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackBf16Args a)
 {
     extern __shared__ __align__(1024) unsigned char tsm[];
-    const int n = a.n, nz = a.nz, tid = threadIdx.x;
+    const int n = a.n, nz = a.nz, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int chunk = blockIdx.x, sidx = blockIdx.y, b = blockIdx.z;
     const int angle = a.sel[sidx];
     const uint16_t* ttab = a.ttab + (size_t)angle * a.ttab_stride;  // this angle's tiles
     const uint32_t base = smem_u32(tsm), part = part_bytes(n);
-    const uint32_t bars = base + back_bar_offset(n);  // Toeplitz slots s at bars + 8 s
-    const uint32_t bar_1 = bars + 24, bar_2 = bars + 32, bar_d = bars + 40;
-    const uint32_t tmem = tc_begin(bars, 6, a.tmem_cols);
-    const uint32_t d1 = tmem;
+    const uint32_t bars = base + back_bar_offset(n);
+    const uint32_t bar_t = bars, bar_1 = bars + 24, bar_2 = bars + 40, bar_s = bars + 56, bar_a = bars + 64,
+                   bar_f = bars + 72, bar_d = bars + 88;
+    if (tid == 0) {
+        for (int q = 0; q < 12; ++q) mbar_init(bars + 8u * q, (q >= 7 && q <= 10) ? 32u * kWorkers : 1u);
+        mbar_init_fence();
+    }
+    const uint32_t tmem = tc_alloc(bars + kTmemSlot, a.tmem_cols);  // D1[0], D1[1], D2[0], D2[1]
     const uint32_t b1 = base + kBackSlots * kTile, a2 = b1 + 2u * part;
     const uint32_t idesc = idesc_bf16(kTcM, n);
     const int np = chunk < n ? (n - 1 - chunk) / a.chunks + 1 : 0;
     const size_t item = (size_t)b * a.n_sel + sidx;
     const float* pr = a.proj ? a.proj + (size_t)b * a.proj_bstride + (size_t)sidx * n * nz : nullptr;
     float* bvol = a.bvol + item * (size_t)n * n * nz;
-    const int warp = tid >> 5, lane = tid & 31;
-    const int k = 32 * (warp & 3) + lane;
-    const uint32_t quad = (uint32_t)(32 * (warp & 3)) << 16;  // this warp's TMEM lane quadrant
     auto plane = [&](int p) { return chunk + p * a.chunks; };
     auto tap = [&](int s) { return base + (uint32_t)s * kTile; };
-    auto d2 = [&](int s) { return tmem + (uint32_t)n * (1u + (uint32_t)s); };
+    auto d1 = [&](int s) { return tmem + (uint32_t)s * (uint32_t)n; };
+    auto d2 = [&](int s) { return tmem + (uint32_t)(2 + s) * (uint32_t)n; };
     auto tsrc = [&](int p) { return ttab + (size_t)plane(p) * kTcM * kTcM; };
     auto arow = [&](int p) -> const float* {
         return a.atten ? a.atten + ((size_t)angle * n + plane(p)) * n * nz : nullptr;
     };
-    // A of plane p for this thread's elements (lane k, columns cc + q of its
-    // at most two 16-column chunks), loaded ahead of the waits
-    auto load_a = [&](int p, float (&aw)[2][16]) {
-        const float* ar = arow(p);
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            const int cc = 16 * (warp >> 2) + 64 * m;
-#pragma unroll
-            for (int q = 0; q < 16; ++q) aw[m][q] = (ar && cc < n && k < nz) ? __ldg(ar + (size_t)(cc + q) * nz + k) : 1.f;
-        }
-    };
-    // B[plane p][j][k] = A * (K_i r)[j][k]; D2 holds (K_i r)^T (lanes k)
-    auto finish = [&](int p, const float (&aw)[2][16]) {
-        float* brow = bvol + (size_t)plane(p) * n * nz;
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            const int cc = 16 * (warp >> 2) + 64 * m;
-            if (cc < n) {
-                float v[16];
-                tc_ld16(d2(p & 1) + quad + (uint32_t)cc, v);
-                if (k < nz) {
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) brow[(size_t)(cc + q) * nz + k] = v[q] * aw[m][q];
+
+    if (np > 0 && warp == 0) {
+        if (lane == 0) {
+            TileLoads tl;
+            for (int s = 0; s < kBackSlots && s < np; ++s) tl.load(s, tap(s), tsrc(s), bar_t);
+            bool ok = mbar_wait(bar_s, 0u);
+            for (int q = 0; q < 2 && q < np && ok; ++q) {
+                ok = tl.wait(q, bar_t);
+                if (ok) {
+                    tc_fence_after();
+                    issue_gemm1(tap(q), b1, part, d1(q), idesc, n, bar_1 + 8u * q);
                 }
             }
-        }
-    };
-    TileLoads tl;
-    bool ok = true;
-
-    if (np > 0 && tid == 0)
-        for (int s = 0; s < kBackSlots && s < np; ++s) tl.load(s, tap(s), tsrc(s), bars);
-    if (np > 0 && a.atten) tc_prefetch_plane(arow(0), n, nz);
-    tc_stage_proj(b1, part, pr, a.fov ? a.fov + (size_t)angle * n * nz : nullptr, n, nz);
-    fence_async_smem();
-    __syncthreads();
-    if (np > 0) {
-        bool okt = true;
-        if (tid == 0) {
-            okt = tl.wait(0, bars);
-            if (okt) {
+            for (int p = 0; p < np && ok; ++p) {
+                ok = mbar_wait(bar_a, (uint32_t)p & 1u);  // A2 holds plane p
+                // D2[p&1] was last read by the finish of plane p-2
+                if (ok && p >= 2) ok = mbar_wait(bar_f + 8u * (p & 1), (uint32_t)((p - 2) >> 1) & 1u);
+                if (!ok) break;
                 tc_fence_after();
-                issue_gemm1(tap(0), b1, part, d1, idesc, n, bar_1);
+                issue_gemm2(a2, part, tap(p % 3), d2(p & 1), idesc, n, false, bar_2 + 8u * (p & 1));
+                // GEMM 2(p) done: A2 is free and plane p's Toeplitz slot takes plane p+3's tile
+                ok = mbar_wait(bar_2 + 8u * (p & 1), (uint32_t)(p >> 1) & 1u);
+                if (!ok) break;
+                if (p + 3 < np) tl.load(p % 3, tap(p % 3), tsrc(p + 3), bar_t);
+                if (p + 2 < np) {
+                    ok = tl.wait((p + 2) % 3, bar_t);
+                    if (ok) issue_gemm1(tap((p + 2) % 3), b1, part, d1(p & 1), idesc, n, bar_1 + 8u * (p & 1));
+                }
+            }
+            if (!ok) {
+                report_timeout(a.err);
+                tl.drain(bar_t, kBackSlots);
+            }
+            tc_drain(bar_d);
+        }
+        __syncwarp();
+    } else if (np > 0) {
+        const int wi = warp - 1;
+        const int k = 32 * tm_quad(warp) + lane, col0 = tm_col0(warp);
+        const uint32_t quad = (uint32_t)(32 * tm_quad(warp)) << 16;
+        // A of plane p for this thread's elements (lane k, columns cc + q of
+        // its at most two 16-column chunks), loaded ahead of the waits
+        auto load_a = [&](int p, float (&aw)[2][16]) {
+            const float* ar = arow(p);
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                const int cc = col0 + 64 * m;
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    aw[m][q] = (ar && cc < n && k < nz) ? __ldg(ar + (size_t)(cc + q) * nz + k) : 1.f;
+            }
+        };
+        // B[plane p][j][k] = A * (K_i r)[j][k]; D2 holds (K_i r)^T (lanes k)
+        auto finish = [&](int p, const float (&aw)[2][16]) {
+            float* brow = bvol + (size_t)plane(p) * n * nz;
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                const int cc = col0 + 64 * m;
+                if (cc < n) {
+                    float v[16];
+                    tc_ld16(d2(p & 1) + quad + (uint32_t)cc, v);
+                    if (k < nz) {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) brow[(size_t)(cc + q) * nz + k] = v[q] * aw[m][q];
+                    }
+                }
+            }
+        };
+        if (a.atten) prefetch_rows(arow(0), n, nz, wi);
+        stage_proj_rows(b1, part, pr, a.fov ? a.fov + (size_t)angle * n * nz : nullptr, n, nz, wi);
+        fence_async_smem();
+        mbar_arrive(bar_s);
+        bool ok = true;
+        for (int p = 0; p < np && ok; ++p) {
+            float aw[2][16];
+            if (p > 0) load_a(p - 1, aw);
+            if (a.atten && p + 1 < np) prefetch_rows(arow(p + 1), n, nz, wi);
+            // GEMM 1(p) done; GEMM 2(p-1) done: A2 is free and D2[(p-1)&1] ready
+            ok = mbar_wait(bar_1 + 8u * (p & 1), (uint32_t)(p >> 1) & 1u);
+            if (ok && p > 0) ok = mbar_wait(bar_2 + 8u * ((p - 1) & 1), (uint32_t)((p - 1) >> 1) & 1u);
+            if (!ok) break;
+            tc_fence_after();
+            d1_to_a2(a2, part, d1(p & 1), n);
+            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(bar_a);
+            if (p > 0) {
+                finish(p - 1, aw);
+                tc_fence_before();
+                mbar_arrive(bar_f + 8u * ((p - 1) & 1));
             }
         }
-        ok = all_ok(okt, a.err);
-    }
-    for (int p = 0; p < np && ok; ++p) {
-        float aw[2][16];
-        if (p > 0) load_a(p - 1, aw);
-        if (a.atten && p + 1 < np) tc_prefetch_plane(arow(p + 1), n, nz);
-        // GEMM 1(p) done; so is GEMM 2(p-1), issued before it: A2, D2[(p-1)&1]
-        // and the Toeplitz slot of plane p-1 are free
-        const bool ok1 = mbar_wait(bar_1, (uint32_t)p & 1u);
-        if (tid == 0 && ok1 && p > 0 && p + 2 < np) tl.load((p + 2) % 3, tap((p + 2) % 3), tsrc(p + 2), bars);
-        tc_fence_after();
-        if (ok1) d1_to_a2(a2, part, d1, n);
-        fence_async_smem();
-        tc_fence_before();
-        ok = all_ok(ok1, a.err);
-        if (!ok) break;
-        if (tid == 0) {
-            tc_fence_after();
-            issue_gemm2(a2, part, tap(p % 3), d2(p & 1), idesc, n, false, p + 1 == np ? bar_2 : 0u);
-            if (p + 1 < np && tl.wait((p + 1) % 3, bars)) issue_gemm1(tap((p + 1) % 3), b1, part, d1, idesc, n, bar_1);
-        }
-        __syncwarp();  // warp 0 reconverges before its warp-wide TMEM loads
-        if (p > 0) finish(p - 1, aw);
-    }
-    if (ok && np > 0) {
-        float aw[2][16];
-        load_a(np - 1, aw);
-        ok = all_ok(mbar_wait(bar_2, 0u), a.err);  // the last GEMM 2
         if (ok) {
-            tc_fence_after();
-            finish(np - 1, aw);
+            float aw[2][16];
+            load_a(np - 1, aw);
+            ok = mbar_wait(bar_2 + 8u * ((np - 1) & 1), (uint32_t)((np - 1) >> 1) & 1u);  // the last GEMM 2
+            if (ok) {
+                tc_fence_after();
+                finish(np - 1, aw);
+            }
         }
-    }
-    if (!ok && tid == 0) {
-        tl.drain(bars, kBackSlots);
-        tc_drain(bar_d);
+        if (!ok && lane == 0) report_timeout(a.err);
     }
     tc_end(tmem, a.tmem_cols);
 }

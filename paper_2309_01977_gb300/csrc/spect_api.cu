@@ -311,7 +311,7 @@ int run_forward(spect_plan* p, spect_plan_scratch& sc, const float* x, float* ou
             a.n_sel = n_sel;
             a.batch = nb;
             a.chunks = chunks;
-            a.tmem_cols = bf16_tmem_cols(p->n, 2);  // D1, D2
+            a.tmem_cols = bf16_tmem_cols(p->n, 3);  // D1 twice, D2
             a.out = out + (size_t)b0 * n_sel * plane;
             a.partials = use_partials ? sc.partials : nullptr;
             a.err = p->d_err;
@@ -397,7 +397,7 @@ int run_back(spect_plan* p, spect_plan_scratch& sc, const float* proj, float* x_
                 bb.n_sel = ng;
                 bb.batch = nb;
                 bb.chunks = chunk_target(p, (long)nb * ng);
-                bb.tmem_cols = bf16_tmem_cols(p->n, 3);  // D1, D2 twice
+                bb.tmem_cols = bf16_tmem_cols(p->n, 4);  // D1 twice, D2 twice
                 bb.bvol = sc.bvol;
                 bb.err = p->d_err;
                 e = timed(p, "blur_back_bf16", st, 1, [&] { return launch_blur_back_bf16(bb, st); });
