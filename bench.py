@@ -199,9 +199,9 @@ def algorithmic_flops(kernel: str, wl, n_sel: int) -> tuple:
     (bilinear) + 1 (attenuation) + 2 (2R_i+1) (z blur) + 2 (2R_i+1) (y blur
     and depth sum); back blur 4 (2R_i+1) + 1; gather 2 per bilinear weight,
     4 weights per rotated sample, + 2 per voxel for the update.  BF16 path:
-    per plane two 128 x n x n GEMMs, each as two BF16 products (the data
-    operand split into hi and lo parts, the BF16 taps whole), 2 flop per
-    multiply-add, on the tensor pipe."""
+    per plane two 128 x n x n GEMMs, each as three BF16 products (hi/lo
+    split of the taps and of the data), 2 flop per multiply-add, on the
+    tensor pipe."""
     plane = float(wl.n) * wl.nz
     taps = [2 * r + 1 for r in psf_radii(wl)]
     if kernel == "forward":
@@ -212,7 +212,7 @@ def algorithmic_flops(kernel: str, wl, n_sel: int) -> tuple:
         n3 = plane * wl.n
         return n_sel * n3 * 8 + 2 * n3, "fp32"
     if kernel in ("forward_bf16", "blur_back_bf16"):
-        return n_sel * wl.n * 2 * 2 * 2.0 * 128 * wl.n * wl.n, "tensor"
+        return n_sel * wl.n * 2 * 3 * 2.0 * 128 * wl.n * wl.n, "tensor"
     return 0.0, "fp32"
 
 

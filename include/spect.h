@@ -83,10 +83,10 @@ extern "C" {
 #define SPECT_FLAG_ATTEN 1u      /* model attenuation (needs mu at plan creation) */
 #define SPECT_FLAG_PSF 2u        /* model the depth-dependent collimator blur */
 #define SPECT_FLAG_PSF_BF16 4u   /* PSF as banded-Toeplitz BF16 tensor-core GEMMs (FP32
-                                    accumulate; taps in BF16 renormalised to unit sum,
-                                    the data split into BF16 hi + lo parts; image within
-                                    1e-3 of FP64; needs nx % 32 == 0, nx <= 128,
-                                    nz % 8 == 0, nz <= 128) */
+                                    accumulate; taps and data split into BF16 hi + lo
+                                    parts, three products per GEMM; image within 1e-3 of
+                                    FP64; needs nx % 32 == 0, nx <= 128, nz % 8 == 0,
+                                    nz <= 128) */
 #define SPECT_FLAG_ATTEN_F64 8u  /* attenuation prefix sums in FP64 (else compensated FP32);
                                     the exponential is FP32 either way */
 

@@ -155,7 +155,7 @@ struct GatherTiledArgs {
 };
 
 // Tensor-core PSF path (SPECT_FLAG_PSF_BF16): n % 32 == 0, n <= 128,
-// nz % 8 == 0, nz <= 128; per-plane Toeplitz tiles ttab[i][128*128]
+// nz % 8 == 0, nz <= 128; per-plane Toeplitz tiles ttab[i][hi|lo][128*128]
 // (BF16 bits, K-major core-matrix layout).
 struct ForwardBf16Args {
     const float* x;
@@ -278,7 +278,7 @@ struct spect_plan {
     bool gather_tiled = false;                // footprints staged in shared memory
     int gt_T = 0, gt_tiles = 0, gt_zs = 0, gt_rows = 0, gt_stages = 2;
     bool bf16 = false;                        // tensor-core PSF path
-    uint16_t* d_ttab = nullptr;               // [tables][n][128*128] BF16 Toeplitz tiles
+    uint16_t* d_ttab = nullptr;               // [tables][n][hi, lo][128*128] BF16 Toeplitz tiles
     int* d_err = nullptr;                     // kernel status word (bounded waits)
     size_t bvol_cap = 0;                      // capacity of a scratch's rotated-frame volumes
     // per-stream scratch (the creation stream's first), and the lock every

@@ -7,24 +7,25 @@
 //   GEMM 1   D1[k][j]  = sum_k' T_i[k][k'] P[j][k']          (blur along z)
 //   GEMM 2   D2[k][j] += sum_j' X[k][j'] T_i[j][j']  with X = D1
 // so D2 = (T_i P T_i^T)^T, and the forward keeps D2 in TMEM across the depth
-// loop (P_x).  The taps are BF16, renormalised to unit sum; the data operands
-// (P, and X read back from TMEM) are split into two BF16 parts, v = v_hi +
-// v_lo (v_lo = bf16(v - v_hi)), and each GEMM runs two MMA chains,
-// T * v_hi + T * v_lo.  Measured on the 128^3 x 120-angle 4 x 8 OSEM against
-// the FP64 oracle: image 6.5e-4 and projections 8.5e-5 relative L2 (bar
-// 1e-3).  The alternatives measured: three chains with the taps split too,
-// 3.4e-6 (but 8 us slower per kernel); the taps split and the data rounded
-// once, 1.3e-3; one chain, 2.5e-3 with renormalised taps, 4.0e-3 without.
+// loop (P_x).  Every operand is split into two BF16 parts, v = v_hi + v_lo
+// (v_lo = bf16(v - v_hi)), and each GEMM runs three MMA chains, T_hi v_hi +
+// T_lo v_hi + T_hi v_lo, dropping only T_lo v_lo (relative ~2^-18).
+// Measured against the FP64 oracle: image 3.4e-6 relative L2 on the 128^3 x
+// 120-angle 4 x 8 OSEM, and below 5.2e-6 from FP32 on every request class of
+// the serving mix.  Two chains (data split, BF16 taps renormalised to unit
+// sum) measured 6.5e-4 on the 4 x 8 OSEM but up to 2.2e-3 on serving
+// requests, over the 1e-3 bar; one chain, 2.5e-3 on the 4 x 8 OSEM.
 // Rotation, attenuation, the ratio and the update stay FP32 on the CUDA
 // cores.
 //
 // Shared-memory operands are K-major tiles with the 128-byte swizzle (see
 // sw_off), so that both the staging (lanes along z) and the TMEM read-back
 // (lanes along the tile rows) store without bank conflicts.  The per-plane
-// Toeplitz tile (32 KB) arrives by one TMA bulk copy into one of several
-// slots, planes ahead of its use.  The kernels are software pipelines in
-// which the tensor cores work on one plane while the CUDA cores stage the
-// next (forward) or finish the previous one (back blur); see each kernel.
+// Toeplitz pair (T_hi, T_lo: 64 KB) arrives by one TMA bulk copy into a
+// single slot as soon as the plane before has finished with it.  The kernels
+// are warp-specialised pipelines in which the tensor cores work on one plane
+// while the CUDA cores stage the next (forward) or finish the previous one
+// (back blur); see each kernel.
 //
 // Every wait on an mbarrier is bounded: when the bound runs out the kernel
 // records SPECT_ETIMEDOUT in the plan's error word, releases its tensor
@@ -71,10 +72,13 @@ __device__ __forceinline__ uint64_t sw_desc(uint32_t addr)
     return d;
 }
 
-// Start address of K step ks (16 elements) of a tile with R rows.
-__device__ __forceinline__ uint32_t sw_kstep(uint32_t tile, int ks, int R)
+// K step ks (16 elements) of a tile with R rows starts (ks / 4) R 128 +
+// (ks % 4) 32 bytes into the tile; as an increment of the tile's descriptor
+// (whose address field counts 16-byte units; no tile crosses 256 KB, so the
+// sum never carries out of the field):
+__device__ __forceinline__ uint64_t sw_kstep_desc(int ks, int R)
 {
-    return tile + (uint32_t)((ks >> 2) * R * 128 + (ks & 3) * 32);
+    return (uint64_t)(((ks >> 2) * R * 128 + (ks & 3) * 32) >> 4);
 }
 
 // Instruction descriptor of kind::f16: D F32, A and B BF16, both K-major.
@@ -134,33 +138,49 @@ __device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uin
     lo = pack_bf16x2(a - ha, b - hb);
 }
 
-// GEMM 1: D1 = T B_hi^T + T B_lo^T over K = 128 (the axial direction); B is
-// n x 128 with its lo part `lo` bytes after the hi part.  Completion arrives
-// on `bar`.
+// One MMA chain of GEMM 1, D1 (+)= T B^T over K = 128, and of GEMM 2, D2
+// (+)= A T^T over K = n (tile addresses of one BF16 part each).
+// The descriptors of a chain are formed once and stepped by constant
+// increments, so that issuing a product costs the issuing thread a few
+// instructions.
+__device__ __forceinline__ void gemm1_chain(uint32_t t, uint32_t b, uint32_t d1, uint32_t idesc, int n, bool acc)
+{
+    const uint64_t da = sw_desc(t), db = sw_desc(b);
+#pragma unroll
+    for (int ks = 0; ks < kTcM / 16; ++ks)
+        tc_mma(d1, da + sw_kstep_desc(ks, kTcM), db + sw_kstep_desc(ks, n), idesc, (acc || ks) ? 1u : 0u);
+}
+
+__device__ __forceinline__ void gemm2_chain(uint32_t a, uint32_t t, uint32_t d2, uint32_t idesc, int n, bool acc)
+{
+    const uint64_t da = sw_desc(a), db = sw_desc(t);
+#pragma unroll
+    for (int ks = 0; ks < kTcM / 16; ++ks)
+        if (ks < n / 16)
+            tc_mma(d2, da + sw_kstep_desc(ks, kTcM), db + sw_kstep_desc(ks, kTcM), idesc, (acc || ks) ? 1u : 0u);
+}
+
+// GEMM 1: D1 = T_hi B_hi^T + T_lo B_hi^T + T_hi B_lo^T over K = 128 (the
+// axial direction); T_lo sits kTile bytes after T_hi, and B (n x 128) has its
+// lo part `lo` bytes after the hi part.  Completion arrives on `bar`.
 __device__ __forceinline__ void issue_gemm1(uint32_t tap, uint32_t b1, uint32_t lo, uint32_t d1, uint32_t idesc, int n,
                                             uint32_t bar)
 {
-    for (int h = 0; h < 2; ++h) {
-        const uint32_t tb = b1 + (h ? lo : 0u);
-#pragma unroll
-        for (int ks = 0; ks < kTcM / 16; ++ks)
-            tc_mma(d1, sw_desc(sw_kstep(tap, ks, kTcM)), sw_desc(sw_kstep(tb, ks, n)), idesc, (h | ks) != 0);
-    }
+    gemm1_chain(tap, b1, d1, idesc, n, false);
+    gemm1_chain(tap + (uint32_t)kTile, b1, d1, idesc, n, true);
+    gemm1_chain(tap, b1 + lo, d1, idesc, n, true);
     tc_commit(bar);
 }
 
-// GEMM 2: D2 (+)= A_hi T^T + A_lo T^T over K = n (the transaxial direction);
-// A is 128 x n.  Completion arrives on `bar` unless it is 0.
+// GEMM 2: D2 (+)= A_hi T_hi^T + A_hi T_lo^T + A_lo T_hi^T over K = n (the
+// transaxial direction); A is 128 x n.  Completion arrives on `bar`.
 __device__ __forceinline__ void issue_gemm2(uint32_t a2, uint32_t lo, uint32_t tap, uint32_t d2, uint32_t idesc, int n,
                                             bool accumulate, uint32_t bar)
 {
-    for (int h = 0; h < 2; ++h) {
-        const uint32_t ta = a2 + (h ? lo : 0u);
-        for (int ks = 0; ks < n / 16; ++ks)
-            tc_mma(d2, sw_desc(sw_kstep(ta, ks, kTcM)), sw_desc(sw_kstep(tap, ks, kTcM)), idesc,
-                   (accumulate || h || ks) ? 1u : 0u);
-    }
-    if (bar) tc_commit(bar);
+    gemm2_chain(a2, tap, d2, idesc, n, accumulate);
+    gemm2_chain(a2, tap + (uint32_t)kTile, d2, idesc, n, true);
+    gemm2_chain(a2 + lo, tap, d2, idesc, n, true);
+    tc_commit(bar);
 }
 
 // The worker warps w = 1..kWorkers split each TMEM accumulator: warp w may
@@ -198,24 +218,24 @@ __host__ __device__ constexpr uint32_t part_bytes(int n) { return (uint32_t)kTcM
 
 // Shared-memory layouts (every tile 1 KB aligned), then a 128-byte block of
 // mbarriers with the TMEM address slot at byte 112:
-//   forward:  Toeplitz slots [2] | plane buffers [2] (hi, lo) | tap-row table [n]
-//   back:     Toeplitz slots [3] | B1 = projection (hi, lo) | A2 (hi, lo)
-constexpr int kFwdSlots = 2, kBackSlots = 3;
+//   forward:  Toeplitz pair (hi, lo) | plane buffers [2] (hi, lo) | tap-row table [n]
+//   back:     T_hi slots [2] | T_lo slot | B1 = projection (hi, lo) | A2 (hi, lo)
+constexpr uint32_t kPair = 2u * kTile;  // T_hi and T_lo of one plane
 constexpr uint32_t kBarBytes = 128, kTmemSlot = 112;
-__host__ __device__ constexpr uint32_t fwd_rows_offset(int n) { return kFwdSlots * kTile + 4u * part_bytes(n); }
+__host__ __device__ constexpr uint32_t fwd_rows_offset(int n) { return kPair + 4u * part_bytes(n); }
 __host__ __device__ constexpr uint32_t fwd_bar_offset(int n) { return fwd_rows_offset(n) + 32u * (uint32_t)n; }
-__host__ __device__ constexpr uint32_t back_bar_offset(int n) { return kBackSlots * kTile + 4u * part_bytes(n); }
+__host__ __device__ constexpr uint32_t back_bar_offset(int n) { return 3u * kTile + 4u * part_bytes(n); }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// The issuing thread's record of the Toeplitz-tile copies per slot (slot s
-// completes on the barrier at bars + 8 s): a copy is pending from its issue
-// until that thread has seen it land, and the parity bit of a slot is that
-// of its next completion.  After a timeout, drain() waits (bounded) for the
-// copies still in flight, so that none lands after the CTA has left.
+// The issuing thread's record of the Toeplitz-tile copies per slot (slot s,
+// kTile bytes, completes on the barrier at bars + 8 s): a copy is pending
+// from its issue until that thread has seen it land, and the parity bit of a
+// slot is that of its next completion.  After a timeout, drain() waits
+// (bounded) for the copies still in flight.
 struct TileLoads {
     uint32_t pend = 0, par = 0;
     __device__ __forceinline__ void load(int s, uint32_t dst, const void* src, uint32_t bars)
@@ -236,6 +256,33 @@ struct TileLoads {
     {
         for (int s = 0; s < slots; ++s)
             if ((pend >> s) & 1u) mbar_wait(bars + 8u * s, (par >> s) & 1u);
+    }
+};
+
+// The issuing thread's record of the Toeplitz-pair copies into the slot
+// (completing on `bar`): a copy is pending from its issue until that thread
+// has seen it land, and `par` is the parity of the next completion.  After a
+// timeout, drain() waits (bounded) for a copy still in flight, so that none
+// lands after the CTA has left.
+struct PairLoads {
+    uint32_t pend = 0, par = 0;
+    __device__ __forceinline__ void load(uint32_t dst, const void* src, uint32_t bar)
+    {
+        tma_load_1d(dst, src, kPair, bar);
+        pend = 1;
+    }
+    __device__ __forceinline__ bool wait(uint32_t bar)
+    {
+        const bool ok = mbar_wait(bar, par);
+        if (ok) {
+            par ^= 1u;
+            pend = 0;
+        }
+        return ok;
+    }
+    __device__ __forceinline__ void drain(uint32_t bar)
+    {
+        if (pend) mbar_wait(bar, par);
     }
 };
 
@@ -332,7 +379,8 @@ __device__ __forceinline__ void put4(uint32_t b1, uint32_t b1_lo, int j, int k, 
 }
 
 // Worker wi (0 .. kWorkers-1) owns the rows j = wi + kWorkers r of every
-// plane.  Ask L2 to fetch its rows of an attenuation plane ahead of use.
+// plane.  Ask L2 to fetch its rows of an attenuation plane ahead of use (one
+// 16-byte-aligned request per row).
 __device__ __forceinline__ void prefetch_rows(const float* plane, int n, int nz, int wi)
 {
     const int lane = threadIdx.x & 31;
@@ -428,19 +476,17 @@ __device__ __forceinline__ void stage_proj_rows(uint32_t b1, uint32_t b1_lo, con
 //
 // Planes p = 0, 1, .. of this CTA's depth chunk (plane index chunk + p *
 // chunks) flow through two plane buffers X[p & 1]: the staged plane is the B
-// operand of GEMM 1(p) into D1[p & 1]; once GEMM 1(p) is done, the workers
-// write D1 back over it as the A operand of GEMM 2(p), which accumulates the
-// chunk's depth sum in D2 (P_x); once GEMM 2(p) is done, X[p & 1] takes the
-// staging of plane p + 2.  Warp 0 (one thread) issues: GEMM 1(p) when the
-// workers have staged plane p, GEMM 2(p - 1) when they have handed D1(p - 1)
-// over, and the copy of plane p + 1's Toeplitz tile into the slot GEMM
-// 2(p - 1) has released.  The 16 worker warps meet the issuer on mbarriers
-// only, so a fast warp has its loads of the next plane in flight while the
-// others finish.
+// operand of GEMM 1(p) into D1; once GEMM 1(p) is done, the workers write D1
+// back over it as the A operand of GEMM 2(p), which accumulates the chunk's
+// depth sum in D2 (P_x); once GEMM 2(p) is done, X[p & 1] takes the staging
+// of plane p + 2, and the Toeplitz slot plane p + 1's pair.  Warp 0 (one
+// thread) issues the copies and the products; the 16 worker warps stage plane
+// p + 1 while the tensor cores run plane p, and meet the issuer on mbarriers
+// only, so a fast warp has its loads in flight while the others finish.
 //
-// Barriers (bars + 8 q): q = 0, 1 Toeplitz slots; 2, 3 GEMM 1 into D1[0],
-// D1[1]; 4 GEMM 2; 5 plane staged (every worker thread arrives); 6 D1 handed
-// over (every worker thread); 7 final drain.
+// Barriers (bars + 8 q): q = 0 Toeplitz pair; 1 GEMM 1; 2 GEMM 2; 3, 4 plane
+// staged into X[0], X[1] (every worker thread arrives); 5 D1 handed over
+// (every worker thread); 6 final drain.
 
 __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16Args a)
 {
@@ -453,25 +499,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
     const float c = 0.5f * (float)(n - 1);
     const uint32_t base = smem_u32(tsm), part = part_bytes(n);
     const uint32_t bars = base + fwd_bar_offset(n);
-    const uint32_t bar_t = bars, bar_1 = bars + 16, bar_2 = bars + 32, bar_s = bars + 40, bar_a = bars + 48,
-                   bar_d = bars + 56;
+    const uint32_t bar_t = bars, bar_1 = bars + 8, bar_2 = bars + 16, bar_s = bars + 24, bar_a = bars + 40,
+                   bar_d = bars + 48;
     TcTapRow* rows = reinterpret_cast<TcTapRow*>(tsm + fwd_rows_offset(n));  // [n]
     if (tid == 0) {
-        for (int q = 0; q < 8; ++q) mbar_init(bars + 8u * q, (q == 5 || q == 6) ? 32u * kWorkers : 1u);
+        for (int q = 0; q < 7; ++q) mbar_init(bars + 8u * q, (q >= 3 && q <= 5) ? 32u * kWorkers : 1u);
         mbar_init_fence();
     }
-    const uint32_t tmem = tc_alloc(bars + kTmemSlot, a.tmem_cols);  // D1[0], D1[1], D2
-    const uint32_t d2 = tmem + 2u * (uint32_t)n;
+    const uint32_t tmem = tc_alloc(bars + kTmemSlot, a.tmem_cols);  // D1, D2
+    const uint32_t d1 = tmem, d2 = tmem + (uint32_t)n;
     const uint32_t idesc = idesc_bf16(kTcM, n);
+    const uint32_t tap = base;
     const int np = chunk < n ? (n - 1 - chunk) / a.chunks + 1 : 0;
     const float* xb = a.x + (size_t)b * n * n * nz;
     const size_t item = (size_t)b * a.n_sel + sidx;
     float* dst = a.partials ? a.partials + (item * a.chunks + chunk) * (size_t)n * nz : a.out + item * (size_t)n * nz;
     auto plane = [&](int p) { return chunk + p * a.chunks; };
-    auto tap = [&](int s) { return base + (uint32_t)s * kTile; };
-    auto xbuf = [&](int s) { return base + kFwdSlots * kTile + (uint32_t)s * 2u * part; };
-    auto d1 = [&](int s) { return tmem + (uint32_t)s * (uint32_t)n; };
-    auto tsrc = [&](int p) { return ttab + (size_t)plane(p) * kTcM * kTcM; };
+    auto xbuf = [&](int s) { return base + kPair + (uint32_t)s * 2u * part; };
+    auto tsrc = [&](int p) { return ttab + (size_t)plane(p) * 2 * kTcM * kTcM; };
     auto arow = [&](int p) -> const float* {
         return a.atten ? a.atten + ((size_t)angle * n + plane(p)) * n * nz : nullptr;
     };
@@ -481,35 +526,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
         for (int e = tid; e < n * nz; e += blockDim.x) dst[e] = 0.f;
     } else if (warp == 0) {
         if (lane == 0) {
-            TileLoads tl;
-            tl.load(0, tap(0), tsrc(0), bar_t);
-            if (np > 1) tl.load(1, tap(1), tsrc(1), bar_t);
+            PairLoads tl;
+            tl.load(tap, tsrc(0), bar_t);
             bool ok = true;
             for (int p = 0; p < np && ok; ++p) {
-                ok = mbar_wait(bar_s, (uint32_t)p & 1u) && tl.wait(p & 1, bar_t);
+                ok = mbar_wait(bar_s + 8u * (p & 1), (uint32_t)(p >> 1) & 1u) && tl.wait(bar_t);
                 if (!ok) break;
                 tc_fence_after();
-                issue_gemm1(tap(p & 1), xbuf(p & 1), part, d1(p & 1), idesc, n, bar_1 + 8u * (p & 1));
-                if (p > 0) {
-                    ok = mbar_wait(bar_a, (uint32_t)(p - 1) & 1u);
-                    if (!ok) break;
-                    tc_fence_after();
-                    issue_gemm2(xbuf((p - 1) & 1), part, tap((p - 1) & 1), d2, idesc, n, p > 1, bar_2);
-                    // GEMM 2(p-1) done: its Toeplitz slot takes plane p+1's tile
-                    ok = mbar_wait(bar_2, (uint32_t)(p - 1) & 1u);
-                    if (ok && p + 1 < np) tl.load((p + 1) & 1, tap((p + 1) & 1), tsrc(p + 1), bar_t);
-                }
-            }
-            if (ok) {
-                ok = mbar_wait(bar_a, (uint32_t)(np - 1) & 1u);
-                if (ok) {
-                    tc_fence_after();
-                    issue_gemm2(xbuf((np - 1) & 1), part, tap((np - 1) & 1), d2, idesc, n, np > 1, bar_2);
-                }
+                issue_gemm1(tap, xbuf(p & 1), part, d1, idesc, n, bar_1);
+                ok = mbar_wait(bar_a, (uint32_t)p & 1u);
+                if (!ok) break;
+                tc_fence_after();
+                issue_gemm2(xbuf(p & 1), part, tap, d2, idesc, n, p > 0, bar_2);
+                // GEMM 2(p) done: the Toeplitz slot takes plane p+1's pair
+                ok = mbar_wait(bar_2, (uint32_t)p & 1u);
+                if (ok && p + 1 < np) tl.load(tap, tsrc(p + 1), bar_t);
             }
             if (!ok) {
                 report_timeout(a.err);
-                tl.drain(bar_t, kFwdSlots);
+                tl.drain(bar_t);
             }
             tc_drain(bar_d);
         }
@@ -527,17 +562,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
                 ok = stage_rows(xbuf((p + 1) & 1), part, rows, xb, arow(p + 1), n, nz, plane(p + 1), cs, c, wi,
                                 p > 0 ? bar_2 : 0u, (uint32_t)(p - 1) & 1u);
                 fence_async_smem();
-                mbar_arrive(bar_s);
+                mbar_arrive(bar_s + 8u * ((p + 1) & 1));
             } else if (p > 0) {
                 ok = mbar_wait(bar_2, (uint32_t)(p - 1) & 1u);  // keep this warp's waits on bar_2 in order
             }
             if (!ok) break;
-            // GEMM 1(p) is done: D1[p&1] becomes the A operand of GEMM 2(p),
-            // over GEMM 1(p)'s B operand in X[p&1]
-            ok = mbar_wait(bar_1 + 8u * (p & 1), (uint32_t)(p >> 1) & 1u);
+            // GEMM 1(p) is done: D1 becomes the A operand of GEMM 2(p), over
+            // GEMM 1(p)'s B operand in X[p&1]
+            ok = mbar_wait(bar_1, (uint32_t)p & 1u);
             if (!ok) break;
             tc_fence_after();
-            d1_to_a2(xbuf(p & 1), part, d1(p & 1), n);
+            d1_to_a2(xbuf(p & 1), part, d1, n);
             fence_async_smem();
             tc_fence_before();
             mbar_arrive(bar_a);
@@ -565,17 +600,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
 // ---------------------------------------------------------------- back blur
 //
 // The projection of the angle is the B operand of every plane's GEMM 1.
-// Plane p: GEMM 1(p) into D1[p & 1]; the workers hand D1 over to A2; GEMM
-// 2(p) into D2[p & 1]; the workers finish the plane from D2: times A, stored
-// as B.  The issuer keeps GEMM 1 two planes ahead (D1 double buffered) and
-// issues GEMM 2(p) once A2 holds plane p and the workers have finished plane
-// p - 2 from the same D2 buffer.  Three Toeplitz slots: plane p + 3's tile
-// goes into plane p's slot once GEMM 2(p) is done.
+// Plane p: GEMM 1(p) into D1; the workers hand D1 over to A2; GEMM 2(p) into
+// D2[p & 1]; the workers finish the plane from D2 (times A, stored as B)
+// while the tensor cores run plane p + 1.  The issuer starts GEMM 2(p) once
+// A2 holds plane p and the workers have finished plane p - 2 from the same
+// D2 buffer.  T_hi has two slots and is copied a plane ahead; T_lo has one:
+// GEMM 2 runs its T_lo chain first, so that plane p + 1's T_lo is copied
+// while GEMM 2(p)'s T_hi chains and GEMM 1(p + 1)'s run.
 //
-// Barriers (bars + 8 q): q = 0..2 Toeplitz slots; 3, 4 GEMM 1 into D1[0],
-// D1[1]; 5, 6 GEMM 2 into D2[0], D2[1]; 7 projection staged (every worker
-// thread arrives); 8 A2 handed over (every worker thread); 9, 10 plane
-// finished from D2[0], D2[1] (every worker thread); 11 final drain.
+// Barriers (bars + 8 q): q = 0, 1 T_hi slots; 2 T_lo slot; 3 GEMM 1; 4, 5
+// GEMM 2 into D2[0], D2[1]; 6 GEMM 2's T_lo chain; 7 projection staged
+// (every worker thread arrives); 8 A2 handed over (every worker thread); 9,
+// 10 plane finished from D2[0], D2[1] (every worker thread); 11 final drain.
 
 __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackBf16Args a)
 {
@@ -586,59 +622,71 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
     const uint16_t* ttab = a.ttab + (size_t)angle * a.ttab_stride;  // this angle's tiles
     const uint32_t base = smem_u32(tsm), part = part_bytes(n);
     const uint32_t bars = base + back_bar_offset(n);
-    const uint32_t bar_t = bars, bar_1 = bars + 24, bar_2 = bars + 40, bar_s = bars + 56, bar_a = bars + 64,
-                   bar_f = bars + 72, bar_d = bars + 88;
+    const uint32_t bar_t = bars, bar_1 = bars + 24, bar_2 = bars + 32, bar_l = bars + 48, bar_s = bars + 56,
+                   bar_a = bars + 64, bar_f = bars + 72, bar_d = bars + 88;
     if (tid == 0) {
         for (int q = 0; q < 12; ++q) mbar_init(bars + 8u * q, (q >= 7 && q <= 10) ? 32u * kWorkers : 1u);
         mbar_init_fence();
     }
-    const uint32_t tmem = tc_alloc(bars + kTmemSlot, a.tmem_cols);  // D1[0], D1[1], D2[0], D2[1]
-    const uint32_t b1 = base + kBackSlots * kTile, a2 = b1 + 2u * part;
+    const uint32_t tmem = tc_alloc(bars + kTmemSlot, a.tmem_cols);  // D1, D2[0], D2[1]
+    const uint32_t d1 = tmem;
+    const uint32_t t_lo = base + 2u * kTile, b1 = base + 3u * kTile, a2 = b1 + 2u * part;
     const uint32_t idesc = idesc_bf16(kTcM, n);
     const int np = chunk < n ? (n - 1 - chunk) / a.chunks + 1 : 0;
     const size_t item = (size_t)b * a.n_sel + sidx;
     const float* pr = a.proj ? a.proj + (size_t)b * a.proj_bstride + (size_t)sidx * n * nz : nullptr;
     float* bvol = a.bvol + item * (size_t)n * n * nz;
     auto plane = [&](int p) { return chunk + p * a.chunks; };
-    auto tap = [&](int s) { return base + (uint32_t)s * kTile; };
-    auto d1 = [&](int s) { return tmem + (uint32_t)s * (uint32_t)n; };
-    auto d2 = [&](int s) { return tmem + (uint32_t)(2 + s) * (uint32_t)n; };
-    auto tsrc = [&](int p) { return ttab + (size_t)plane(p) * kTcM * kTcM; };
+    auto t_hi = [&](int s) { return base + (uint32_t)s * kTile; };
+    auto d2 = [&](int s) { return tmem + (uint32_t)(1 + s) * (uint32_t)n; };
+    auto src_hi = [&](int p) { return ttab + (size_t)plane(p) * 2 * kTcM * kTcM; };
+    auto src_lo = [&](int p) { return ttab + ((size_t)plane(p) * 2 + 1) * kTcM * kTcM; };
     auto arow = [&](int p) -> const float* {
         return a.atten ? a.atten + ((size_t)angle * n + plane(p)) * n * nz : nullptr;
     };
 
     if (np > 0 && warp == 0) {
         if (lane == 0) {
-            TileLoads tl;
-            for (int s = 0; s < kBackSlots && s < np; ++s) tl.load(s, tap(s), tsrc(s), bar_t);
+            TileLoads tl;  // slots 0, 1: T_hi; slot 2: T_lo
+            tl.load(0, t_hi(0), src_hi(0), bar_t);
+            tl.load(2, t_lo, src_lo(0), bar_t);
+            if (np > 1) tl.load(1, t_hi(1), src_hi(1), bar_t);
             bool ok = mbar_wait(bar_s, 0u);
-            for (int q = 0; q < 2 && q < np && ok; ++q) {
-                ok = tl.wait(q, bar_t);
-                if (ok) {
-                    tc_fence_after();
-                    issue_gemm1(tap(q), b1, part, d1(q), idesc, n, bar_1 + 8u * q);
-                }
-            }
             for (int p = 0; p < np && ok; ++p) {
-                ok = mbar_wait(bar_a, (uint32_t)p & 1u);  // A2 holds plane p
-                // D2[p&1] was last read by the finish of plane p-2
-                if (ok && p >= 2) ok = mbar_wait(bar_f + 8u * (p & 1), (uint32_t)((p - 2) >> 1) & 1u);
+                const int s = p & 1;
+                // GEMM 2(p-1) done: its T_hi slot takes plane p+1's
+                if (p > 0) {
+                    ok = mbar_wait(bar_2 + 8u * ((p - 1) & 1), (uint32_t)((p - 1) >> 1) & 1u);
+                    if (!ok) break;
+                    if (p + 1 < np) tl.load((p + 1) & 1, t_hi((p + 1) & 1), src_hi(p + 1), bar_t);
+                }
+                // GEMM 1(p): the T_hi chains, then the T_lo chain
+                ok = tl.wait(s, bar_t);
                 if (!ok) break;
                 tc_fence_after();
-                issue_gemm2(a2, part, tap(p % 3), d2(p & 1), idesc, n, false, bar_2 + 8u * (p & 1));
-                // GEMM 2(p) done: A2 is free and plane p's Toeplitz slot takes plane p+3's tile
-                ok = mbar_wait(bar_2 + 8u * (p & 1), (uint32_t)(p >> 1) & 1u);
+                gemm1_chain(t_hi(s), b1, d1, idesc, n, false);
+                gemm1_chain(t_hi(s), b1 + part, d1, idesc, n, true);
+                ok = tl.wait(2, bar_t);
                 if (!ok) break;
-                if (p + 3 < np) tl.load(p % 3, tap(p % 3), tsrc(p + 3), bar_t);
-                if (p + 2 < np) {
-                    ok = tl.wait((p + 2) % 3, bar_t);
-                    if (ok) issue_gemm1(tap((p + 2) % 3), b1, part, d1(p & 1), idesc, n, bar_1 + 8u * (p & 1));
-                }
+                gemm1_chain(t_lo, b1, d1, idesc, n, true);
+                tc_commit(bar_1);
+                ok = mbar_wait(bar_a, (uint32_t)p & 1u);  // A2 holds plane p
+                // D2[p&1] was last read by the finish of plane p-2
+                if (ok && p >= 2) ok = mbar_wait(bar_f + 8u * s, (uint32_t)((p - 2) >> 1) & 1u);
+                if (!ok) break;
+                tc_fence_after();
+                gemm2_chain(a2, t_lo, d2(s), idesc, n, false);
+                tc_commit(bar_l);
+                gemm2_chain(a2, t_hi(s), d2(s), idesc, n, true);
+                gemm2_chain(a2 + part, t_hi(s), d2(s), idesc, n, true);
+                tc_commit(bar_2 + 8u * s);
+                // the T_lo chain done: the slot takes plane p+1's T_lo
+                ok = mbar_wait(bar_l, (uint32_t)p & 1u);
+                if (ok && p + 1 < np) tl.load(2, t_lo, src_lo(p + 1), bar_t);
             }
             if (!ok) {
                 report_timeout(a.err);
-                tl.drain(bar_t, kBackSlots);
+                tl.drain(bar_t, 3);
             }
             tc_drain(bar_d);
         }
@@ -685,11 +733,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
             if (p > 0) load_a(p - 1, aw);
             if (a.atten && p + 1 < np) prefetch_rows(arow(p + 1), n, nz, wi);
             // GEMM 1(p) done; GEMM 2(p-1) done: A2 is free and D2[(p-1)&1] ready
-            ok = mbar_wait(bar_1 + 8u * (p & 1), (uint32_t)(p >> 1) & 1u);
+            ok = mbar_wait(bar_1, (uint32_t)p & 1u);
             if (ok && p > 0) ok = mbar_wait(bar_2 + 8u * ((p - 1) & 1), (uint32_t)((p - 1) >> 1) & 1u);
             if (!ok) break;
             tc_fence_after();
-            d1_to_a2(a2, part, d1(p & 1), n);
+            d1_to_a2(a2, part, d1, n);
             fence_async_smem();
             tc_fence_before();
             mbar_arrive(bar_a);

@@ -172,7 +172,7 @@ size_t request_bytes(const spect_geom& g, int num_sms)
     b += max_subset * plane * 4 + vol * 4;                               // ratio, back projection
     if (g.flags & SPECT_FLAG_ATTEN) b += na * vol * 4;                   // attenuation cache
     const size_t tables = g.det_offsets ? na : 1;                        // PSF tables (orbit)
-    if (g.flags & SPECT_FLAG_PSF_BF16) b += tables * n * 128 * 128 * 2;  // Toeplitz tiles
+    if (g.flags & SPECT_FLAG_PSF_BF16) b += tables * n * 2 * 128 * 128 * 2;  // Toeplitz tiles (hi, lo)
     b += tables * (n * 41 * 4 + spect::psf_int_stride((int)n) * 4);             // taps, radii, work, chunk bounds
     if (g.fov_mask) b += na * plane * 4;                                 // T_fov weights
     b += 3 * vol * 4 + na * plane * 4;                                   // mu, x, y

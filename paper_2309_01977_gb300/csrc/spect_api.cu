@@ -199,17 +199,15 @@ float bf16_value(uint16_t h)
 }
 
 // Per-plane banded Toeplitz tiles T_i[r][c] = w_i(r - c) (|r - c| <= R_i) of
-// the tensor-core PSF path in BF16, in the K-major 128-byte-swizzled layout
-// of a 128 x 128 tile: K blocks of 64 columns (16 KB apart), rows of 128 B,
-// 8-row atoms of 1 KB in which the 16-byte chunk c of row r sits at chunk
-// c ^ (r % 8).  The taps are rounded to BF16 and renormalised: the centre
-// tap takes up what the rounded taps miss of 1, so that the plane's blur
-// keeps its unit gain.
+// the tensor-core PSF path, as BF16 hi and lo parts (w = hi + lo to ~2^-17),
+// in the K-major 128-byte-swizzled layout of a 128 x 128 tile: K blocks of
+// 64 columns (16 KB apart), rows of 128 B, 8-row atoms of 1 KB in which the
+// 16-byte chunk c of row r sits at chunk c ^ (r % 8).
 void build_toeplitz_bf16(const spect_geom& g, int n, double offset, std::vector<uint16_t>& all)
 {
     const int T = 128;
     const size_t base = all.size();
-    all.resize(base + (size_t)n * T * T, 0);
+    all.resize(base + (size_t)n * 2 * T * T, 0);
     uint16_t* out = all.data() + base;
     for (int i = 0; i < n; ++i) {
         const double d = (double)n - i - 0.5 + offset;
@@ -219,17 +217,19 @@ void build_toeplitz_bf16(const spect_geom& g, int n, double offset, std::vector<
         double sum = 0.0;
         for (int t = -r; t <= r; ++t) sum += (w[t + r] = std::exp(-(double)t * t / (2.0 * s * s)));
         for (double& v : w) v /= sum;
-        std::vector<uint16_t> wb(2 * r + 1);
-        double sb = 0.0;
-        for (int t = 0; t <= 2 * r; ++t) sb += (double)bf16_value(wb[t] = bf16_bits((float)w[t]));
-        wb[r] = bf16_bits((float)((double)bf16_value(wb[r]) + (1.0 - sb)));
-        uint16_t* tile = out + (size_t)i * T * T;
+        uint16_t* hi = out + (size_t)i * 2 * T * T;
+        uint16_t* lo = hi + (size_t)T * T;
         for (int row = 0; row < T; ++row)
             for (int col = std::max(0, row - r); col <= std::min(T - 1, row + r); ++col) {
+                const double wv = w[row - col + r];
+                const uint16_t h = bf16_bits((float)wv);
+                const uint16_t l = bf16_bits((float)(wv - (double)bf16_value(h)));
                 const int kb = col >> 6, kk = col & 63;
                 const size_t byte = (size_t)kb * T * 128 + ((size_t)(row >> 3) << 10) + ((row & 7) << 7) +
                                     ((((kk >> 3) ^ (row & 7))) << 4) + ((kk & 7) << 1);
-                tile[byte >> 1] = wb[row - col + r];
+                const size_t e = byte >> 1;
+                hi[e] = h;
+                lo[e] = l;
             }
     }
 }
@@ -304,14 +304,14 @@ int run_forward(spect_plan* p, spect_plan_scratch& sc, const float* x, float* ou
             a.atten = p->d_atten;
             a.cs = p->d_cs;
             a.ttab = p->d_ttab;
-            a.ttab_stride = p->psf_tables > 1 ? (size_t)p->n * kTcTile : 0;
+            a.ttab_stride = p->psf_tables > 1 ? (size_t)p->n * 2 * kTcTile : 0;
             a.sel = sel_dev;
             a.n = p->n;
             a.nz = p->nz;
             a.n_sel = n_sel;
             a.batch = nb;
             a.chunks = chunks;
-            a.tmem_cols = bf16_tmem_cols(p->n, 3);  // D1 twice, D2
+            a.tmem_cols = bf16_tmem_cols(p->n, 2);  // D1, D2
             a.out = out + (size_t)b0 * n_sel * plane;
             a.partials = use_partials ? sc.partials : nullptr;
             a.err = p->d_err;
@@ -390,14 +390,14 @@ int run_back(spect_plan* p, spect_plan_scratch& sc, const float* proj, float* x_
                 bb.fov = p->d_fov;
                 bb.atten = p->d_atten;
                 bb.ttab = p->d_ttab;
-                bb.ttab_stride = p->psf_tables > 1 ? (size_t)p->n * kTcTile : 0;
+                bb.ttab_stride = p->psf_tables > 1 ? (size_t)p->n * 2 * kTcTile : 0;
                 bb.sel = sel_dev + g0;
                 bb.n = p->n;
                 bb.nz = p->nz;
                 bb.n_sel = ng;
                 bb.batch = nb;
                 bb.chunks = chunk_target(p, (long)nb * ng);
-                bb.tmem_cols = bf16_tmem_cols(p->n, 4);  // D1 twice, D2 twice
+                bb.tmem_cols = bf16_tmem_cols(p->n, 3);  // D1, D2 twice
                 bb.bvol = sc.bvol;
                 bb.err = p->d_err;
                 e = timed(p, "blur_back_bf16", st, 1, [&] { return launch_blur_back_bf16(bb, st); });

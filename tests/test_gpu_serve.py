@@ -6,8 +6,8 @@
   - admission respects the HBM budget (peak bytes <= budget) and a request
     larger than the whole budget is refused; queued requests can be
     cancelled; a bounded wait reports SPECT_ETIMEDOUT;
-  - BF16-PSF requests mix with FP32 ones and stay within 1e-3 of FP32 (the
-    BF16 path's bar against FP64).
+  - BF16-PSF requests mix with FP32 ones and stay within 1e-4 of FP32 (the
+    three-product BF16 form measures about 5e-6).
 """
 import numpy as np
 import pytest
@@ -131,4 +131,4 @@ def test_serve_bf16_requests(spect_lib, cuda):
     xs = [sv.wait(i)[0] for i in ids]
     sv.close()
     assert np.array_equal(xs[1], x16_alone)
-    assert rel_l2(xs[1], xs[2]) <= 1e-3
+    assert rel_l2(xs[1], xs[2]) <= 1e-4
