@@ -31,6 +31,7 @@ def _t(a, dev):
     (64, 40, 12, 3, -1, 7),   # axial size below 128 and not a multiple of 16
     (64, 64, 16, 4, -1, 8),   # non-circular orbit (per-angle Toeplitz tiles)
     (64, 48, 16, 4, -1, 9),   # non-central projections (T_trans) and a field-of-view mask (T_fov)
+    (32, 32, 16, 2, 1, 12),   # the smallest plane (n = 32): one 64-column swizzle block
 ])
 def test_bf16_projection_parity(spect_lib, oracle_mod, cuda, n, nz, na, M, subset, seed):
     offs = [3.0 + 2.0 * math.cos(2 * 2 * math.pi * a / na) for a in range(na)] if seed == 8 else None
@@ -56,6 +57,34 @@ def test_bf16_projection_parity(spect_lib, oracle_mod, cuda, n, nz, na, M, subse
     plan.check()
     print("bf16 %dx%d: forward %.2e back %.2e" % (n, nz, e_fwd, e_back))
     assert e_fwd <= TOL_BF16 and e_back <= TOL_BF16
+    # element-wise: a wrong plane, chunk or tile shows up locally
+    bref = oracle_mod.back(q, og, sel)
+    assert np.max(np.abs(p - ref)) <= 10 * TOL_BF16 * np.max(np.abs(ref))
+    assert np.max(np.abs(b - bref)) <= 10 * TOL_BF16 * np.max(np.abs(bref))
+
+
+def test_bf16_single_angle_batch(spect_lib, oracle_mod, cuda):
+    """One angle per subset (more depth chunks than planes, so some CTAs have
+    no plane) and a batch of two volumes / two projection sets."""
+    n, nz, na, M = 64, 64, 8, 8
+    g = spect_lib.Geometry(n=n, nz=nz, n_angles=na, n_subsets=M, psf_bf16=True, atten_f64=True)
+    f0, mu = phantom_inputs(n, nz, 13)
+    f1, _ = phantom_inputs(n, nz, 14)
+    plan = spect_lib.Plan(g, _t(mu, cuda))
+    og = oracle_geom(oracle_mod, g, mu)
+    for subset in (0, 5):
+        sel = plan.subset_angles(subset)
+        assert len(sel) == 1
+        p = plan.forward(_t(np.stack([f0, f1]), cuda), subset).cpu().numpy().reshape(2, 1, n, nz)
+        q = f32(np.random.Generator(np.random.PCG64(subset)).uniform(0.5, 1.5, size=(2, 1, n, nz)))
+        b = plan.back(_t(q, cuda), subset).cpu().numpy().reshape(2, n, n, nz)
+        for k, f in enumerate((f0, f1)):
+            ref = oracle_mod.forward(f, og, sel)
+            bref = oracle_mod.back(q[k], og, sel)
+            print("bf16 one angle, entry %d: forward %.2e back %.2e" % (k, rel_l2(p[k], ref), rel_l2(b[k], bref)))
+            assert rel_l2(p[k], ref) <= TOL_BF16 and rel_l2(b[k], bref) <= TOL_BF16
+            assert np.max(np.abs(p[k] - ref)) <= 10 * TOL_BF16 * np.max(np.abs(ref))
+    plan.check()
 
 
 def test_bf16_adjoint_and_sensitivity(spect_lib, oracle_mod, cuda):
