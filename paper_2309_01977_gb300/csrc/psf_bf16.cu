@@ -143,12 +143,16 @@ __device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uin
 // The descriptors of a chain are formed once and stepped by constant
 // increments, so that issuing a product costs the issuing thread a few
 // instructions.
-__device__ __forceinline__ void gemm1_chain(uint32_t t, uint32_t b, uint32_t d1, uint32_t idesc, int n, bool acc)
+// GEMM 1 runs K steps 0 .. kz-1 only, kz = ceil(nz / 16): its B operand
+// is zero beyond the axial size, so the steps past it would add zeros.
+__device__ __forceinline__ void gemm1_chain(uint32_t t, uint32_t b, uint32_t d1, uint32_t idesc, int n, int kz,
+                                            bool acc)
 {
     const uint64_t da = sw_desc(t), db = sw_desc(b);
 #pragma unroll
     for (int ks = 0; ks < kTcM / 16; ++ks)
-        tc_mma(d1, da + sw_kstep_desc(ks, kTcM), db + sw_kstep_desc(ks, n), idesc, (acc || ks) ? 1u : 0u);
+        if (ks < kz)
+            tc_mma(d1, da + sw_kstep_desc(ks, kTcM), db + sw_kstep_desc(ks, n), idesc, (acc || ks) ? 1u : 0u);
 }
 
 __device__ __forceinline__ void gemm2_chain(uint32_t a, uint32_t t, uint32_t d2, uint32_t idesc, int n, bool acc)
@@ -164,11 +168,11 @@ __device__ __forceinline__ void gemm2_chain(uint32_t a, uint32_t t, uint32_t d2,
 // axial direction); T_lo sits kTile bytes after T_hi, and B (n x 128) has its
 // lo part `lo` bytes after the hi part.  Completion arrives on `bar`.
 __device__ __forceinline__ void issue_gemm1(uint32_t tap, uint32_t b1, uint32_t lo, uint32_t d1, uint32_t idesc, int n,
-                                            uint32_t bar)
+                                            int kz, uint32_t bar)
 {
-    gemm1_chain(tap, b1, d1, idesc, n, false);
-    gemm1_chain(tap + (uint32_t)kTile, b1, d1, idesc, n, true);
-    gemm1_chain(tap, b1 + lo, d1, idesc, n, true);
+    gemm1_chain(tap, b1, d1, idesc, n, kz, false);
+    gemm1_chain(tap + (uint32_t)kTile, b1, d1, idesc, n, kz, true);
+    gemm1_chain(tap, b1 + lo, d1, idesc, n, kz, true);
     tc_commit(bar);
 }
 
@@ -509,6 +513,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
     const uint32_t tmem = tc_alloc(bars + kTmemSlot, a.tmem_cols);  // D1, D2
     const uint32_t d1 = tmem, d2 = tmem + (uint32_t)n;
     const uint32_t idesc = idesc_bf16(kTcM, n);
+    const int kz = (nz + 15) / 16;  // GEMM 1's K steps
     const uint32_t tap = base;
     const int np = chunk < n ? (n - 1 - chunk) / a.chunks + 1 : 0;
     const float* xb = a.x + (size_t)b * n * n * nz;
@@ -533,7 +538,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
                 ok = mbar_wait(bar_s + 8u * (p & 1), (uint32_t)(p >> 1) & 1u) && tl.wait(bar_t);
                 if (!ok) break;
                 tc_fence_after();
-                issue_gemm1(tap, xbuf(p & 1), part, d1, idesc, n, bar_1);
+                issue_gemm1(tap, xbuf(p & 1), part, d1, idesc, n, kz, bar_1);
                 ok = mbar_wait(bar_a, (uint32_t)p & 1u);
                 if (!ok) break;
                 tc_fence_after();
@@ -632,6 +637,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
     const uint32_t d1 = tmem;
     const uint32_t t_lo = base + 2u * kTile, b1 = base + 3u * kTile, a2 = b1 + 2u * part;
     const uint32_t idesc = idesc_bf16(kTcM, n);
+    const int kz = (nz + 15) / 16;  // GEMM 1's K steps
     const int np = chunk < n ? (n - 1 - chunk) / a.chunks + 1 : 0;
     const size_t item = (size_t)b * a.n_sel + sidx;
     const float* pr = a.proj ? a.proj + (size_t)b * a.proj_bstride + (size_t)sidx * n * nz : nullptr;
@@ -664,11 +670,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
                 ok = tl.wait(s, bar_t);
                 if (!ok) break;
                 tc_fence_after();
-                gemm1_chain(t_hi(s), b1, d1, idesc, n, false);
-                gemm1_chain(t_hi(s), b1 + part, d1, idesc, n, true);
+                gemm1_chain(t_hi(s), b1, d1, idesc, n, kz, false);
+                gemm1_chain(t_hi(s), b1 + part, d1, idesc, n, kz, true);
                 ok = tl.wait(2, bar_t);
                 if (!ok) break;
-                gemm1_chain(t_lo, b1, d1, idesc, n, true);
+                gemm1_chain(t_lo, b1, d1, idesc, n, kz, true);
                 tc_commit(bar_1);
                 ok = mbar_wait(bar_a, (uint32_t)p & 1u);  // A2 holds plane p
                 // D2[p&1] was last read by the finish of plane p-2
