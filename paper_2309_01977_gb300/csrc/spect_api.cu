@@ -14,6 +14,8 @@
 #include <vector>
 
 #include "async_copy.cuh"
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 using namespace spect;
@@ -742,6 +744,17 @@ int refresh_mu(spect_plan* p, spect_plan_scratch& sc, const float* mu_dev, cudaS
 
 }  // namespace
 
+// An NVTX range over one library call (host side: argument checks and the
+// queueing of its kernels), named after the call, so that a profiler's
+// timeline shows which call issued which kernels.  NVTX is header-only and
+// costs a branch when no tool is attached.
+struct CallRange {
+    explicit CallRange(const char* name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+    CallRange(const CallRange&) = delete;
+    CallRange& operator=(const CallRange&) = delete;
+};
+
 extern "C" {
 
 const char* spect_version(void) { return "libspect 0.1 (sm_103a)"; }
@@ -766,6 +779,7 @@ const char* spect_status_str(int status)
 
 int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream, spect_plan** out)
 {
+    CallRange range("spect_plan_create");
     if (!out) return fail(SPECT_EINVAL, "out is NULL");
     *out = nullptr;
     if (!geom) return fail(SPECT_EINVAL, "geom is NULL");
@@ -1064,6 +1078,7 @@ int spect_subset_angles(const spect_plan* plan, int subset, int* out)
 
 int spect_forward(spect_plan* plan, const float* x, float* proj, int subset, int batch, void* stream)
 {
+    CallRange range("spect_forward");
     if (int rc = check_plan(plan)) return rc;
     if (!x || !proj) return fail(SPECT_EINVAL, "x and proj must be device pointers");
     if (!aligned16(x) || !aligned16(proj)) return fail(SPECT_EINVAL, "x and proj must be 16-byte aligned");
@@ -1082,6 +1097,7 @@ int spect_forward(spect_plan* plan, const float* x, float* proj, int subset, int
 
 int spect_back(spect_plan* plan, const float* proj, float* x_out, int subset, int batch, void* stream)
 {
+    CallRange range("spect_back");
     if (int rc = check_plan(plan)) return rc;
     if (!proj || !x_out) return fail(SPECT_EINVAL, "proj and x_out must be device pointers");
     if (!aligned16(proj) || !aligned16(x_out)) return fail(SPECT_EINVAL, "proj and x_out must be 16-byte aligned");
@@ -1100,6 +1116,7 @@ int spect_back(spect_plan* plan, const float* proj, float* x_out, int subset, in
 
 int spect_sensitivity(spect_plan* plan, int subset, float* out, void* stream)
 {
+    CallRange range("spect_sensitivity");
     if (int rc = check_plan(plan)) return rc;
     if (!out || !aligned16(out)) return fail(SPECT_EINVAL, "out must be a 16-byte aligned device pointer");
     const int* sel;
@@ -1124,6 +1141,7 @@ int spect_sensitivity(spect_plan* plan, int subset, float* out, void* stream)
 int spect_osem_run(spect_plan* plan, const float* y, float s, float* x_inout, int first_subiter, int n_subiters,
                    double* diag_dev, void* stream)
 {
+    CallRange range("spect_osem_run");
     if (!std::isfinite(s) || s < 0.f) return fail(SPECT_EINVAL, "s must be finite and >= 0");
     return osem_core(plan, y, s, nullptr, x_inout, first_subiter, n_subiters, diag_dev, stream);
 }
@@ -1131,12 +1149,14 @@ int spect_osem_run(spect_plan* plan, const float* y, float s, float* x_inout, in
 int spect_osem_run_dev(spect_plan* plan, const float* y, const float* s_dev, float* x_inout, int first_subiter,
                        int n_subiters, double* diag_dev, void* stream)
 {
+    CallRange range("spect_osem_run_dev");
     if (!s_dev) return fail(SPECT_EINVAL, "s_dev must be a device pointer");
     return osem_core(plan, y, 0.f, s_dev, x_inout, first_subiter, n_subiters, diag_dev, stream);
 }
 
 int spect_plan_set_mu(spect_plan* plan, const float* mu_dev, void* stream)
 {
+    CallRange range("spect_plan_set_mu");
     if (int rc = check_plan(plan)) return rc;
     if (plan->d_atten && (!mu_dev || !aligned16(mu_dev)))
         return fail(SPECT_EINVAL, "the plan models attenuation: mu must be a 16-byte aligned device pointer");
@@ -1153,12 +1173,14 @@ int spect_plan_set_mu(spect_plan* plan, const float* mu_dev, void* stream)
 int spect_map_run(spect_plan* plan, const float* y, float s, float* x_inout, int first_subiter, int n_subiters,
                   const spect_map_params* params, void* stream)
 {
+    CallRange range("spect_map_run");
     return map_core(plan, y, s, x_inout, first_subiter, n_subiters, params, stream);
 }
 
 int spect_multi_osem_run(spect_plan* const* plans, const float* scales, int n_peaks, const float* const* y,
                          const float* s, float* x_inout, int first_subiter, int n_subiters, void* stream)
 {
+    CallRange range("spect_multi_osem_run");
     return multi_core(plans, scales, n_peaks, y, s, x_inout, first_subiter, n_subiters, stream);
 }
 
@@ -1178,6 +1200,7 @@ int spect_prior_grad(const float* x, int n, int nz, int prior, float delta, floa
 int spect_poisson_ll(spect_plan* plan, const float* y, const float* p, float s, size_t count, double* ll_dev,
                      float* grad_proj, void* stream)
 {
+    CallRange range("spect_poisson_ll");
     if (int rc = check_plan(plan)) return rc;
     if (!y || !p || !ll_dev) return fail(SPECT_EINVAL, "y, p and ll must be device pointers");
     if (!aligned16(y) || !aligned16(p) || (grad_proj && !aligned16(grad_proj)))
