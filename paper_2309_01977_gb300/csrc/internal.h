@@ -188,7 +188,7 @@ struct BlurBackBf16Args {
 cudaError_t launch_forward_bf16(const ForwardBf16Args& a, cudaStream_t st);
 cudaError_t launch_blur_back_bf16(const BlurBackBf16Args& a, cudaStream_t st);
 size_t bf16_smem_bytes(int n);
-uint32_t bf16_tmem_cols(int n, int tiles);  // TMEM columns for `tiles` n-column accumulators
+uint32_t bf16_tmem_cols(int n, int tiles);  // TMEM columns: `tiles` n-column accumulators and GEMM 2's A operand
 int bf16_occupancy(int n);
 
 PlaneTiling plane_tiling(int n, int nz, int rmax, size_t cap, size_t limit);

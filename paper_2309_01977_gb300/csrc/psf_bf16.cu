@@ -99,6 +99,21 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, 
         : "memory");
 }
 
+// The same product with its A operand in tensor memory: A's rows are TMEM
+// lanes and its K elements run along the columns, two BF16 per 32-bit
+// column (the lower K index in the lower half).  Only B is read from shared
+// memory, half the shared-memory traffic of a product with both operands
+// there.
+__device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 __device__ __forceinline__ void tc_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -118,16 +133,22 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16])
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// Eight 32-bit values into eight consecutive TMEM columns of this thread's
+// lane, and the wait for this thread's stores.
+__device__ __forceinline__ void tc_st8(uint32_t taddr, const uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 {
     uint32_t r;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
     return r;
-}
-
-__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
-{
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
 // Two values as BF16 hi parts and BF16 residuals: v = hi + lo to ~2^-17.
@@ -138,13 +159,12 @@ __device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uin
     lo = pack_bf16x2(a - ha, b - hb);
 }
 
-// One MMA chain of GEMM 1, D1 (+)= T B^T over K = 128, and of GEMM 2, D2
-// (+)= A T^T over K = n (tile addresses of one BF16 part each).
-// The descriptors of a chain are formed once and stepped by constant
-// increments, so that issuing a product costs the issuing thread a few
-// instructions.
-// GEMM 1 runs K steps 0 .. kz-1 only, kz = ceil(nz / 16): its B operand
-// is zero beyond the axial size, so the steps past it would add zeros.
+// One MMA chain of GEMM 1, D1 (+)= T B^T over K = 128 (tile addresses of
+// one BF16 part each).  The descriptors of a chain are formed once and
+// stepped by constant increments, so that issuing a product costs the
+// issuing thread a few instructions.  GEMM 1 runs K steps 0 .. kz-1 only,
+// kz = ceil(nz / 16): its B operand is zero beyond the axial size, so the
+// steps past it would add zeros.
 __device__ __forceinline__ void gemm1_chain(uint32_t t, uint32_t b, uint32_t d1, uint32_t idesc, int n, int kz,
                                             bool acc)
 {
@@ -155,14 +175,6 @@ __device__ __forceinline__ void gemm1_chain(uint32_t t, uint32_t b, uint32_t d1,
             tc_mma(d1, da + sw_kstep_desc(ks, kTcM), db + sw_kstep_desc(ks, n), idesc, (acc || ks) ? 1u : 0u);
 }
 
-__device__ __forceinline__ void gemm2_chain(uint32_t a, uint32_t t, uint32_t d2, uint32_t idesc, int n, bool acc)
-{
-    const uint64_t da = sw_desc(a), db = sw_desc(t);
-#pragma unroll
-    for (int ks = 0; ks < kTcM / 16; ++ks)
-        if (ks < n / 16)
-            tc_mma(d2, da + sw_kstep_desc(ks, kTcM), db + sw_kstep_desc(ks, kTcM), idesc, (acc || ks) ? 1u : 0u);
-}
 
 // GEMM 1: D1 = T_hi B_hi^T + T_lo B_hi^T + T_hi B_lo^T over K = 128 (the
 // axial direction); T_lo sits kTile bytes after T_hi, and B (n x 128) has its
@@ -176,16 +188,16 @@ __device__ __forceinline__ void issue_gemm1(uint32_t tap, uint32_t b1, uint32_t 
     tc_commit(bar);
 }
 
-// GEMM 2: D2 (+)= A_hi T_hi^T + A_hi T_lo^T + A_lo T_hi^T over K = n (the
-// transaxial direction); A is 128 x n.  Completion arrives on `bar`.
-__device__ __forceinline__ void issue_gemm2(uint32_t a2, uint32_t lo, uint32_t tap, uint32_t d2, uint32_t idesc, int n,
-                                            bool accumulate, uint32_t bar)
+// One chain of GEMM 2 with A in tensor memory: K step ks starts 8 columns
+// (16 BF16) further along A.
+__device__ __forceinline__ void gemm2_chain_ts(uint32_t a_tmem, uint32_t t, uint32_t d2, uint32_t idesc, int n, bool acc)
 {
-    gemm2_chain(a2, tap, d2, idesc, n, accumulate);
-    gemm2_chain(a2, tap + (uint32_t)kTile, d2, idesc, n, true);
-    gemm2_chain(a2 + lo, tap, d2, idesc, n, true);
-    tc_commit(bar);
+    const uint64_t db = sw_desc(t);
+#pragma unroll
+    for (int ks = 0; ks < kTcM / 16; ++ks)
+        if (ks < n / 16) tc_mma_ts(d2, a_tmem + 8u * ks, db + sw_kstep_desc(ks, kTcM), idesc, (acc || ks) ? 1u : 0u);
 }
+
 
 // The worker warps w = 1..kWorkers split each TMEM accumulator: warp w may
 // only access TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31 (its lane quadrant),
@@ -194,41 +206,44 @@ __device__ __forceinline__ void issue_gemm2(uint32_t a2, uint32_t lo, uint32_t t
 __device__ __forceinline__ int tm_quad(int warp) { return warp & 3; }
 __device__ __forceinline__ int tm_col0(int warp) { return 16 * ((warp - 1) >> 2); }
 
-// D1 (TMEM, lanes k, columns j) -> BF16 hi/lo -> A operand of GEMM 2
-// (K-major [k][j], K = n; lo part `lo` bytes after the hi part); this
-// worker's lanes and chunks.
-__device__ __forceinline__ void d1_to_a2(uint32_t a2, uint32_t lo, uint32_t d1, int n)
+
+// D1 (TMEM, lanes k, columns j) -> BF16 hi/lo -> GEMM 2's A operand in TMEM
+// (lanes k; the hi part from column a2hi, the lo part from a2lo, j / 2
+// columns in); this worker's lanes and chunks.  Returns after this thread's
+// stores are done.
+__device__ __forceinline__ void d1_to_a2_tmem(uint32_t a2hi, uint32_t a2lo, uint32_t d1, int n)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = 32 * tm_quad(warp) + lane;
+    const int warp = threadIdx.x >> 5;
+    const uint32_t quad = (uint32_t)(32 * tm_quad(warp)) << 16;
     for (int c = tm_col0(warp); c < n; c += 64) {
         float v[16];
-        tc_ld16(d1 + ((uint32_t)(32 * tm_quad(warp)) << 16) + (uint32_t)c, v);
+        tc_ld16(d1 + quad + (uint32_t)c, v);
         uint32_t h[8], l[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) split_bf16x2(v[2 * q], v[2 * q + 1], h[q], l[q]);
-        const uint32_t o0 = a2 + sw_off(k, c, kTcM), o1 = a2 + sw_off(k, c + 8, kTcM);
-        st_shared_v4(o0, h[0], h[1], h[2], h[3]);
-        st_shared_v4(o1, h[4], h[5], h[6], h[7]);
-        st_shared_v4(o0 + lo, l[0], l[1], l[2], l[3]);
-        st_shared_v4(o1 + lo, l[4], l[5], l[6], l[7]);
+        tc_st8(a2hi + quad + (uint32_t)(c >> 1), h);
+        tc_st8(a2lo + quad + (uint32_t)(c >> 1), l);
     }
+    tc_wait_st();
 }
 
-// Bytes of one BF16 part (hi or lo) of a plane operand: the larger of the
-// GEMM 1 B operand (n rows x 128) and the GEMM 2 A operand (128 rows x n,
-// rounded up to whole 64-column swizzle blocks).
-__host__ __device__ constexpr uint32_t part_bytes(int n) { return (uint32_t)kTcM * ((n + 63) / 64 * 64) * 2u; }
+// TMEM columns: `tiles` accumulators of n columns, then GEMM 2's A operand
+// (hi and lo parts, up to 64 columns each) from a 64-column boundary.
+__host__ __device__ constexpr uint32_t a2_tmem_col(int n, int tiles) { return (uint32_t)((tiles * n + 63) / 64 * 64); }
+
+// Bytes of one BF16 part (hi or lo) of GEMM 1's B operand (n rows x 128 K
+// elements; 1 KB aligned as n % 8 == 0).
+__host__ __device__ constexpr uint32_t part_bytes(int n) { return (uint32_t)n * kTcM * 2u; }
 
 // Shared-memory layouts (every tile 1 KB aligned), then a 128-byte block of
 // mbarriers with the TMEM address slot at byte 112:
 //   forward:  Toeplitz pair (hi, lo) | plane buffers [2] (hi, lo) | tap-row table [n]
-//   back:     T_hi slots [2] | T_lo slot | B1 = projection (hi, lo) | A2 (hi, lo)
+//   back:     T_hi slots [2] | T_lo slot | B1 = projection (hi, lo)
 constexpr uint32_t kPair = 2u * kTile;  // T_hi and T_lo of one plane
 constexpr uint32_t kBarBytes = 128, kTmemSlot = 112;
 __host__ __device__ constexpr uint32_t fwd_rows_offset(int n) { return kPair + 4u * part_bytes(n); }
 __host__ __device__ constexpr uint32_t fwd_bar_offset(int n) { return fwd_rows_offset(n) + 32u * (uint32_t)n; }
-__host__ __device__ constexpr uint32_t back_bar_offset(int n) { return 3u * kTile + 4u * part_bytes(n); }
+__host__ __device__ constexpr uint32_t back_bar_offset(int n) { return 3u * kTile + 2u * part_bytes(n); }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
@@ -395,13 +410,10 @@ __device__ __forceinline__ void prefetch_rows(const float* plane, int n, int nz,
 // k < nz, 0 for nz <= k < 128, as BF16 hi and lo parts.  Lanes compute the
 // rows' taps into the shared table first; then lane l covers k = 4l..4l+3
 // with 128-bit loads (one 512-byte row per load instruction), four rows at a
-// time so that twenty loads per lane are in flight together.  When wait_bar
-// is not 0 the buffer is still an operand of products in flight: the first
-// stores wait for phase parity wait_par of that barrier, behind the first
-// loads.  Returns false when that wait ran out.
-__device__ __forceinline__ bool stage_rows(uint32_t b1, uint32_t b1_lo, TcTapRow* rows, const float* __restrict__ xb,
+// time so that twenty loads per lane are in flight together.
+__device__ __forceinline__ void stage_rows(uint32_t b1, uint32_t b1_lo, TcTapRow* rows, const float* __restrict__ xb,
                                            const float* __restrict__ arow, int n, int nz, int i, float4 cs, float c,
-                                           int wi, uint32_t wait_bar, uint32_t wait_par)
+                                           int wi)
 {
     constexpr int kRows = 4;
     const int lane = threadIdx.x & 31;
@@ -411,7 +423,6 @@ __device__ __forceinline__ bool stage_rows(uint32_t b1, uint32_t b1_lo, TcTapRow
     __syncwarp();
     const int k = 4 * lane;
     const bool in = k < nz;
-    bool ok = true;
     for (int r0 = 0; r0 < nr; r0 += kRows) {
         float4 v[kRows];
         int jr[kRows];
@@ -442,16 +453,10 @@ __device__ __forceinline__ bool stage_rows(uint32_t b1, uint32_t b1_lo, TcTapRow
                 v[r].w *= av[r].w;
             }
         }
-        if (wait_bar) {
-            ok = mbar_wait(wait_bar, wait_par);
-            wait_bar = 0;
-        }
 #pragma unroll
         for (int r = 0; r < kRows; ++r)
             if (jr[r] < n) put4(b1, b1_lo, jr[r], k, n, v[r]);
     }
-    if (wait_bar) ok = mbar_wait(wait_bar, wait_par);
-    return ok;
 }
 
 // B1[j][k] = proj[j][k] (all ones when proj is NULL) times the T_fov weight
@@ -480,13 +485,14 @@ __device__ __forceinline__ void stage_proj_rows(uint32_t b1, uint32_t b1_lo, con
 //
 // Planes p = 0, 1, .. of this CTA's depth chunk (plane index chunk + p *
 // chunks) flow through two plane buffers X[p & 1]: the staged plane is the B
-// operand of GEMM 1(p) into D1; once GEMM 1(p) is done, the workers write D1
-// back over it as the A operand of GEMM 2(p), which accumulates the chunk's
-// depth sum in D2 (P_x); once GEMM 2(p) is done, X[p & 1] takes the staging
-// of plane p + 2, and the Toeplitz slot plane p + 1's pair.  Warp 0 (one
-// thread) issues the copies and the products; the 16 worker warps stage plane
-// p + 1 while the tensor cores run plane p, and meet the issuer on mbarriers
-// only, so a fast warp has its loads in flight while the others finish.
+// operand of GEMM 1(p) into D1, and X[p & 1] takes the staging of plane
+// p + 2 once GEMM 1(p) is done.  The workers hand D1 over, as BF16 hi and lo
+// parts, to GEMM 2's A operand A2 in tensor memory (once GEMM 2(p - 1) has
+// read it); GEMM 2(p) accumulates the chunk's depth sum in D2 (P_x); once it
+// is done, the Toeplitz slot takes plane p + 1's pair.  Warp 0 (one thread)
+// issues the copies and the products; the 16 worker warps stage plane p + 1
+// while the tensor cores run plane p, and meet the issuer on mbarriers only,
+// so a fast warp has its loads in flight while the others finish.
 //
 // Barriers (bars + 8 q): q = 0 Toeplitz pair; 1 GEMM 1; 2 GEMM 2; 3, 4 plane
 // staged into X[0], X[1] (every worker thread arrives); 5 D1 handed over
@@ -510,8 +516,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
         for (int q = 0; q < 7; ++q) mbar_init(bars + 8u * q, (q >= 3 && q <= 5) ? 32u * kWorkers : 1u);
         mbar_init_fence();
     }
-    const uint32_t tmem = tc_alloc(bars + kTmemSlot, a.tmem_cols);  // D1, D2
+    const uint32_t tmem = tc_alloc(bars + kTmemSlot, a.tmem_cols);  // D1, D2, A2 (hi, lo)
     const uint32_t d1 = tmem, d2 = tmem + (uint32_t)n;
+    const uint32_t a2hi = tmem + a2_tmem_col(n, 2), a2lo = a2hi + 64u;
     const uint32_t idesc = idesc_bf16(kTcM, n);
     const int kz = (nz + 15) / 16;  // GEMM 1's K steps
     const uint32_t tap = base;
@@ -542,7 +549,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
                 ok = mbar_wait(bar_a, (uint32_t)p & 1u);
                 if (!ok) break;
                 tc_fence_after();
-                issue_gemm2(xbuf(p & 1), part, tap, d2, idesc, n, p > 0, bar_2);
+                gemm2_chain_ts(a2hi, tap, d2, idesc, n, p > 0);
+                gemm2_chain_ts(a2hi, tap + (uint32_t)kTile, d2, idesc, n, true);
+                gemm2_chain_ts(a2lo, tap, d2, idesc, n, true);
+                tc_commit(bar_2);
                 // GEMM 2(p) done: the Toeplitz slot takes plane p+1's pair
                 ok = mbar_wait(bar_2, (uint32_t)p & 1u);
                 if (ok && p + 1 < np) tl.load(tap, tsrc(p + 1), bar_t);
@@ -557,28 +567,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
     } else {
         const int wi = warp - 1;
         if (a.atten && np > 1) prefetch_rows(arow(1), n, nz, wi);
-        bool ok = stage_rows(xbuf(0), part, rows, xb, arow(0), n, nz, plane(0), cs, c, wi, 0u, 0u);
+        stage_rows(xbuf(0), part, rows, xb, arow(0), n, nz, plane(0), cs, c, wi);
+        bool ok = true;
         fence_async_smem();
         mbar_arrive(bar_s);
         for (int p = 0; p < np && ok; ++p) {
             if (p + 1 < np) {
                 if (a.atten && p + 2 < np) prefetch_rows(arow(p + 2), n, nz, wi);
-                // X[(p+1)&1] last held the A operand of GEMM 2(p-1)
-                ok = stage_rows(xbuf((p + 1) & 1), part, rows, xb, arow(p + 1), n, nz, plane(p + 1), cs, c, wi,
-                                p > 0 ? bar_2 : 0u, (uint32_t)(p - 1) & 1u);
+                // X[(p+1)&1] was last read by GEMM 1(p-1), which this warp
+                // saw done before its previous hand-over
+                stage_rows(xbuf((p + 1) & 1), part, rows, xb, arow(p + 1), n, nz, plane(p + 1), cs, c, wi);
                 fence_async_smem();
                 mbar_arrive(bar_s + 8u * ((p + 1) & 1));
-            } else if (p > 0) {
-                ok = mbar_wait(bar_2, (uint32_t)(p - 1) & 1u);  // keep this warp's waits on bar_2 in order
             }
-            if (!ok) break;
-            // GEMM 1(p) is done: D1 becomes the A operand of GEMM 2(p), over
-            // GEMM 1(p)'s B operand in X[p&1]
-            ok = mbar_wait(bar_1, (uint32_t)p & 1u);
+            // GEMM 1(p) is done, and GEMM 2(p-1) has read A2: D1 becomes the
+            // A operand of GEMM 2(p)
+            ok = ok && mbar_wait(bar_1, (uint32_t)p & 1u);
+            if (ok && p > 0) ok = mbar_wait(bar_2, (uint32_t)(p - 1) & 1u);
             if (!ok) break;
             tc_fence_after();
-            d1_to_a2(xbuf(p & 1), part, d1, n);
-            fence_async_smem();
+            d1_to_a2_tmem(a2hi, a2lo, d1, n);
             tc_fence_before();
             mbar_arrive(bar_a);
         }
@@ -605,9 +613,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
 // ---------------------------------------------------------------- back blur
 //
 // The projection of the angle is the B operand of every plane's GEMM 1.
-// Plane p: GEMM 1(p) into D1; the workers hand D1 over to A2; GEMM 2(p) into
-// D2[p & 1]; the workers finish the plane from D2 (times A, stored as B)
-// while the tensor cores run plane p + 1.  The issuer starts GEMM 2(p) once
+// Plane p: GEMM 1(p) into D1; the workers hand D1 over, as BF16 hi and lo
+// parts, to GEMM 2's A operand A2 in tensor memory; GEMM 2(p) into D2[p & 1];
+// the workers finish the plane from D2 (times A, stored as B) while the
+// tensor cores run plane p + 1.  The issuer starts GEMM 2(p) once
 // A2 holds plane p and the workers have finished plane p - 2 from the same
 // D2 buffer.  T_hi has two slots and is copied a plane ahead; T_lo has one:
 // GEMM 2 runs its T_lo chain first, so that plane p + 1's T_lo is copied
@@ -633,9 +642,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
         for (int q = 0; q < 12; ++q) mbar_init(bars + 8u * q, (q >= 7 && q <= 10) ? 32u * kWorkers : 1u);
         mbar_init_fence();
     }
-    const uint32_t tmem = tc_alloc(bars + kTmemSlot, a.tmem_cols);  // D1, D2[0], D2[1]
+    const uint32_t tmem = tc_alloc(bars + kTmemSlot, a.tmem_cols);  // D1, D2[0], D2[1], A2 (hi, lo)
     const uint32_t d1 = tmem;
-    const uint32_t t_lo = base + 2u * kTile, b1 = base + 3u * kTile, a2 = b1 + 2u * part;
+    const uint32_t a2hi = tmem + a2_tmem_col(n, 3), a2lo = a2hi + 64u;
+    const uint32_t t_lo = base + 2u * kTile, b1 = base + 3u * kTile;
     const uint32_t idesc = idesc_bf16(kTcM, n);
     const int kz = (nz + 15) / 16;  // GEMM 1's K steps
     const int np = chunk < n ? (n - 1 - chunk) / a.chunks + 1 : 0;
@@ -681,10 +691,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
                 if (ok && p >= 2) ok = mbar_wait(bar_f + 8u * s, (uint32_t)((p - 2) >> 1) & 1u);
                 if (!ok) break;
                 tc_fence_after();
-                gemm2_chain(a2, t_lo, d2(s), idesc, n, false);
+                gemm2_chain_ts(a2hi, t_lo, d2(s), idesc, n, false);
                 tc_commit(bar_l);
-                gemm2_chain(a2, t_hi(s), d2(s), idesc, n, true);
-                gemm2_chain(a2 + part, t_hi(s), d2(s), idesc, n, true);
+                gemm2_chain_ts(a2hi, t_hi(s), d2(s), idesc, n, true);
+                gemm2_chain_ts(a2lo, t_hi(s), d2(s), idesc, n, true);
                 tc_commit(bar_2 + 8u * s);
                 // the T_lo chain done: the slot takes plane p+1's T_lo
                 ok = mbar_wait(bar_l, (uint32_t)p & 1u);
@@ -743,8 +753,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
             if (ok && p > 0) ok = mbar_wait(bar_2 + 8u * ((p - 1) & 1), (uint32_t)((p - 1) >> 1) & 1u);
             if (!ok) break;
             tc_fence_after();
-            d1_to_a2(a2, part, d1, n);
-            fence_async_smem();
+            d1_to_a2_tmem(a2hi, a2lo, d1, n);
             tc_fence_before();
             mbar_arrive(bar_a);
             if (p > 0) {
@@ -806,7 +815,7 @@ size_t bf16_smem_bytes(int n) { return std::max(fwd_smem(n), back_smem(n)); }
 uint32_t bf16_tmem_cols(int n, int tiles)
 {
     uint32_t c = 32;
-    while (c < (uint32_t)(tiles * n)) c <<= 1;
+    while (c < a2_tmem_col(n, tiles) + 128u) c <<= 1;
     return c;
 }
 
