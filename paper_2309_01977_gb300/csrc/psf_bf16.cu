@@ -250,16 +250,24 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// The issuing thread's record of the Toeplitz-tile copies per slot (slot s,
-// kTile bytes, completes on the barrier at bars + 8 s): a copy is pending
+// The bytes of a Toeplitz tile that the GEMMs read: its leading 64-column K
+// blocks (16 KB each) up to the larger of the axial size (GEMM 1's K) and
+// the plane width (GEMM 2's K).
+__host__ __device__ constexpr uint32_t tile_bytes(int n, int nz)
+{
+    return (uint32_t)(((n > nz ? n : nz) + 63) / 64) * (uint32_t)(kTcM * 128);
+}
+
+// The issuing thread's record of the Toeplitz-tile copies per slot (slot s
+// completes on the barrier at bars + 8 s): a copy is pending
 // from its issue until that thread has seen it land, and the parity bit of a
 // slot is that of its next completion.  After a timeout, drain() waits
 // (bounded) for the copies still in flight.
 struct TileLoads {
     uint32_t pend = 0, par = 0;
-    __device__ __forceinline__ void load(int s, uint32_t dst, const void* src, uint32_t bars)
+    __device__ __forceinline__ void load(int s, uint32_t dst, const void* src, uint32_t bytes, uint32_t bars)
     {
-        tma_load_1d(dst, src, (uint32_t)kTile, bars + 8u * s);
+        tma_load_1d(dst, src, bytes, bars + 8u * s);
         pend |= 1u << s;
     }
     __device__ __forceinline__ bool wait(int s, uint32_t bars)
@@ -285,9 +293,12 @@ struct TileLoads {
 // lands after the CTA has left.
 struct PairLoads {
     uint32_t pend = 0, par = 0;
-    __device__ __forceinline__ void load(uint32_t dst, const void* src, uint32_t bar)
+    // the leading `bytes` of T_hi (at src) and of T_lo (kTile bytes further)
+    __device__ __forceinline__ void load(uint32_t dst, const uint16_t* src, uint32_t bytes, uint32_t bar)
     {
-        tma_load_1d(dst, src, kPair, bar);
+        mbar_expect_tx(bar, 2u * bytes);
+        bulk_load(dst, src, bytes, bar);
+        bulk_load(dst + (uint32_t)kTile, src + kTcM * kTcM, bytes, bar);
         pend = 1;
     }
     __device__ __forceinline__ bool wait(uint32_t bar)
@@ -521,6 +532,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
     const uint32_t a2hi = tmem + a2_tmem_col(n, 2), a2lo = a2hi + 64u;
     const uint32_t idesc = idesc_bf16(kTcM, n);
     const int kz = (nz + 15) / 16;  // GEMM 1's K steps
+    const uint32_t tbytes = tile_bytes(n, nz);  // per Toeplitz tile copy
     const uint32_t tap = base;
     const int np = chunk < n ? (n - 1 - chunk) / a.chunks + 1 : 0;
     const float* xb = a.x + (size_t)b * n * n * nz;
@@ -539,7 +551,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
     } else if (warp == 0) {
         if (lane == 0) {
             PairLoads tl;
-            tl.load(tap, tsrc(0), bar_t);
+            tl.load(tap, tsrc(0), tbytes, bar_t);
             bool ok = true;
             for (int p = 0; p < np && ok; ++p) {
                 ok = mbar_wait(bar_s + 8u * (p & 1), (uint32_t)(p >> 1) & 1u) && tl.wait(bar_t);
@@ -555,7 +567,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_bf16_kernel(ForwardBf16
                 tc_commit(bar_2);
                 // GEMM 2(p) done: the Toeplitz slot takes plane p+1's pair
                 ok = mbar_wait(bar_2, (uint32_t)p & 1u);
-                if (ok && p + 1 < np) tl.load(tap, tsrc(p + 1), bar_t);
+                if (ok && p + 1 < np) tl.load(tap, tsrc(p + 1), tbytes, bar_t);
             }
             if (!ok) {
                 report_timeout(a.err);
@@ -648,6 +660,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
     const uint32_t t_lo = base + 2u * kTile, b1 = base + 3u * kTile;
     const uint32_t idesc = idesc_bf16(kTcM, n);
     const int kz = (nz + 15) / 16;  // GEMM 1's K steps
+    const uint32_t tbytes = tile_bytes(n, nz);  // per Toeplitz tile copy
     const int np = chunk < n ? (n - 1 - chunk) / a.chunks + 1 : 0;
     const size_t item = (size_t)b * a.n_sel + sidx;
     const float* pr = a.proj ? a.proj + (size_t)b * a.proj_bstride + (size_t)sidx * n * nz : nullptr;
@@ -664,9 +677,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
     if (np > 0 && warp == 0) {
         if (lane == 0) {
             TileLoads tl;  // slots 0, 1: T_hi; slot 2: T_lo
-            tl.load(0, t_hi(0), src_hi(0), bar_t);
-            tl.load(2, t_lo, src_lo(0), bar_t);
-            if (np > 1) tl.load(1, t_hi(1), src_hi(1), bar_t);
+            tl.load(0, t_hi(0), src_hi(0), tbytes, bar_t);
+            tl.load(2, t_lo, src_lo(0), tbytes, bar_t);
+            if (np > 1) tl.load(1, t_hi(1), src_hi(1), tbytes, bar_t);
             bool ok = mbar_wait(bar_s, 0u);
             for (int p = 0; p < np && ok; ++p) {
                 const int s = p & 1;
@@ -674,7 +687,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
                 if (p > 0) {
                     ok = mbar_wait(bar_2 + 8u * ((p - 1) & 1), (uint32_t)((p - 1) >> 1) & 1u);
                     if (!ok) break;
-                    if (p + 1 < np) tl.load((p + 1) & 1, t_hi((p + 1) & 1), src_hi(p + 1), bar_t);
+                    if (p + 1 < np) tl.load((p + 1) & 1, t_hi((p + 1) & 1), src_hi(p + 1), tbytes, bar_t);
                 }
                 // GEMM 1(p): the T_hi chains, then the T_lo chain
                 ok = tl.wait(s, bar_t);
@@ -698,7 +711,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) blur_back_bf16_kernel(BlurBackB
                 tc_commit(bar_2 + 8u * s);
                 // the T_lo chain done: the slot takes plane p+1's T_lo
                 ok = mbar_wait(bar_l, (uint32_t)p & 1u);
-                if (ok && p + 1 < np) tl.load(2, t_lo, src_lo(p + 1), bar_t);
+                if (ok && p + 1 < np) tl.load(2, t_lo, src_lo(p + 1), tbytes, bar_t);
             }
             if (!ok) {
                 report_timeout(a.err);
