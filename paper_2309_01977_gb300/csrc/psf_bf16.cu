@@ -3,11 +3,13 @@
 //
 // Per depth plane i, the 2-D blur of Eq. (1)'s T_cdr is K_i P = T_i P T_i^T
 // with T_i the symmetric banded Toeplitz matrix of the plane's Gaussian taps.
-// Both products are issued with K-major operands only:
+// Both products are issued with K-major operands:
 //   GEMM 1   D1[k][j]  = sum_k' T_i[k][k'] P[j][k']          (blur along z)
 //   GEMM 2   D2[k][j] += sum_j' X[k][j'] T_i[j][j']  with X = D1
 // so D2 = (T_i P T_i^T)^T, and the forward keeps D2 in TMEM across the depth
-// loop (P_x).  Every operand is split into two BF16 parts, v = v_hi + v_lo
+// loop (P_x).  GEMM 1 reads T_i and P from shared memory; GEMM 2 reads X
+// from tensor memory (the workers convert D1 there) and T_i from shared
+// memory.  Every operand is split into two BF16 parts, v = v_hi + v_lo
 // (v_lo = bf16(v - v_hi)), and each GEMM runs three MMA chains, T_hi v_hi +
 // T_lo v_hi + T_hi v_lo, dropping only T_lo v_lo (relative ~2^-18).
 // Measured against the FP64 oracle: image 3.4e-6 relative L2 on the 128^3 x
@@ -19,11 +21,11 @@
 // cores.
 //
 // Shared-memory operands are K-major tiles with the 128-byte swizzle (see
-// sw_off), so that both the staging (lanes along z) and the TMEM read-back
-// (lanes along the tile rows) store without bank conflicts.  The per-plane
-// Toeplitz pair (T_hi, T_lo: 64 KB) arrives by one TMA bulk copy into a
-// single slot as soon as the plane before has finished with it.  The kernels
-// are warp-specialised pipelines in which the tensor cores work on one plane
+// sw_off), so that the staging (lanes along z) stores without bank
+// conflicts.  The per-plane Toeplitz pair (T_hi, T_lo) arrives by TMA bulk
+// copies, only the 64-column K blocks the GEMMs read, into slots refilled as
+// soon as the products before have finished with them.  The kernels are
+// warp-specialised pipelines in which the tensor cores work on one plane
 // while the CUDA cores stage the next (forward) or finish the previous one
 // (back blur); see each kernel.
 //
