@@ -334,6 +334,29 @@ __device__ __forceinline__ float2 row_pair_value(const RowSrc& r, int c)
     return v;
 }
 
+// The row's values at columns klo + c .. klo + c + 3 (c a multiple of 4;
+// 16-byte aligned loads), each with the arithmetic of row_pair_value.
+template <bool kSmemA>
+__device__ __forceinline__ float4 row_quad_value(const RowSrc& r, int c)
+{
+    const float4 f0 = __ldg(reinterpret_cast<const float4*>(r.f[0] + c));
+    float2 lo = make_float2(r.w[0] * f0.x, r.w[0] * f0.y), hi = make_float2(r.w[0] * f0.z, r.w[0] * f0.w);
+#pragma unroll
+    for (int q = 1; q < 4; ++q) {
+        const float4 f = __ldg(reinterpret_cast<const float4*>(r.f[q] + c));
+        const float2 w = make_float2(r.w[q], r.w[q]);
+        lo = __ffma2_rn(w, make_float2(f.x, f.y), lo);
+        hi = __ffma2_rn(w, make_float2(f.z, f.w), hi);
+    }
+    if (r.a) {
+        const float4 a = kSmemA ? *reinterpret_cast<const float4*>(r.a + c)
+                                : __ldg(reinterpret_cast<const float4*>(r.a + c));
+        lo = make_float2(lo.x * a.x, lo.y * a.y);
+        hi = make_float2(hi.x * a.z, hi.y * a.w);
+    }
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
 // P quads of every row pair over columns [klo, khi) (both even), from the
 // row table: one row pair per warp at a time, lanes on consecutive column
 // pairs.  Rows at or past n are zero.  In a partial last pass the column is
@@ -346,6 +369,35 @@ __device__ __forceinline__ void stage_plane(float4* P, const PlaneTiling& t, con
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int ncols = khi - klo;
+    // A row that fits one pass of 16-byte loads (4 columns per lane), with
+    // every source row and the attenuation row 16-byte aligned at klo: half
+    // the load instructions of the 8-byte path below, the same values.
+    const bool wide = ncols <= 128 && (ncols & 3) == 0 && (klo & 3) == 0 && (aoff & 3) == 0 && (astride & 3) == 0;
+    if (wide) {
+        for (int jp = warp; jp < (t.npad >> 1); jp += nw) {
+            float4* prow = P + jp * t.sp + ((klo - kw0) >> 1);
+            const int j0 = 2 * jp, j1 = 2 * jp + 1;
+            const int c4 = 4 * lane;
+            if (j0 >= n) {
+                if (c4 < ncols) {
+                    prow[c4 >> 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    prow[(c4 >> 1) + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                continue;
+            }
+            const RowSrc r0 = row_src(rows, j0, xb, arow, astride, aoff, klo);
+            const RowSrc r1 = row_src(rows, j1 < n ? j1 : j0, xb, arow, astride, aoff, klo);
+            const int x4 = min(c4, ncols - 4);
+            const float4 v0 = row_quad_value<kSmemA>(r0, x4);
+            float4 v1 = row_quad_value<kSmemA>(r1, x4);
+            if (j1 >= n) v1 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c4 < ncols) {
+                prow[c4 >> 1] = make_float4(v0.x, v1.x, v0.y, v1.y);
+                prow[(c4 >> 1) + 1] = make_float4(v0.z, v1.z, v0.w, v1.w);
+            }
+        }
+        return;
+    }
     for (int jp = warp; jp < (t.npad >> 1); jp += nw) {
         float4* prow = P + jp * t.sp + ((klo - kw0) >> 1);
         const int j0 = 2 * jp, j1 = 2 * jp + 1;
