@@ -135,56 +135,75 @@ cudaError_t launch_gather_tiled_tables(const float4* cs, int n, int nz, int n_an
 
 namespace {
 
-// Warp 0 fills buffer `buf` for one angle: lane 0 announces the bytes on
+// The footprint descriptor of one (angle, tile), as the issuing warp holds
+// it: every lane the header, lane l the run of footprint row l
+// (kFpMaxRows = 32, so one row per lane covers every footprint).  Read from
+// the CTA's shared-memory copy of its descriptors.
+struct Footprint {
+    int i0, ni, rows;  // first rotated row, rows i, footprint rows in all
+    int jlo, len;      // this lane's row: first j and length of its run
+};
+
+__device__ __forceinline__ Footprint read_footprint(const int* d)
+{
+    const int lane = threadIdx.x & 31;
+    Footprint f;
+    f.i0 = d[0];
+    f.ni = d[1];
+    f.rows = d[2];
+    // in bounds for every lane (kFpDescInts = 4 + 2 * 32); rows past ni are
+    // ignored at the copies
+    f.jlo = d[4 + 2 * lane];
+    f.len = d[5 + 2 * lane];
+    return f;
+}
+
+// The issuing warp fills buffer `buf` for one angle: lane 0 announces the bytes on
 // `bar` and copies the tile's table slice (after the footprint rows, at row
-// rows_cap); lane l copies footprint row-run l (and l + 32, ...).  zs == nz:
-// one copy per run of rows (contiguous); else one copy per row of the z
-// segment [z0, z0 + zs).
-__device__ __forceinline__ void issue_footprint(const GatherTiledArgs& a, const int* __restrict__ d,
+// rows_cap); lane l copies footprint row-run l.  zs == nz: one copy per run
+// of rows (contiguous); else one copy per row of the z segment
+// [z0, z0 + zs).
+__device__ __forceinline__ void issue_footprint(const GatherTiledArgs& a, const Footprint& f,
                                                 const int2* __restrict__ tab, const float* __restrict__ bslot,
                                                 uint32_t buf, uint32_t bar)
 {
     const int lane = threadIdx.x & 31;
-    const int i0 = __ldg(d + 0), ni = __ldg(d + 1), rows = __ldg(d + 2);
     const int z0 = blockIdx.z * a.zs;
     const uint32_t row_bytes = (uint32_t)a.zs * 4u;
     const uint32_t tab_bytes = (uint32_t)(a.T * a.T * kMaxCand) * 8u;
     if (lane == 0) {
-        mbar_expect_tx(bar, (uint32_t)rows * row_bytes + tab_bytes);
+        mbar_expect_tx(bar, (uint32_t)f.rows * row_bytes + tab_bytes);
         bulk_load(buf + (uint32_t)a.rows_cap * row_bytes, tab, tab_bytes, bar);
     }
     __syncwarp();
-    // offsets of the runs: exclusive prefix of the lengths over the warp
-    int off = 0;
-    for (int r0 = 0; r0 < ni; r0 += 32) {
-        const int r = r0 + lane;
-        const int jlo = r < ni ? __ldg(d + 4 + 2 * r) : 0;
-        const int len = r < ni ? __ldg(d + 5 + 2 * r) : 0;
-        int incl = len;
+    // offset of this lane's run: exclusive prefix of the lengths over the warp
+    const int len = lane < f.ni ? f.len : 0;
+    int incl = len;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int start = incl - len;
+    if (len > 0) {
+        const float* src = bslot + ((size_t)(f.i0 + lane) * a.n + f.jlo) * a.nz + z0;
+        if (a.zs == a.nz) {
+            bulk_load(buf + (uint32_t)start * row_bytes, src, (uint32_t)len * row_bytes, bar);
+        } else {
+            for (int q = 0; q < len; ++q)
+                bulk_load(buf + (uint32_t)(start + q) * row_bytes, src + (size_t)q * a.nz, row_bytes, bar);
         }
-        const int start = off + incl - len;
-        if (len > 0) {
-            const float* src = bslot + ((size_t)(i0 + r) * a.n + jlo) * a.nz + z0;
-            if (a.zs == a.nz) {
-                bulk_load(buf + (uint32_t)start * row_bytes, src, (uint32_t)len * row_bytes, bar);
-            } else {
-                for (int q = 0; q < len; ++q)
-                    bulk_load(buf + (uint32_t)(start + q) * row_bytes, src + (size_t)q * a.nz, row_bytes, bar);
-            }
-        }
-        off += __shfl_sync(0xffffffffu, incl, 31);
     }
 }
 
 }  // namespace
 
-// 256 threads: warp w sums columns w, w + 8, ... of the T x T tile; lane l
-// holds float4 l of the z segment (lanes past zs/4 idle).  Two CTAs per SM
-// (their shared memory allows two): at most 128 registers.
+// 288 threads: warps w < 8 sum columns w, w + 8, ... of the T x T tile, lane
+// l holding float4 l of the z segment (lanes past zs/4 idle); warp 8 issues
+// the footprint copies (about a dozen bulk copies an angle, which take as
+// long to issue as the sums of an angle take), so that they overlap the
+// sums.  Two CTAs per SM (their shared memory allows two): at most 112
+// registers.
 template <int T>
 __global__ void __launch_bounds__(kGatherTiledThreads, 2) gather_tiled_kernel(GatherTiledArgs a)
 {
@@ -193,6 +212,7 @@ __global__ void __launch_bounds__(kGatherTiledThreads, 2) gather_tiled_kernel(Ga
     const int tiles_x = (a.n + T - 1) / T;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool producer = warp == kGatherSumWarps;
     const int zw = a.zs >> 2;  // float4 per row segment
     const int z0 = blockIdx.z * a.zs;
     const size_t vol = (size_t)a.n * a.n * a.nz;
@@ -200,24 +220,45 @@ __global__ void __launch_bounds__(kGatherTiledThreads, 2) gather_tiled_kernel(Ga
     constexpr int kCols = (ncols + 7) / 8;  // columns per warp
     const size_t buf_f4 = (size_t)a.rows_cap * zw + (size_t)T * T * kMaxCand / 2;  // rows, then the table
     const int S = a.stages;  // footprint buffers: angle g uses buffer g % S
+    // shared memory: S footprint buffers, S + 1 mbarriers (the buffers',
+    // then the descriptors'), the CTA's footprint descriptors and angle ids
     float4* bufs = gsm;
     uint64_t* bars = reinterpret_cast<uint64_t*>(gsm + S * buf_f4);
+    int* sdesc = reinterpret_cast<int*>(gsm + S * buf_f4 + (S + 2) / 2);
+    int* s_sel = sdesc + a.n_sel * kFpDescInts;
     const float* bvol_b = a.bvol + (size_t)b * a.n_sel * vol;
     const size_t tab_stride = (size_t)a.n_tiles * ncols * kMaxCand;  // per angle
 
     if (threadIdx.x == 0) {
-        for (int q = 0; q < S; ++q) mbar_init(smem_u32(bars + q), 1);
+        for (int q = 0; q <= S; ++q) mbar_init(smem_u32(bars + q), 1);
         mbar_init_fence();
     }
     __syncthreads();
+    // The producer warp copies the CTA's descriptors (one per angle of the
+    // group, lane g the one of angle g; n_sel <= 32, checked at launch) into
+    // shared memory, then issues the first footprints.
     auto issue = [&](int g) {
         const int q = g % S;
-        issue_footprint(a, a.desc + ((size_t)a.sel[g] * a.n_tiles + tile) * kFpDescInts,
-                        a.tab + (size_t)a.sel[g] * tab_stride + (size_t)tile * ncols * kMaxCand,
+        issue_footprint(a, read_footprint(sdesc + g * kFpDescInts),
+                        a.tab + (size_t)s_sel[g] * tab_stride + (size_t)tile * ncols * kMaxCand,
                         bvol_b + (size_t)g * vol, smem_u32(bufs + q * buf_f4), smem_u32(bars + q));
     };
-    if (warp == 0)
-        for (int g = 0; g < S - 1 && g < a.n_sel; ++g) issue(g);
+    bool desc_ok = true;
+    if (producer) {
+        const uint32_t dbar = smem_u32(bars + S);
+        if (lane == 0) mbar_expect_tx(dbar, (uint32_t)a.n_sel * kFpDescInts * 4u);
+        __syncwarp();
+        if (lane < a.n_sel) {
+            const int ag = __ldg(a.sel + lane);
+            s_sel[lane] = ag;
+            bulk_load(smem_u32(sdesc + lane * kFpDescInts), a.desc + ((size_t)ag * a.n_tiles + tile) * kFpDescInts,
+                      kFpDescInts * 4u, dbar);
+        }
+        desc_ok = mbar_wait(dbar, 0);
+        __syncwarp();
+        if (desc_ok)
+            for (int g = 0; g < S - 1 && g < a.n_sel; ++g) issue(g);
+    }
 
     float4 acc[kCols];
 #pragma unroll
@@ -227,50 +268,52 @@ __global__ void __launch_bounds__(kGatherTiledThreads, 2) gather_tiled_kernel(Ga
     for (; g < a.n_sel; ++g) {
         // buffer (g + S - 1) % S was last read by angle g - 1, before the
         // barrier that ended it
-        if (warp == 0 && g + S - 1 < a.n_sel) {
+        if (producer && desc_ok && g + S - 1 < a.n_sel) {
             fence_async_smem();
             issue(g + S - 1);
         }
         const int q = g % S;
-        const bool landed = mbar_wait(smem_u32(bars + q), (uint32_t)((g / S) & 1));
+        const bool landed = producer ? desc_ok : mbar_wait(smem_u32(bars + q), (uint32_t)((g / S) & 1));
         const float4* buf = bufs + q * buf_f4;
         const int2* tab = reinterpret_cast<const int2*>(buf + (size_t)a.rows_cap * zw);
-        // Columns in groups of kGroup (all of a warp's columns at T = 8),
-        // candidate slot by slot: the slot's
-        // entries of the group's columns are read together (each a
-        // warp-wide broadcast of one shared-memory word), then their data
-        // rows, then the sums, so that the group's loads are in flight at
-        // once.  A column's candidates come first in its list, in the order
-        // they are summed; a slot empty in every column of the group ends it.
-        constexpr int kGroup = 8;
-#pragma unroll
-        for (int k0 = 0; k0 < kCols; k0 += kGroup) {
-#pragma unroll 1
-            for (int e = 0; e < kMaxCand; ++e) {
-                int2 ent[kGroup];
-                bool any = false;
-#pragma unroll
-                for (int u = 0; u < kGroup; ++u) {
-                    const int cl = warp + 8 * (k0 + u);
-                    ent[u] = (landed && k0 + u < kCols && cl < ncols) ? tab[cl * kMaxCand + e] : make_int2(0, 0);
-                    any |= ent[u].y != 0;
-                }
-                if (!any) break;
-                if (lane < zw) {
-                    float4 v[kGroup];
-#pragma unroll
-                    for (int u = 0; u < kGroup; ++u)
-                        if (k0 + u < kCols && ent[u].y != 0) v[u] = buf[(size_t)ent[u].x * zw + lane];
-#pragma unroll
+        if (!producer) {
+            // Columns in groups of kGroup (all of a warp's columns at T = 8),
+            // candidate slot by slot: the slot's
+            // entries of the group's columns are read together (each a
+            // warp-wide broadcast of one shared-memory word), then their data
+            // rows, then the sums, so that the group's loads are in flight at
+            // once.  A column's candidates come first in its list, in the order
+            // they are summed; a slot empty in every column of the group ends it.
+            constexpr int kGroup = 8;
+    #pragma unroll
+            for (int k0 = 0; k0 < kCols; k0 += kGroup) {
+    #pragma unroll 1
+                for (int e = 0; e < kMaxCand; ++e) {
+                    int2 ent[kGroup];
+                    bool any = false;
+    #pragma unroll
                     for (int u = 0; u < kGroup; ++u) {
-                        if (k0 + u >= kCols || ent[u].y == 0) continue;
-                        const float w = __int_as_float(ent[u].y);
-                        float4& a4 = acc[k0 + u];
-                        const float2 lo = __ffma2_rn(make_float2(w, w), make_float2(v[u].x, v[u].y),
-                                                     make_float2(a4.x, a4.y));
-                        const float2 hi = __ffma2_rn(make_float2(w, w), make_float2(v[u].z, v[u].w),
-                                                     make_float2(a4.z, a4.w));
-                        a4 = make_float4(lo.x, lo.y, hi.x, hi.y);
+                        const int cl = warp + 8 * (k0 + u);
+                        ent[u] = (landed && k0 + u < kCols && cl < ncols) ? tab[cl * kMaxCand + e] : make_int2(0, 0);
+                        any |= ent[u].y != 0;
+                    }
+                    if (!any) break;
+                    if (lane < zw) {
+                        float4 v[kGroup];
+    #pragma unroll
+                        for (int u = 0; u < kGroup; ++u)
+                            if (k0 + u < kCols && ent[u].y != 0) v[u] = buf[(size_t)ent[u].x * zw + lane];
+    #pragma unroll
+                        for (int u = 0; u < kGroup; ++u) {
+                            if (k0 + u >= kCols || ent[u].y == 0) continue;
+                            const float w = __int_as_float(ent[u].y);
+                            float4& a4 = acc[k0 + u];
+                            const float2 lo = __ffma2_rn(make_float2(w, w), make_float2(v[u].x, v[u].y),
+                                                         make_float2(a4.x, a4.y));
+                            const float2 hi = __ffma2_rn(make_float2(w, w), make_float2(v[u].z, v[u].w),
+                                                         make_float2(a4.z, a4.w));
+                            a4 = make_float4(lo.x, lo.y, hi.x, hi.y);
+                        }
                     }
                 }
             }
@@ -287,34 +330,49 @@ __global__ void __launch_bounds__(kGatherTiledThreads, 2) gather_tiled_kernel(Ga
         return;
     }
 
-    // epilogue: store, accumulate, or the fused OSEM update
+    // epilogue: store, accumulate, or the fused OSEM update.  The image
+    // values and sensitivities of kEpi columns are loaded before any of their
+    // stores: in program order a store could alias the next column's loads,
+    // and each column would wait out its own memory round trip.
+    if (producer) return;
+    constexpr int kEpi = kCols < 4 ? kCols : 4;
+    const bool upd = a.upd.mode != kUpdNone;
+    const bool need_x = upd || a.accumulate;
+    float4* out_b = reinterpret_cast<float4*>(a.out + (size_t)b * vol);
 #pragma unroll
-    for (int k = 0; k < kCols; ++k) {
-        const int cl = warp + 8 * k;
-        const int x = tx * T + cl / T, y = ty * T + cl % T;
-        if (cl < ncols && x < a.n && y < a.n && lane < zw) {
-            const size_t col = (size_t)x * a.n + y;
-            float4* o = reinterpret_cast<float4*>(a.out + (size_t)b * vol + col * a.nz + z0) + lane;
-            const float4 s4 = acc[k];
-            if (a.upd.mode != kUpdNone) {
-                *o = update4(a.upd, *o, s4, ((col * a.nz + z0) >> 2) + lane);
-            } else if (a.accumulate) {
-                float4 f = *o;
-                f.x += s4.x;
-                f.y += s4.y;
-                f.z += s4.z;
-                f.w += s4.w;
-                *o = f;
-            } else {
-                *o = s4;
-            }
+    for (int k0 = 0; k0 < kCols; k0 += kEpi) {
+        float4 xv[kEpi], sv[kEpi];
+        size_t i4[kEpi];
+        bool live[kEpi];
+#pragma unroll
+        for (int u = 0; u < kEpi; ++u) {
+            const int cl = warp + 8 * (k0 + u);
+            const int x = tx * T + cl / T, y = ty * T + cl % T;
+            live[u] = cl < ncols && x < a.n && y < a.n && lane < zw;
+            i4[u] = ((((size_t)x * a.n + y) * a.nz + z0) >> 2) + lane;  // float4 of the volume
+            xv[u] = sv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (live[u] && need_x) xv[u] = out_b[i4[u]];
+            if (live[u] && upd) sv[u] = __ldg(reinterpret_cast<const float4*>(a.upd.sens) + i4[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kEpi; ++u) {
+            if (!live[u]) continue;
+            const float4 s4 = acc[k0 + u];
+            if (upd)
+                out_b[i4[u]] = update4_sv(a.upd, xv[u], s4, sv[u], i4[u]);
+            else if (a.accumulate)
+                out_b[i4[u]] = make_float4(xv[u].x + s4.x, xv[u].y + s4.y, xv[u].z + s4.z, xv[u].w + s4.w);
+            else
+                out_b[i4[u]] = s4;
         }
     }
 }
 
-size_t gather_tiled_smem(int rows_cap, int zs, int T, int stages)
+size_t gather_tiled_smem(int rows_cap, int zs, int T, int stages, int n_sel)
 {
-    return stages * ((size_t)rows_cap * zs * sizeof(float) + (size_t)T * T * kMaxCand * sizeof(int2) + 8);
+    const size_t bufs = stages * ((size_t)rows_cap * zs * sizeof(float) + (size_t)T * T * kMaxCand * sizeof(int2));
+    const size_t bars = 16 * (size_t)((stages + 2) / 2);
+    return bufs + bars + (size_t)n_sel * (kFpDescInts + 1) * sizeof(int);
 }
 
 template <int T>
@@ -332,8 +390,9 @@ cudaError_t launch_gather_tiled_t(const GatherTiledArgs& a, cudaStream_t st)
         if (e != cudaSuccess) return e;
         mask |= 1ull << (dev & 63);
     }
+    if (a.n_sel > 32) return cudaErrorInvalidValue;  // warp 0 holds one angle id per lane
     dim3 grid(a.n_tiles, a.batch, a.nz / a.zs);
-    gather_tiled_kernel<T><<<grid, kGatherTiledThreads, gather_tiled_smem(a.rows_cap, a.zs, T, a.stages), st>>>(a);
+    gather_tiled_kernel<T><<<grid, kGatherTiledThreads, gather_tiled_smem(a.rows_cap, a.zs, T, a.stages, a.n_sel), st>>>(a);
     return cudaGetLastError();
 }
 

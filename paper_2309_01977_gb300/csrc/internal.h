@@ -136,7 +136,9 @@ struct GatherArgs {
 // rows of each angle staged in shared memory by bulk copies.
 constexpr int kFpMaxRows = 32;                    // rotated rows i per footprint
 constexpr int kFpDescInts = 4 + 2 * kFpMaxRows;   // {i0, ni, rows, 0}, then (jlo, len) per i
-constexpr int kGatherTiledThreads = 256;
+constexpr int kGatherMaxAngles = 16;                                // angles per back blur + gather launch
+constexpr int kGatherSumWarps = 8;                                  // tiled gather: warps that sum
+constexpr int kGatherTiledThreads = 32 * (kGatherSumWarps + 1);      // and one that issues the copies
 
 struct GatherTiledArgs {
     const float* bvol;     // [batch][n_sel][n][n][nz]
@@ -199,7 +201,7 @@ cudaError_t launch_gather_tables(const float4* cs, int n, int nz, int n_angles, 
 cudaError_t launch_gather_tiled_tables(const float4* cs, int n, int nz, int n_angles, int T, int2* tab, int* desc,
                                        int* rows_max, int* err, cudaStream_t st);
 cudaError_t launch_gather_tiled(const GatherTiledArgs& a, cudaStream_t st);
-size_t gather_tiled_smem(int rows_cap, int zs, int T, int stages);
+size_t gather_tiled_smem(int rows_cap, int zs, int T, int stages, int n_sel);  // n_sel: angles per launch
 int forward_max_blocks_per_sm(const PlaneTiling& t);
 
 // Per-IPT instantiations (one translation unit each, compiled in parallel).

@@ -372,7 +372,7 @@ int run_back(spect_plan* p, spect_plan_scratch& sc, const float* proj, float* x_
              int batch, const UpdateSpec* upd, cudaStream_t st, bool accumulate = false)
 {
     const size_t vol = vol_elems(p), plane = plane_elems(p);
-    const int gmax = (int)std::min<size_t>(16, p->bvol_cap);
+    const int gmax = (int)std::min<size_t>(kGatherMaxAngles, p->bvol_cap);
     const bool fused = upd && n_sel <= gmax;
     // Angle groups of a fixed size (independent of the batch, so that each
     // volume is summed in the same order alone or in a batch), and as many
@@ -998,7 +998,7 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
         p->gt_rows = std::max(rows, 1);
         p->gt_zs = p->nz;
         p->gt_stages = 2;
-        if (err != 0 || gather_tiled_smem(p->gt_rows, p->gt_zs, p->gt_T, 2) > (size_t)smem_optin) {
+        if (err != 0 || gather_tiled_smem(p->gt_rows, p->gt_zs, p->gt_T, 2, kGatherMaxAngles) > (size_t)smem_optin) {
             // footprints too large for shared memory: the per-column gather
             p->gather_tiled = false;
             SPECT_CK(cudaMemsetAsync(p->d_err, 0, sizeof(int), st), "clear status");

@@ -30,19 +30,24 @@ __device__ __forceinline__ float update1(const UpdateSpec& u, float f, float bp,
     }
 }
 
-// Float4 i4 of a volume: x holds the current image, bp the back projection.
-__device__ __forceinline__ float4 update4(const UpdateSpec& u, float4 x, float4 bp, size_t i4)
+// Float4 i4 of a volume: x holds the current image, bp the back projection,
+// sv the subset sensitivity (loaded by the caller).
+__device__ __forceinline__ float4 update4_sv(const UpdateSpec& u, float4 x, float4 bp, float4 sv, size_t i4)
 {
     if (u.bp_add) {
         const float4 b2 = __ldg(reinterpret_cast<const float4*>(u.bp_add) + i4);
         bp = make_float4(bp.x + b2.x, bp.y + b2.y, bp.z + b2.z, bp.w + b2.w);
     }
-    const float4 sv = __ldg(reinterpret_cast<const float4*>(u.sens) + i4);
     float4 gv = make_float4(0.f, 0.f, 0.f, 0.f), sa = gv;
     if (u.grad) gv = __ldg(reinterpret_cast<const float4*>(u.grad) + i4);
     if (u.sens_all) sa = __ldg(reinterpret_cast<const float4*>(u.sens_all) + i4);
     return make_float4(update1(u, x.x, bp.x, sv.x, gv.x, sa.x), update1(u, x.y, bp.y, sv.y, gv.y, sa.y),
                        update1(u, x.z, bp.z, sv.z, gv.z, sa.z), update1(u, x.w, bp.w, sv.w, gv.w, sa.w));
+}
+
+__device__ __forceinline__ float4 update4(const UpdateSpec& u, float4 x, float4 bp, size_t i4)
+{
+    return update4_sv(u, x, bp, __ldg(reinterpret_cast<const float4*>(u.sens) + i4), i4);
 }
 
 }  // namespace spect
