@@ -1,18 +1,23 @@
-// Transpose of the bilinear rotation (T_rot^T of Eq. 1), tiled: the same
-// sums as gather_kernel, with the rotated-frame rows that a tile of output
-// columns needs staged in shared memory by bulk copies.
+// Transpose of the bilinear rotation (T_rot^T of Eq. 1), tiled: the sums of
+// gather_kernel, with the rotated-frame rows that a tile of output columns
+// needs staged in shared memory by bulk copies.
 //
-// Output columns q = (x, y) are grouped in T x T tiles.  For angle a, the
+// Output columns q = (x, y) are grouped in 8 x 8 tiles.  For angle a, the
 // footprint of a tile is the set of rotated-frame rows p = (i, j) with a
 // nonzero bilinear weight toward some column of the tile; for each i it is
 // held as the whole run j in [jlo_i, jlo_i + len_i), which is contiguous in
 // the rotated-frame volume B_a[i][j][z].  The plan stores, per (angle,
 // tile):
 //   a descriptor  {i0, ni, rows} and (jlo_i, len_i) for i = i0 .. i0+ni-1;
-//   per column of the tile, up to kMaxCand (row of the footprint in its
-//   shared-memory copy, weight) entries, in the order of gather_kernel's
-//   table (rotated row i, then j), with the weights recomputed by the
-//   forward's own arithmetic, so the sums are bitwise those of gather_kernel.
+//   per row y of the tile, the footprint samples whose weights reach it, in
+//   lists by the column of their lower weight, each entry {row of the
+//   footprint in its shared-memory copy, weight to that column, weight to
+//   the next}.  The weights are the products gather_kernel's table forms
+//   (recomputed by the forward's own arithmetic); a sample is read from
+//   shared memory once per tile row and added to both its columns, half the
+//   reads of a per-column walk.  Each column's sum runs over its samples in
+//   list order (row-major within a list), so it differs from gather_kernel's
+//   by the rounding of the summation order only.
 // The gather CTA of (tile, z segment, batch entry) walks the subset's
 // angles through `stages` footprint buffers: while it sums angle g, the
 // bulk copies of the next angles fill the other buffers.  Every wait is
@@ -28,7 +33,8 @@ namespace spect {
 
 // ---------------------------------------------------------------- tables
 
-// One CTA per (tile, angle), one thread per column of the tile.
+// One CTA per (tile, angle): first one thread per column of the tile (the
+// footprint), then one per strip list.
 __global__ void gather_tiled_table_kernel(const float4* __restrict__ cs_tab, int n, int nz, int T, int tiles_x,
                                           int2* __restrict__ tab, int* __restrict__ desc, int* __restrict__ rows_max,
                                           int* __restrict__ err)
@@ -51,7 +57,7 @@ __global__ void gather_tiled_table_kernel(const float4* __restrict__ cs_tab, int
     __syncthreads();
 
     // candidates of this column, enumerated exactly as gather_table_kernel
-    int ci[kMaxCand], cj[kMaxCand], cw[kMaxCand];
+    int ci[kMaxCand], cj[kMaxCand];
     int count = 0;
     if (live) {
         const float c = 0.5f * (float)(n - 1);
@@ -74,7 +80,6 @@ __global__ void gather_tiled_table_kernel(const float4* __restrict__ cs_tab, int
                 if (wx != 0.f && wy != 0.f && count < kMaxCand) {
                     ci[count] = i;
                     cj[count] = j;
-                    cw[count] = __float_as_int(wx * wy);
                     ++count;
                 }
             }
@@ -110,13 +115,55 @@ __global__ void gather_tiled_table_kernel(const float4* __restrict__ cs_tab, int
         if (!fits) atomicExch(err, SPECT_EINVAL);
     }
     __syncthreads();
-    if (cl < T * T) {
-        int2* out = tab + (((size_t)angle * gridDim.x + tile) * (T * T) + cl) * kMaxCand;
-        for (int e = 0; e < kMaxCand; ++e) {
-            if (e < count && fits)
-                out[e] = make_int2(s_off[ci[e] - i0] + cj[e] - s_jlo[ci[e] - i0], cw[e]);
-            else
-                out[e] = make_int2(0, 0);
+    // Strip lists: thread (w, l) of the first kGtT * kGtLists builds list l
+    // of tile row w, the footprint's samples (i, j) in row-major order whose
+    // lower bilinear column is xa = tx T + l - 1 and whose rows ya, ya + 1
+    // include the tile row y: weights (1 - ax) wy to column xa and ax wy to
+    // xa + 1, each the product gather_kernel's table forms (zero where the
+    // column lies outside the tile or the volume).  Two passes: count, then
+    // write when the list fits its kGtMaxList slots (else the plan takes the
+    // per-column gather).
+    const int lt = threadIdx.x;
+    const bool lister = fits && lt < kGtT * kGtLists;
+    const int w = lt / kGtLists, l = lt % kGtLists;
+    const int yr = ty * T + w, xa_l = tx * T + l - 1;
+    auto walk = [&](int2* out) {
+        int count = 0;
+        if (!lister || yr >= n) return 0;
+        const float c = 0.5f * (float)(n - 1);
+        const float4 cs = cs_tab[angle];
+        for (int r = 0; r < ni; ++r) {
+            if (s_jhi[r] < s_jlo[r]) continue;
+            for (int j = s_jlo[r]; j <= s_jhi[r]; ++j) {
+                float u, v;
+                sample_point(cs.x, cs.y, c, cs.z, i0 + r, j, u, v);
+                const float fu = floorf(u), fv = floorf(v);
+                const int xa = (int)fu, ya = (int)fv;
+                if (xa != xa_l) continue;
+                const float ax = u - fu, by = v - fv;
+                const float wy = (yr == ya) ? (1.f - by) : (yr == ya + 1 ? by : 0.f);
+                if (wy == 0.f) continue;
+                const float w0 = (l >= 1 && xa < n) ? (1.f - ax) * wy : 0.f;
+                const float w1 = (l + 1 <= T && xa + 1 < n) ? ax * wy : 0.f;
+                if (w0 == 0.f && w1 == 0.f) continue;
+                if (out) {
+                    out[2 * count] = make_int2(s_off[r] + j - s_jlo[r], __float_as_int(w0));
+                    out[2 * count + 1] = make_int2(__float_as_int(w1), 0);
+                }
+                ++count;
+            }
+        }
+        return count;
+    };
+    int* hdr = reinterpret_cast<int*>(tab) + ((size_t)angle * gridDim.x + tile) * (kGtSliceBytes / 4);
+    int2* ent = reinterpret_cast<int2*>(hdr + kGtT * kGtHdr);
+    if (lister) {
+        const int cnt = walk(nullptr);
+        if (cnt > kGtMaxList) {
+            atomicExch(err, SPECT_EINVAL);
+        } else {
+            walk(ent + 2 * (size_t)kGtMaxList * (w * kGtLists + l));
+            hdr[w * kGtHdr + l] = cnt;
         }
     }
 }
@@ -126,7 +173,8 @@ cudaError_t launch_gather_tiled_tables(const float4* cs, int n, int nz, int n_an
 {
     const int tiles_x = (n + T - 1) / T;
     dim3 grid(tiles_x * tiles_x, n_angles);
-    gather_tiled_table_kernel<<<grid, ((T * T + 31) / 32) * 32, 0, st>>>(cs, n, nz, T, tiles_x, tab, desc, rows_max,
+    if (T != kGtT) return cudaErrorInvalidValue;
+    gather_tiled_table_kernel<<<grid, ((kGtT * kGtLists + 31) / 32) * 32, 0, st>>>(cs, n, nz, T, tiles_x, tab, desc, rows_max,
                                                                           err);
     return cudaGetLastError();
 }
@@ -170,7 +218,7 @@ __device__ __forceinline__ void issue_footprint(const GatherTiledArgs& a, const 
     const int lane = threadIdx.x & 31;
     const int z0 = blockIdx.z * a.zs;
     const uint32_t row_bytes = (uint32_t)a.zs * 4u;
-    const uint32_t tab_bytes = (uint32_t)(a.T * a.T * kMaxCand) * 8u;
+    const uint32_t tab_bytes = (uint32_t)kGtSliceBytes;
     if (lane == 0) {
         mbar_expect_tx(bar, (uint32_t)f.rows * row_bytes + tab_bytes);
         bulk_load(buf + (uint32_t)a.rows_cap * row_bytes, tab, tab_bytes, bar);
@@ -204,9 +252,17 @@ __device__ __forceinline__ void issue_footprint(const GatherTiledArgs& a, const 
 // long to issue as the sums of an angle take), so that they overlap the
 // sums.  Two CTAs per SM (their shared memory allows two): at most 112
 // registers.
+__device__ __forceinline__ void fma4(float4& a4, float w, const float4& v)
+{
+    const float2 lo = __ffma2_rn(make_float2(w, w), make_float2(v.x, v.y), make_float2(a4.x, a4.y));
+    const float2 hi = __ffma2_rn(make_float2(w, w), make_float2(v.z, v.w), make_float2(a4.z, a4.w));
+    a4 = make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
 template <int T>
 __global__ void __launch_bounds__(kGatherTiledThreads, 2) gather_tiled_kernel(GatherTiledArgs a)
 {
+    static_assert(T == kGtT, "strip tables are built for 8 x 8 tiles");
     extern __shared__ __align__(16) float4 gsm[];
     const int tile = blockIdx.x, b = blockIdx.y;
     const int tiles_x = (a.n + T - 1) / T;
@@ -218,7 +274,7 @@ __global__ void __launch_bounds__(kGatherTiledThreads, 2) gather_tiled_kernel(Ga
     const size_t vol = (size_t)a.n * a.n * a.nz;
     constexpr int ncols = T * T;
     constexpr int kCols = (ncols + 7) / 8;  // columns per warp
-    const size_t buf_f4 = (size_t)a.rows_cap * zw + (size_t)T * T * kMaxCand / 2;  // rows, then the table
+    const size_t buf_f4 = (size_t)a.rows_cap * zw + kGtSliceBytes / 16;  // rows, then the strip table
     const int S = a.stages;  // footprint buffers: angle g uses buffer g % S
     // shared memory: S footprint buffers, S + 1 mbarriers (the buffers',
     // then the descriptors'), the CTA's footprint descriptors and angle ids
@@ -227,7 +283,7 @@ __global__ void __launch_bounds__(kGatherTiledThreads, 2) gather_tiled_kernel(Ga
     int* sdesc = reinterpret_cast<int*>(gsm + S * buf_f4 + (S + 2) / 2);
     int* s_sel = sdesc + a.n_sel * kFpDescInts;
     const float* bvol_b = a.bvol + (size_t)b * a.n_sel * vol;
-    const size_t tab_stride = (size_t)a.n_tiles * ncols * kMaxCand;  // per angle
+    const size_t tab_stride = (size_t)a.n_tiles * (kGtSliceBytes / 8);  // int2 per angle
 
     if (threadIdx.x == 0) {
         for (int q = 0; q <= S; ++q) mbar_init(smem_u32(bars + q), 1);
@@ -240,7 +296,7 @@ __global__ void __launch_bounds__(kGatherTiledThreads, 2) gather_tiled_kernel(Ga
     auto issue = [&](int g) {
         const int q = g % S;
         issue_footprint(a, read_footprint(sdesc + g * kFpDescInts),
-                        a.tab + (size_t)s_sel[g] * tab_stride + (size_t)tile * ncols * kMaxCand,
+                        a.tab + (size_t)s_sel[g] * tab_stride + (size_t)tile * (kGtSliceBytes / 8),
                         bvol_b + (size_t)g * vol, smem_u32(bufs + q * buf_f4), smem_u32(bars + q));
     };
     bool desc_ok = true;
@@ -275,48 +331,38 @@ __global__ void __launch_bounds__(kGatherTiledThreads, 2) gather_tiled_kernel(Ga
         const int q = g % S;
         const bool landed = producer ? desc_ok : mbar_wait(smem_u32(bars + q), (uint32_t)((g / S) & 1));
         const float4* buf = bufs + q * buf_f4;
-        const int2* tab = reinterpret_cast<const int2*>(buf + (size_t)a.rows_cap * zw);
-        if (!producer) {
-            // Columns in groups of kGroup (all of a warp's columns at T = 8),
-            // candidate slot by slot: the slot's
-            // entries of the group's columns are read together (each a
-            // warp-wide broadcast of one shared-memory word), then their data
-            // rows, then the sums, so that the group's loads are in flight at
-            // once.  A column's candidates come first in its list, in the order
-            // they are summed; a slot empty in every column of the group ends it.
-            constexpr int kGroup = 8;
-    #pragma unroll
-            for (int k0 = 0; k0 < kCols; k0 += kGroup) {
-    #pragma unroll 1
-                for (int e = 0; e < kMaxCand; ++e) {
-                    int2 ent[kGroup];
-                    bool any = false;
-    #pragma unroll
-                    for (int u = 0; u < kGroup; ++u) {
-                        const int cl = warp + 8 * (k0 + u);
-                        ent[u] = (landed && k0 + u < kCols && cl < ncols) ? tab[cl * kMaxCand + e] : make_int2(0, 0);
-                        any |= ent[u].y != 0;
+        const float4* tabs = buf + (size_t)a.rows_cap * zw;
+        if (!producer && landed && lane < zw) {
+            // This warp's tile row, list by list: list l holds the samples
+            // whose lower column is l - 1, each read once and added to
+            // columns l - 1 and l.
+            const int* hdr = reinterpret_cast<const int*>(tabs) + warp * kGtHdr;
+            const int4* ent = reinterpret_cast<const int4*>(reinterpret_cast<const int*>(tabs) + kGtT * kGtHdr) +
+                              warp * (kGtLists * kGtMaxList);
+            // Fixed slots, filled under a predicate: the loads of different
+            // slots are independent, so many are in flight at once.  The
+            // list lengths and footprint rows come from the plan's tables;
+            // one outside its buffer is reported (SPECT_EINVAL) and skipped
+            // rather than read.
+            bool bad = false;
+#pragma unroll
+            for (int l = 0; l < kGtLists; ++l) {
+                const int cnt = hdr[l];
+                bad |= cnt > kGtMaxList;
+#pragma unroll
+                for (int k = 0; k < kGtMaxList; ++k) {
+                    if (k >= cnt) continue;
+                    const int4 en = ent[l * kGtMaxList + k];
+                    if ((unsigned)en.x >= (unsigned)a.rows_cap) {
+                        bad = true;
+                        continue;
                     }
-                    if (!any) break;
-                    if (lane < zw) {
-                        float4 v[kGroup];
-    #pragma unroll
-                        for (int u = 0; u < kGroup; ++u)
-                            if (k0 + u < kCols && ent[u].y != 0) v[u] = buf[(size_t)ent[u].x * zw + lane];
-    #pragma unroll
-                        for (int u = 0; u < kGroup; ++u) {
-                            if (k0 + u >= kCols || ent[u].y == 0) continue;
-                            const float w = __int_as_float(ent[u].y);
-                            float4& a4 = acc[k0 + u];
-                            const float2 lo = __ffma2_rn(make_float2(w, w), make_float2(v[u].x, v[u].y),
-                                                         make_float2(a4.x, a4.y));
-                            const float2 hi = __ffma2_rn(make_float2(w, w), make_float2(v[u].z, v[u].w),
-                                                         make_float2(a4.z, a4.w));
-                            a4 = make_float4(lo.x, lo.y, hi.x, hi.y);
-                        }
-                    }
+                    const float4 v = buf[(size_t)en.x * zw + lane];
+                    if (l >= 1) fma4(acc[l - 1], __int_as_float(en.y), v);
+                    if (l < kGtT) fma4(acc[l], __int_as_float(en.z), v);
                 }
             }
+            if (bad) atomicExch(a.err, SPECT_EINVAL);
         }
         ok = __syncthreads_and(landed);  // and buffer q is free for angle g + S
         if (!ok) break;
@@ -370,7 +416,7 @@ __global__ void __launch_bounds__(kGatherTiledThreads, 2) gather_tiled_kernel(Ga
 
 size_t gather_tiled_smem(int rows_cap, int zs, int T, int stages, int n_sel)
 {
-    const size_t bufs = stages * ((size_t)rows_cap * zs * sizeof(float) + (size_t)T * T * kMaxCand * sizeof(int2));
+    const size_t bufs = stages * ((size_t)rows_cap * zs * sizeof(float) + (size_t)kGtSliceBytes);
     const size_t bars = 16 * (size_t)((stages + 2) / 2);
     return bufs + bars + (size_t)n_sel * (kFpDescInts + 1) * sizeof(int);
 }
@@ -398,7 +444,7 @@ cudaError_t launch_gather_tiled_t(const GatherTiledArgs& a, cudaStream_t st)
 
 cudaError_t launch_gather_tiled(const GatherTiledArgs& a, cudaStream_t st)
 {
-    return a.T == 8 ? launch_gather_tiled_t<8>(a, st) : launch_gather_tiled_t<4>(a, st);
+    return a.T == kGtT ? launch_gather_tiled_t<kGtT>(a, st) : cudaErrorInvalidValue;
 }
 
 }  // namespace spect

@@ -136,13 +136,25 @@ struct GatherArgs {
 // rows of each angle staged in shared memory by bulk copies.
 constexpr int kFpMaxRows = 32;                    // rotated rows i per footprint
 constexpr int kFpDescInts = 4 + 2 * kFpMaxRows;   // {i0, ni, rows, 0}, then (jlo, len) per i
+// Tiled gather strip tables, per (angle, 8 x 8 tile): for each tile row (a
+// warp) the rotated-grid samples whose bilinear weights reach the row, in
+// kGtLists lists by the tile column of their lower weight (-1 .. 7), each of
+// at most kGtMaxList entries (a 1 x 2 cell of the rotated unit grid holds at
+// most three samples): a header of kGtHdr ints per row (the list lengths),
+// then per row kGtLists x kGtMaxList int4 entries {footprint row, weight to
+// column s, weight to s + 1, 0}.
+constexpr int kGtT = 8;
+constexpr int kGtLists = kGtT + 1;
+constexpr int kGtMaxList = 3;
+constexpr int kGtHdr = 12;
+constexpr int kGtSliceBytes = kGtT * kGtHdr * 4 + kGtT * kGtLists * kGtMaxList * 16;
 constexpr int kGatherMaxAngles = 16;                                // angles per back blur + gather launch
 constexpr int kGatherSumWarps = 8;                                  // tiled gather: warps that sum
 constexpr int kGatherTiledThreads = 32 * (kGatherSumWarps + 1);      // and one that issues the copies
 
 struct GatherTiledArgs {
     const float* bvol;     // [batch][n_sel][n][n][nz]
-    const int2* tab;       // [n_angles][n_tiles][T*T][kMaxCand] (footprint row, weight bits)
+    const int2* tab;       // [n_angles][n_tiles] strip tables of kGtSliceBytes (see gather_tiled.cu)
     const int* desc;       // [n_angles][n_tiles][kFpDescInts]
     const int* sel;        // [n_sel] angle ids
     int n, nz, n_sel, batch;
@@ -270,7 +282,7 @@ struct spect_plan {
     float* d_sens = nullptr;                  // [M][vol]
     size_t partial_planes = 0;                // capacity of a scratch's depth-chunk partials, planes
     int2* d_gtab = nullptr;                   // adjoint-rotation gather tables: [na][n*n][kMaxCand], or
-                                              // tiled [na][gt_tiles][gt_T^2][kMaxCand]
+                                              // tiled [na][gt_tiles] strip tables of kGtSliceBytes
     int* d_gdesc = nullptr;                   // tiled gather footprints [na][gt_tiles][kFpDescInts]
     float* d_sens_all = nullptr;              // BSREM: H^T 1 over all angles (first BSREM call)
     bool sens_all_ok = false;                 // d_sens_all matches the current attenuation map

@@ -977,10 +977,10 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
     // angle in flight; a third buffer measured slower on GB300).
     p->gather_tiled = p->n >= 128 && p->nz <= 128;
     if (p->gather_tiled) {
-        p->gt_T = 8;
+        p->gt_T = kGtT;
         const int tx = (p->n + p->gt_T - 1) / p->gt_T;
         p->gt_tiles = tx * tx;
-        if ((rc = dev_alloc(p, &p->d_gtab, (size_t)p->na * p->gt_tiles * p->gt_T * p->gt_T * kMaxCand)) ||
+        if ((rc = dev_alloc(p, &p->d_gtab, (size_t)p->na * p->gt_tiles * (kGtSliceBytes / 8))) ||
             (rc = dev_alloc(p, &p->d_gdesc, (size_t)p->na * p->gt_tiles * kFpDescInts))) {
             free_plan(p);
             return rc;
