@@ -166,7 +166,7 @@ size_t request_bytes(const spect_geom& g, int num_sms)
     size_t b = 0;
     b += M * vol * 4;                                                    // sensitivities
     b += std::max<size_t>(4 * (size_t)num_sms, max_subset) * plane * 4;  // depth-chunk partials
-    b += na * (n + 7) * (n + 7) * spect::kMaxCand * 8;                   // gather tables (tiles padded)
+    b += na * (n + 7) * (n + 7) * spect::kMaxCand * 8;                   // gather tables (either layout)
     b += na * ((n + 3) / 4) * ((n + 3) / 4) * spect::kFpDescInts * 4;    // tiled-gather footprints
     b += std::max<size_t>(max_subset, 16) * vol * 4;                     // rotated-frame volumes
     b += max_subset * plane * 4 + vol * 4;                               // ratio, back projection

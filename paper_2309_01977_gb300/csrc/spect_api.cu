@@ -999,8 +999,13 @@ int spect_plan_create(const spect_geom* geom, const float* mu_dev, void* stream,
         p->gt_zs = p->nz;
         p->gt_stages = 2;
         if (err != 0 || gather_tiled_smem(p->gt_rows, p->gt_zs, p->gt_T, 2, kGatherMaxAngles) > (size_t)smem_optin) {
-            // footprints too large for shared memory: the per-column gather
+            // footprints too large for shared memory, or a strip list past
+            // its slots: the per-column gather, whose tables replace these
             p->gather_tiled = false;
+            dev_free(p, p->d_gtab, (size_t)p->na * p->gt_tiles * kGtSliceBytes);
+            dev_free(p, p->d_gdesc, (size_t)p->na * p->gt_tiles * kFpDescInts * sizeof(int));
+            p->d_gtab = nullptr;
+            p->d_gdesc = nullptr;
             SPECT_CK(cudaMemsetAsync(p->d_err, 0, sizeof(int), st), "clear status");
         }
     }
