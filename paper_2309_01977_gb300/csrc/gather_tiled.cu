@@ -120,14 +120,14 @@ __global__ void gather_tiled_table_kernel(const float4* __restrict__ cs_tab, int
     // lower bilinear column is xa = tx T + l - 1 and whose rows ya, ya + 1
     // include the tile row y: weights (1 - ax) wy to column xa and ax wy to
     // xa + 1, each the product gather_kernel's table forms (zero where the
-    // column lies outside the tile or the volume).  Two passes: count, then
-    // write when the list fits its kGtMaxList slots (else the plan takes the
-    // per-column gather).
+    // column lies outside the tile or the volume).  Entries go to the list's
+    // kGtMaxList slots as they are found; a longer list is reported and the
+    // plan takes the per-column gather.
     const int lt = threadIdx.x;
     const bool lister = fits && lt < kGtT * kGtLists;
     const int w = lt / kGtLists, l = lt % kGtLists;
     const int yr = ty * T + w, xa_l = tx * T + l - 1;
-    auto walk = [&](int2* out) {
+    auto walk = [&](int2* __restrict__ out) {
         int count = 0;
         if (!lister || yr >= n) return 0;
         const float c = 0.5f * (float)(n - 1);
@@ -146,7 +146,7 @@ __global__ void gather_tiled_table_kernel(const float4* __restrict__ cs_tab, int
                 const float w0 = (l >= 1 && xa < n) ? (1.f - ax) * wy : 0.f;
                 const float w1 = (l + 1 <= T && xa + 1 < n) ? ax * wy : 0.f;
                 if (w0 == 0.f && w1 == 0.f) continue;
-                if (out) {
+                if (count < kGtMaxList) {
                     out[2 * count] = make_int2(s_off[r] + j - s_jlo[r], __float_as_int(w0));
                     out[2 * count + 1] = make_int2(__float_as_int(w1), 0);
                 }
@@ -158,13 +158,9 @@ __global__ void gather_tiled_table_kernel(const float4* __restrict__ cs_tab, int
     int* hdr = reinterpret_cast<int*>(tab) + ((size_t)angle * gridDim.x + tile) * (kGtSliceBytes / 4);
     int2* ent = reinterpret_cast<int2*>(hdr + kGtT * kGtHdr);
     if (lister) {
-        const int cnt = walk(nullptr);
-        if (cnt > kGtMaxList) {
-            atomicExch(err, SPECT_EINVAL);
-        } else {
-            walk(ent + 2 * (size_t)kGtMaxList * (w * kGtLists + l));
-            hdr[w * kGtHdr + l] = cnt;
-        }
+        const int cnt = walk(ent + 2 * (size_t)kGtMaxList * (w * kGtLists + l));
+        if (cnt > kGtMaxList) atomicExch(err, SPECT_EINVAL);
+        hdr[w * kGtHdr + l] = min(cnt, kGtMaxList);
     }
 }
 
