@@ -242,12 +242,7 @@ __device__ __forceinline__ void issue_footprint(const GatherTiledArgs& a, const 
 
 }  // namespace
 
-// 288 threads: warps w < 8 sum columns w, w + 8, ... of the T x T tile, lane
-// l holding float4 l of the z segment (lanes past zs/4 idle); warp 8 issues
-// the footprint copies (about a dozen bulk copies an angle, which take as
-// long to issue as the sums of an angle take), so that they overlap the
-// sums.  Two CTAs per SM (their shared memory allows two): at most 112
-// registers.
+// a4 += w v, two packed FMAs.
 __device__ __forceinline__ void fma4(float4& a4, float w, const float4& v)
 {
     const float2 lo = __ffma2_rn(make_float2(w, w), make_float2(v.x, v.y), make_float2(a4.x, a4.y));
@@ -255,6 +250,13 @@ __device__ __forceinline__ void fma4(float4& a4, float w, const float4& v)
     a4 = make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
+// 288 threads: warp w < 8 owns row w of the 8 x 8 tile (columns x = 8 tx +
+// k, y = 8 ty + w, k = 0 .. 7, in accumulators acc[k]), lane l holding
+// float4 l of the z segment (lanes past zs/4 idle); warp 8 issues the
+// footprint copies (about a dozen bulk copies an angle, which take about as
+// long to issue as an angle's sums), so that they overlap the sums.  Two
+// CTAs per SM (their shared memory allows two; 18 warps cap the registers
+// at 96).
 template <int T>
 __global__ void __launch_bounds__(kGatherTiledThreads, 2) gather_tiled_kernel(GatherTiledArgs a)
 {
