@@ -110,3 +110,19 @@ def test_strip_lists_are_the_bilinear_transpose(n, theta):
     ref = _bilinear_transpose(b, u, v, n)
     got = _strip_gather(b, u, v, n)
     assert np.allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_table_slices_are_whole_bulk_copies():
+    """The issuing warp moves each (angle, tile) strip table and footprint
+    descriptor with one cp.async.bulk: sizes and offsets must be multiples
+    of 16 bytes, and a footprint row per lane must cover a descriptor."""
+    text = open(os.path.join(ROOT, "paper_2309_01977_gb300", "csrc", "internal.h")).read()
+    assert "constexpr int kGtLists = kGtT + 1;" in text
+    T, hdr, slots = _constant("kGtT"), _constant("kGtHdr"), _constant("kGtMaxList")
+    slice_bytes = T * hdr * 4 + T * (T + 1) * slots * 16
+    assert slice_bytes % 16 == 0
+    assert (T * hdr * 4) % 16 == 0  # entries start 16-byte aligned
+    assert hdr >= T + 1
+    desc_ints = 4 + 2 * _constant("kFpMaxRows")
+    assert (desc_ints * 4) % 16 == 0
+    assert _constant("kFpMaxRows") == 32  # one footprint row per lane of the issuing warp
